@@ -1,0 +1,180 @@
+/*
+ * oq: Wilson-clover Dirac operator and mixed-precision solvers for NVIDIA
+ * GB300 (sm_103a).  C ABI.
+ *
+ * The operator is the O(a)-improved Wilson-Dirac operator named in Sec. 1 of
+ * Gruber et al., "Performance optimizations for porting the openQ*D package
+ * to GPUs" (LATTICE2021), whose application to a spinor field is the
+ * SpMV-like kernel the paper singles out (Sec. 1, footnote 1):
+ *
+ *   (D psi)(x) = A(x) psi(x) - 1/2 sum_mu [ U_mu(x)(1 - g_mu) psi(x+mu)
+ *                                        + U_mu(x-mu)^dag (1 + g_mu) psi(x-mu) ]
+ *   A(x) = (4 + m0) + c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x),  m0 = 1/(2 kappa) - 4,
+ *
+ * chiral gamma basis (g5 = diag(1,1,-1,-1)), clover-leaf F_{mu nu}, fermion
+ * fields antiperiodic (or periodic) in time.  Sites are ordered even-first
+ * (Sec. 3, Fig. 3); the even-odd reduced operator is
+ *   Dhat = D_ee - D_eo D_oo^{-1} D_oe.
+ *
+ * Conventions for every entry point:
+ *  - Return value: OQ_OK (0) or a negative OQ_ERR_* code; oq_error_string()
+ *    names it.  On error nothing was enqueued unless the code is OQ_ERR_CUDA.
+ *  - Pointers named *_dev are device pointers owned by the caller; the
+ *    library never frees or keeps them beyond the call.  Derived state
+ *    (packed links, clover blocks, solver work vectors) is owned by the
+ *    handle and freed by oq_destroy().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Operator applications and packing are asynchronous on it;
+ *    the solvers synchronise it before returning (they fill oq_status).
+ *  - A handle is used by one host thread at a time.
+ *
+ * Canonical host layout (binary64 complex, interleaved re/im):
+ *   site x = ((x0*L1 + x1)*L2 + x2)*L3 + x3, x0 = time (slowest);
+ *   links   U[x][mu][a][b]       (mu = 0..3, 18 doubles per link)
+ *   spinors psi[x][spin][colour] (24 doubles per site)
+ * Packed device layout (what oq_dw_apply / oq_dw_hat_apply read and write):
+ *   one half field per parity, Vh = V/2 sites, eo index = x >> 1, each site's
+ *   24 reals in 16-byte chunks stored chunk-major ([chunk][Vh]); F64: 12
+ *   chunks, F32: 6 chunks, BF16/F16: 3 chunks.  A full field is the even half
+ *   followed by the odd half.  nrhs fields are consecutive in memory.
+ *   oq_spinor_bytes() gives the sizes.
+ */
+#ifndef OQ_H
+#define OQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oq_ctx* oq_handle;
+
+/* storage precision of spinor fields (arithmetic is binary32 for F32/BF16/F16) */
+enum { OQ_F64 = 0, OQ_F32 = 1, OQ_BF16 = 2, OQ_F16 = 3 };
+/* storage of the binary32 link copy: 18 reals, or 12 reals with the third
+ * row rebuilt as conj(row0 x row1) (SU(3) links only) */
+enum { OQ_LINK_18 = 0, OQ_LINK_12 = 1 };
+/* field subsets for packing */
+enum { OQ_EVEN = 0, OQ_ODD = 1, OQ_FULL = 2 };
+
+enum {
+  OQ_OK = 0,
+  OQ_ERR_ARG = -1,       /* invalid argument (null pointer, size, enum) */
+  OQ_ERR_CUDA = -2,      /* a CUDA call failed */
+  OQ_ERR_NOMEM = -3,     /* device allocation failed */
+  OQ_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up */
+  OQ_ERR_NONFINITE = -5, /* NaN/Inf met in a binary64 norm */
+  OQ_ERR_NOCONV = -6,    /* solver stopped at nmx without reaching res */
+  OQ_ERR_STATE = -7      /* call out of order (e.g. no gauge field uploaded) */
+};
+
+typedef struct {
+  int L[4];  /* L[0] = T, all extents even and >= 2 */
+  int bc_t;  /* fermion factor across the time boundary: -1 antiperiodic, +1 periodic */
+} oq_lattice;
+
+/* Solver settings, after Table 2 of the paper (res, nmx, nkv, ncy, nmr, bs)
+ * plus the storage type of the "small" vectors (sdtype; the "large" type and
+ * the reduction type are always binary64, Sec. 2.1, 3.1). */
+typedef struct {
+  double res;        /* target relative residual (binary64) */
+  int nmx;           /* max regular CG steps / GCR steps */
+  int nkv;           /* GCR: Krylov vectors before a restart */
+  int ncy;           /* SAP cycles per GCR step (maximum if adaptive) */
+  int nmr;           /* MR steps per block and cycle (maximum if adaptive) */
+  int bs[4];         /* SAP block extents */
+  int sdtype;        /* OQ_F64 / OQ_F32 / OQ_BF16 / OQ_F16 */
+  double delta;      /* CGNE reset when ||r_rec|| <= delta ||r_reset||; <= 0: 10 eps of sdtype (max 0.1) */
+  int adaptive;      /* SAP: adaptive cycle / MR counts (Sec. 3.2) */
+  double alpha;      /* SAP adaptive MR ratio threshold (Sec. 3.2, default 0.9) */
+} oq_solver_params;
+
+typedef struct {
+  int steps;           /* regular CG steps or GCR steps ("status" of the paper) */
+  int resets;          /* CGNE reset steps (binary64 residual recomputations) */
+  int restarts;        /* GCR restarts */
+  int converged;       /* 1 if true_rel_res <= res */
+  double true_rel_res; /* binary64 ||eta - A psi|| / ||eta|| at exit */
+} oq_status;
+
+/* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no
+ * device: the current CUDA device at creation is used for every call. */
+int oq_create(oq_handle* h, const oq_lattice* lats, int nlat);
+int oq_destroy(oq_handle h);
+const char* oq_error_string(int code);
+
+/* Bytes of one packed spinor field of lattice `lat` (subset OQ_EVEN/OQ_ODD:
+ * half field, OQ_FULL: full field). */
+size_t oq_spinor_bytes(oq_handle h, int lat, int prec, int subset);
+
+/* Upload links (canonical binary64 layout, device memory) and build the
+ * packed binary64 copy and the binary32 copy in `link_fmt`.  OQ_LINK_12 needs
+ * det U = 1 (SU(3)); U(3) = SU(3) x U(1) links need OQ_LINK_18.  Sec. 1
+ * (QCD+QED with O(a)-improved Wilson fermions). */
+int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int link_fmt, void* stream);
+
+/* Clover term A(x) and A^{-1}(x) (odd sites) from the uploaded links:
+ * clover-leaf field strength, two Hermitian 6x6 chiral blocks per site,
+ * built and inverted in binary64, stored in binary64 and binary32. */
+int oq_clover_build(oq_handle h, int lat, double kappa, double csw, void* stream);
+
+/* Convert canonical binary64 spinors (device) to packed `prec` fields and
+ * back.  pack multiplies by `scale` before rounding (round to nearest even),
+ * unpack divides by it.  subset OQ_EVEN / OQ_ODD read/write only those sites
+ * of the canonical field (unpack leaves the other sites untouched). */
+int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const double* canon_dev,
+                   void* packed_dev, double scale, int nrhs, void* stream);
+int oq_spinor_unpack(oq_handle h, int lat, int prec, int subset, const void* packed_dev,
+                     double* canon_dev, double scale, int nrhs, void* stream);
+
+/* out = D in (dagger: D^dag in = g5 D g5 in) on full packed fields of
+ * precision prec (Sec. 1, footnote 1).  in and out must not overlap. */
+int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs,
+                int dagger, void* stream);
+
+/* out_e = Dhat in_e (or Dhat^dag), even half fields of precision prec
+ * (Sec. 3, Fig. 3 even-odd ordering).  Two passes; the odd intermediate
+ * lives in handle-owned scratch.  in and out must not overlap. */
+int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs,
+                    int dagger, void* stream);
+
+/* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and
+ * out[2k], out[2k+1] = Re, Im <x_k, y_k> (host arrays of nrhs / 2 nrhs). */
+int oq_norm2(oq_handle h, int lat, int prec, int subset, const void* x_dev, int nrhs,
+             double* out_host, void* stream);
+int oq_dot(oq_handle h, int lat, int prec, int subset, const void* x_dev, const void* y_dev,
+           int nrhs, double* out_host, void* stream);
+
+/* CGNE with reset steps (Sec. 2, Fig. 4): solves Dhat^dag Dhat psi = eta on
+ * the even sites.  eta_dev / psi_dev: canonical binary64 full-lattice fields
+ * (odd sites ignored on input, zero on output); psi_dev is overwritten (no
+ * initial guess).  Regular steps store vectors in p->sdtype with binary32
+ * arithmetic; reductions, the solution and reset-step residuals are
+ * binary64.  Stops when the binary64 residual ||eta - Dhat^dag Dhat psi|| <=
+ * res ||eta||, or after nmx regular steps (OQ_ERR_NOCONV).  st: host array
+ * of nrhs entries. */
+int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
+                  double* psi_dev, int nrhs, oq_status* st, void* stream);
+
+/* Instrumentation: while profiling is on, every stencil launch is bracketed
+ * by CUDA events on its own stream.  oq_profile_stop() synchronises the
+ * device and returns one entry per (mode, epilogue, precision): mode 0 = full
+ * Dw, 1 = Dhat pass 1 (odd sites), 2 = Dhat pass 2 (even sites); epi 0 =
+ * plain store, 1 = store + norm, 2 = fused CG update, 3 = binary64 residual;
+ * bytes = algorithmic bytes (each operand counted once) of all launches. */
+typedef struct {
+  int mode, epi, prec, launches;
+  double total_ms;
+  double bytes;
+} oq_kernel_time;
+int oq_profile_start(oq_handle h);
+/* Number of kernels the library has launched through this handle so far. */
+long long oq_kernel_launches(oq_handle h);
+int oq_profile_stop(oq_handle h, oq_kernel_time* out, int max_entries, int* n_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OQ_H */

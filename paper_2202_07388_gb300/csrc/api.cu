@@ -1,0 +1,290 @@
+// C ABI of the library: handle management, uploads, operator applications,
+// reductions.  The solvers live in cgne.cu (and the later solver files).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/oq.h"
+#include "ctx.h"
+#include "oq_kernels.h"
+
+using namespace oq;
+
+namespace oq {
+cudaError_t launch_hop(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  switch (L.prec) {
+    case P_F64: return launch_hop_f64(L, a, s);
+    case P_F32: return launch_hop_f32(L, a, s);
+    case P_BF16: return launch_hop_bf16(L, a, s);
+    case P_F16: return launch_hop_f16(L, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace oq
+
+extern "C" const char* oq_error_string(int code) {
+  switch (code) {
+    case OQ_OK: return "ok";
+    case OQ_ERR_ARG: return "invalid argument";
+    case OQ_ERR_CUDA: return "CUDA error";
+    case OQ_ERR_NOMEM: return "out of device memory";
+    case OQ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case OQ_ERR_NONFINITE: return "non-finite value in a binary64 norm";
+    case OQ_ERR_NOCONV: return "solver did not converge within nmx steps";
+    case OQ_ERR_STATE: return "call out of order (gauge field or clover term missing)";
+    default: return "unknown error";
+  }
+}
+
+extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
+  if (!out || !lats || nlat < 1 || nlat > 64) return OQ_ERR_ARG;
+  *out = nullptr;
+  for (int k = 0; k < nlat; ++k) {
+    for (int mu = 0; mu < 4; ++mu)
+      if (lats[k].L[mu] < 2 || (lats[k].L[mu] & 1)) return OQ_ERR_ARG;
+    if (lats[k].bc_t != 1 && lats[k].bc_t != -1) return OQ_ERR_ARG;
+  }
+  oq_ctx* h = new (std::nothrow) oq_ctx();
+  if (!h) return OQ_ERR_NOMEM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return OQ_ERR_CUDA;
+  }
+  h->lats.resize(nlat);
+  for (int k = 0; k < nlat; ++k) {
+    LatCtx& L = h->lats[k];
+    for (int mu = 0; mu < 4; ++mu) L.g.L[mu] = lats[k].L[mu];
+    L.g.Lh3 = lats[k].L[3] / 2;
+    L.g.Vh = (long)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3] / 2;
+    L.g.bc_t = (float)lats[k].bc_t;
+  }
+  *out = h;
+  return OQ_OK;
+}
+
+extern "C" int oq_destroy(oq_handle h) {
+  if (!h) return OQ_ERR_ARG;
+  cudaDeviceSynchronize();
+  h->release();
+  delete h;
+  return OQ_OK;
+}
+
+extern "C" size_t oq_spinor_bytes(oq_handle h, int lat, int prec, int subset) {
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 3 || subset < 0 || subset > 2) return 0;
+  size_t half = (size_t)spinor_half_bytes(h->lats[lat].g.Vh, prec);
+  return subset == OQ_FULL ? 2 * half : half;
+}
+
+extern "C" int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int link_fmt, void* stream) {
+  if (!h || !U_dev || lat < 0 || lat >= (int)h->lats.size()) return OQ_ERR_ARG;
+  if (link_fmt != OQ_LINK_18 && link_fmt != OQ_LINK_12) return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n64 = sizeof(double) * 2 * 4 * 18 * L.g.Vh;
+  const size_t n32 = sizeof(float) * 2 * 4 * (link_fmt == OQ_LINK_12 ? 12 : 18) * L.g.Vh;
+  int rc = h->alloc(&L.u64, n64);
+  if (rc) return rc;
+  rc = h->alloc(&L.u32, n32);
+  if (rc) return rc;
+  L.link_fmt = link_fmt;
+  if (pack_links(L.g, U_dev, (double*)L.u64.p, L.u32.p, link_fmt, s) != cudaSuccess) return OQ_ERR_CUDA;
+  L.has_gauge = true;
+  L.has_clover = false;
+  return OQ_OK;
+}
+
+extern "C" int oq_clover_build(oq_handle h, int lat, double kappa, double csw, void* stream) {
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || !(kappa > 0.0) || !isfinite(csw)) return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  if (!L.has_gauge) return OQ_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n64 = sizeof(double) * 2 * 72 * L.g.Vh, n32 = sizeof(float) * 2 * 72 * L.g.Vh;
+  int rc = h->alloc(&L.a64, n64);
+  if (!rc) rc = h->alloc(&L.a32, n32);
+  if (!rc) rc = h->alloc(&L.i64, n64);
+  if (!rc) rc = h->alloc(&L.i32, n32);
+  if (!rc) rc = h->ensure_scratch();
+  if (rc) return rc;
+  if (cudaMemsetAsync(h->status_dev, 0, sizeof(int), s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (build_clover(L.g, (const double*)L.u64.p, kappa, csw, (double*)L.a64.p, (float*)L.a32.p, (double*)L.i64.p,
+                   (float*)L.i32.p, h->status_dev, s) != cudaSuccess)
+    return OQ_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (st) return OQ_ERR_NONFINITE;  // a singular clover block
+  L.kappa = kappa;
+  L.csw = csw;
+  L.has_clover = true;
+  return OQ_OK;
+}
+
+static bool valid_lat(oq_handle h, int lat) { return h && lat >= 0 && lat < (int)h->lats.size(); }
+
+extern "C" int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const double* canon_dev, void* packed_dev,
+                              double scale, int nrhs, void* stream) {
+  if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 3 || subset < 0 || subset > 2 ||
+      nrhs < 1 || !(scale != 0.0) || !isfinite(scale))
+    return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  const long cstride = 2 * L.g.Vh * 12;  // double2 per canonical field
+  const long ostride = (long)oq_spinor_bytes(h, lat, prec, subset);
+  return pack_spinor(L.g, prec, subset, canon_dev, packed_dev, scale, nrhs, cstride, ostride, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? OQ_OK
+             : OQ_ERR_CUDA;
+}
+
+extern "C" int oq_spinor_unpack(oq_handle h, int lat, int prec, int subset, const void* packed_dev, double* canon_dev,
+                                double scale, int nrhs, void* stream) {
+  if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 3 || subset < 0 || subset > 2 ||
+      nrhs < 1 || !(scale != 0.0) || !isfinite(scale))
+    return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  const long cstride = 2 * L.g.Vh * 12;
+  const long istride = (long)oq_spinor_bytes(h, lat, prec, subset);
+  return unpack_spinor(L.g, prec, subset, packed_dev, canon_dev, scale, nrhs, istride, cstride,
+                       (cudaStream_t)stream) == cudaSuccess
+             ? OQ_OK
+             : OQ_ERR_CUDA;
+}
+
+static bool overlap(const void* a, const void* b, size_t n) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + n && y < x + n;
+}
+
+extern "C" int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs, int dagger,
+                           void* stream) {
+  if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 3 || nrhs < 1) return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  if (!L.has_clover) return OQ_ERR_STATE;
+  const size_t full = oq_spinor_bytes(h, lat, prec, OQ_FULL);
+  if (overlap(in_dev, out_dev, full * nrhs)) return OQ_ERR_ARG;
+  HopArgs a = h->hop_args(lat, prec);
+  a.in = in_dev;
+  a.in2 = in_dev;
+  a.out = out_dev;
+  a.in_stride = a.in2_stride = a.out_stride = (long)full;
+  a.half_bytes = (long)full / 2;
+  a.nrhs = nrhs;
+  HopLaunch hl = h->hop_launch(lat, prec, HOP_DW, dagger ? 1 : 0, EPI_NONE, nrhs);
+  return h->run_hop(hl, a, (cudaStream_t)stream);
+}
+
+extern "C" int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs, int dagger,
+                               void* stream) {
+  if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 3 || nrhs < 1) return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  if (!L.has_clover) return OQ_ERR_STATE;
+  const size_t half = oq_spinor_bytes(h, lat, prec, OQ_EVEN);
+  if (overlap(in_dev, out_dev, half * nrhs)) return OQ_ERR_ARG;
+  void* t = nullptr;
+  int rc = h->workspace(lat, "dwhat_t", half * nrhs, &t);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  HopArgs a = h->hop_args(lat, prec);
+  a.nrhs = nrhs;
+  a.in_stride = a.in2_stride = a.out_stride = (long)half;
+  a.half_bytes = (long)half;
+  // pass 1: t_o = A_oo^{-1} (-1/2 H_oe in_e)
+  a.in = in_dev;
+  a.out = t;
+  a.p = 1;
+  HopLaunch l1 = h->hop_launch(lat, prec, HOP_P1, dagger ? 1 : 0, EPI_NONE, nrhs);
+  rc = h->run_hop(l1, a, s);
+  if (rc) return rc;
+  // pass 2: out_e = A_ee in_e + 1/2 H_eo t_o
+  a.in = t;
+  a.in2 = in_dev;
+  a.out = out_dev;
+  a.p = 0;
+  HopLaunch l2 = h->hop_launch(lat, prec, HOP_P2, dagger ? 1 : 0, EPI_NONE, nrhs);
+  return h->run_hop(l2, a, s);
+}
+
+static int reduce_common(oq_handle h, int lat, int prec, int subset, const void* x, const void* y, int nrhs,
+                         double* out_host, void* stream) {
+  if (!valid_lat(h, lat) || !x || !out_host || prec < 0 || prec > 3 || subset < 0 || subset > 2 || nrhs < 1)
+    return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nslot = (y ? 2 : 1) * nrhs;
+  const int grid = reduce_grid(L.g.Vh);
+  int rc = h->ensure_reduce(nslot * 2, grid);
+  if (rc) return rc;
+  const long half = (long)oq_spinor_bytes(h, lat, prec, OQ_EVEN);
+  const long stride = (long)oq_spinor_bytes(h, lat, prec, subset);
+  const int nparts = subset == OQ_FULL ? 2 : 1;
+  for (int part = 0; part < nparts; ++part) {
+    RedArgs ra = h->red_args(FIN_STORE, 0);
+    ra.result = h->results + part * nslot;
+    const char* xp = (const char*)x + part * half;
+    cudaError_t e = y ? reduce_dot(prec, xp, (const char*)y + part * half, L.g.Vh, stride, nrhs, ra, s)
+                      : reduce_norm2(prec, xp, L.g.Vh, stride, nrhs, ra, s);
+    if (e != cudaSuccess) return OQ_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(h->results_host, h->results, sizeof(double) * nslot * nparts, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return OQ_ERR_CUDA;
+  for (int k = 0; k < nslot; ++k) out_host[k] = h->results_host[k] + (nparts == 2 ? h->results_host[nslot + k] : 0.0);
+  return OQ_OK;
+}
+
+extern "C" int oq_norm2(oq_handle h, int lat, int prec, int subset, const void* x_dev, int nrhs, double* out_host,
+                        void* stream) {
+  return reduce_common(h, lat, prec, subset, x_dev, nullptr, nrhs, out_host, stream);
+}
+
+extern "C" int oq_dot(oq_handle h, int lat, int prec, int subset, const void* x_dev, const void* y_dev, int nrhs,
+                      double* out_host, void* stream) {
+  if (!y_dev) return OQ_ERR_ARG;
+  return reduce_common(h, lat, prec, subset, x_dev, y_dev, nrhs, out_host, stream);
+}
+
+extern "C" int oq_profile_start(oq_handle h) {
+  if (!h) return OQ_ERR_ARG;
+  for (auto& r : h->prof) {
+    h->event_pool.push_back(r.e0);
+    h->event_pool.push_back(r.e1);
+  }
+  h->prof.clear();
+  h->prof_on = true;
+  return OQ_OK;
+}
+
+extern "C" int oq_profile_stop(oq_handle h, oq_kernel_time* out, int max_entries, int* n_entries) {
+  if (!h || !n_entries || (max_entries > 0 && !out)) return OQ_ERR_ARG;
+  h->prof_on = false;
+  if (cudaDeviceSynchronize() != cudaSuccess) return OQ_ERR_CUDA;
+  std::vector<oq_kernel_time> agg;
+  for (auto& r : h->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return OQ_ERR_CUDA;
+    oq_kernel_time* t = nullptr;
+    for (auto& a : agg)
+      if (a.mode == r.mode && a.epi == r.epi && a.prec == r.prec) t = &a;
+    if (!t) {
+      agg.push_back(oq_kernel_time{r.mode, r.epi, r.prec, 0, 0.0, 0.0});
+      t = &agg.back();
+    }
+    t->launches += 1;
+    t->total_ms += ms;
+    t->bytes += r.bytes;
+    h->event_pool.push_back(r.e0);
+    h->event_pool.push_back(r.e1);
+  }
+  h->prof.clear();
+  *n_entries = (int)agg.size();
+  for (int k = 0; k < (int)agg.size() && k < max_entries; ++k) out[k] = agg[k];
+  return OQ_OK;
+}
+
+extern "C" long long oq_kernel_launches(oq_handle h) { return h ? h->launches : -1; }

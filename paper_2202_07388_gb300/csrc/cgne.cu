@@ -1,0 +1,241 @@
+// CGNE with reset steps (Sec. 2 and the caption of Fig. 4).
+//
+// Solves A psi = eta, A = Dhat^dag Dhat, on the even sites.  Regular CG steps
+// run with vectors stored in the small type (binary32, bfloat16 or binary16;
+// binary32 arithmetic), every reduction is binary64.  The small-type CG
+// solves A x_s = r_d / s for the current binary64 residual r_d, scaled by
+// s = ||r_d|| / sqrt(12 Ve) so that stored components are O(1).  A reset step
+// adds s x_s to the binary64 solution x_d and recomputes r_d = eta - A x_d in
+// binary64 once the recursive residual has dropped below delta times its
+// value at the previous reset (delta ~ 10 eps of the small type), reached the
+// target, or nmx steps are used.  The regular steps never wait for the host:
+// alpha, beta and the reset decision are computed on the device by the last
+// CTA of each fused grid reduction; the host looks at the per-rhs state once
+// every CHUNK iterations.
+//
+// One iteration = 5 launches:
+//   P1(p -> t)  ;  P2(t, p -> u = Dhat p) + ||u||^2 -> alpha
+//   P1^dag(u -> t) ; P2^dag(t, u -> q) fused with x += alpha p, r -= alpha q,
+//   ||r||^2 -> beta / stop test  ;  p = r + beta p
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/oq.h"
+#include "ctx.h"
+#include "oq_kernels.h"
+
+using namespace oq;
+
+namespace {
+
+const int CHUNK = 8;
+
+double default_delta(int prec) {
+  const double eps = prec == P_F32 ? ldexp(1.0, -23) : prec == P_BF16 ? ldexp(1.0, -7)
+                   : prec == P_F16 ? ldexp(1.0, -10) : 0.0;
+  double d = 10.0 * eps;
+  return d > 0.1 ? 0.1 : d;
+}
+
+}  // namespace
+
+extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev,
+                             double* psi_dev, int nrhs, oq_status* st, void* stream) {
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
+  const int P = prm->sdtype;
+  if (P < 0 || P > 3 || !(prm->res > 0.0) || prm->nmx < 1) return OQ_ERR_ARG;
+  LatCtx& L = h->lats[lat];
+  if (!L.has_clover) return OQ_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long Vh = L.g.Vh;
+  const int XP = P == P_F64 ? P_F64 : P_F32;
+  const size_t h64 = spinor_half_bytes(Vh, P_F64), hP = spinor_half_bytes(Vh, P), hX = spinor_half_bytes(Vh, XP);
+  const size_t canon_field = sizeof(double) * 24 * 2 * Vh;
+  void *eta64, *xd, *rd, *t64, *u64v, *pv, *rv, *uv, *tv, *xs;
+  int rc = 0;
+  rc |= h->workspace(lat, "cg_eta64", h64 * nrhs, &eta64);
+  rc |= h->workspace(lat, "cg_xd", h64 * nrhs, &xd);
+  rc |= h->workspace(lat, "cg_rd", h64 * nrhs, &rd);
+  rc |= h->workspace(lat, "cg_t64", h64 * nrhs, &t64);
+  rc |= h->workspace(lat, "cg_u64", h64 * nrhs, &u64v);
+  rc |= h->workspace(lat, "cg_p", hP * nrhs, &pv);
+  rc |= h->workspace(lat, "cg_r", hP * nrhs, &rv);
+  rc |= h->workspace(lat, "cg_u", hP * nrhs, &uv);
+  rc |= h->workspace(lat, "cg_t", hP * nrhs, &tv);
+  rc |= h->workspace(lat, "cg_xs", hX * nrhs, &xs);
+  if (rc) return OQ_ERR_NOMEM;
+  const long grid_hop = (Vh + 31) / 32;  // upper bound on CTAs of any stencil launch
+  rc = h->ensure_reduce(2 * nrhs, grid_hop > reduce_grid(Vh) ? grid_hop : reduce_grid(Vh));
+  if (!rc) rc = h->ensure_cg(nrhs);
+  if (rc) return rc;
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return OQ_ERR_CUDA; \
+  } while (0)
+#define KL(x)                                   \
+  do {                                          \
+    h->launches += 1;                           \
+    if ((x) != cudaSuccess) return OQ_ERR_CUDA; \
+  } while (0)
+#define RK(x)              \
+  do {                     \
+    int rc_ = (x);         \
+    if (rc_) return rc_;   \
+  } while (0)
+
+  // eta -> packed binary64 even field; x_d = 0, x_s = 0
+  KL(pack_spinor(L.g, P_F64, OQ_EVEN, eta_dev, eta64, 1.0, nrhs, 2 * Vh * 12, (long)h64, s));
+  CK(cudaMemsetAsync(xd, 0, h64 * nrhs, s));
+  CK(cudaMemsetAsync(xs, 0, hX * nrhs, s));
+  CK(cudaMemcpyAsync(rd, eta64, h64 * nrhs, cudaMemcpyDeviceToDevice, s));
+  {
+    RedArgs ra = h->red_args(FIN_STORE, 0);
+    KL(reduce_norm2(P_F64, eta64, Vh, (long)h64, nrhs, ra, s));
+  }
+  CK(cudaMemcpyAsync(h->results_host, h->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> eta_n(nrhs);
+  std::vector<int> resets(nrhs, 0);
+  const double delta = prm->delta > 0.0 ? prm->delta : default_delta(P);
+  const double ncomp = 12.0 * (double)Vh;
+  CgState* cs = h->cg_host;
+  for (int k = 0; k < nrhs; ++k) {
+    eta_n[k] = sqrt(h->results_host[k]);
+    memset(&cs[k], 0, sizeof(CgState));
+    cs[k].mode = MODE_RESET;
+    cs[k].rd2 = h->results_host[k];
+    cs[k].nmx = prm->nmx;
+    cs[k].delta2 = delta * delta;
+  }
+
+  // decide, per rhs in MODE_RESET, between DONE and a restart of the small CG
+  auto decide = [&](bool count) -> int {
+    int pending = 0;
+    for (int k = 0; k < nrhs; ++k) {
+      CgState& c = cs[k];
+      if (c.mode != MODE_RESET) continue;
+      if (count) resets[k] += 1;
+      const double rn = sqrt(c.rd2);
+      if (!isfinite(c.rd2) || eta_n[k] == 0.0 || rn <= prm->res * eta_n[k] || c.steps >= prm->nmx ||
+          resets[k] > prm->nmx) {
+        c.mode = MODE_DONE;
+        continue;
+      }
+      c.scale = rn / sqrt(ncomp);
+      const double t = prm->res * eta_n[k] / c.scale;
+      c.tol2 = t * t;
+      ++pending;
+    }
+    return pending;
+  };
+
+  auto upload = [&]() -> int {
+    CK(cudaMemcpyAsync(h->cg_dev, cs, sizeof(CgState) * nrhs, cudaMemcpyHostToDevice, s));
+    return OQ_OK;
+  };
+  auto download = [&]() -> int {
+    CK(cudaMemcpyAsync(cs, h->cg_dev, sizeof(CgState) * nrhs, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return OQ_OK;
+  };
+  auto restart = [&]() -> int {
+    RedArgs ra = h->red_args(FIN_RESTART, MODE_RESET);
+    KL(cg_restart(P, (const double*)rd, rv, pv, xs, XP, Vh, (long)h64, (long)hP, (long)hX, nrhs, ra, s));
+    return OQ_OK;
+  };
+
+  // the binary64 reset step for all rhs in MODE_RESET
+  auto reset_step = [&]() -> int {
+    KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
+    HopArgs a = h->hop_args(lat, P_F64);
+    a.nrhs = nrhs;
+    a.cg = h->cg_dev;
+    a.gate = MODE_RESET;
+    a.in_stride = a.in2_stride = a.out_stride = (long)h64;
+    a.half_bytes = (long)h64;
+    // t = A_oo^-1 D_oe x_d ; u = Dhat x_d
+    a.in = xd; a.out = t64; a.p = 1;
+    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P1, 0, EPI_NONE, nrhs), a, s));
+    a.in = t64; a.in2 = xd; a.out = u64v; a.p = 0;
+    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P2, 0, EPI_NONE, nrhs), a, s));
+    // t = ..., r_d = eta - Dhat^dag u, ||r_d||^2
+    a.in = u64v; a.out = t64; a.p = 1;
+    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P1, 1, EPI_NONE, nrhs), a, s));
+    a.in = t64; a.in2 = u64v; a.out = rd; a.p = 0;
+    a.ep_eta = eta64; a.ep_eta_stride = (long)h64;
+    a.red = h->red_args(FIN_RD2, MODE_RESET);
+    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P2, 1, EPI_RESID64, nrhs), a, s));
+    return OQ_OK;
+  };
+
+  // one regular step for all rhs in MODE_RUN
+  HopArgs it = h->hop_args(lat, P);
+  it.nrhs = nrhs;
+  it.cg = h->cg_dev;
+  it.gate = MODE_RUN;
+  it.in_stride = it.in2_stride = it.out_stride = (long)hP;
+  it.half_bytes = (long)hP;
+  auto iteration = [&]() -> int {
+    HopArgs a = it;
+    a.in = pv; a.out = tv; a.p = 1;
+    RK(h->run_hop(h->hop_launch(lat, P, HOP_P1, 0, EPI_NONE, nrhs), a, s));
+    a.in = tv; a.in2 = pv; a.out = uv; a.p = 0;
+    a.red = h->red_args(FIN_ALPHA, MODE_RUN);
+    RK(h->run_hop(h->hop_launch(lat, P, HOP_P2, 0, EPI_NORM, nrhs), a, s));
+    a = it;
+    a.in = uv; a.out = tv; a.p = 1;
+    RK(h->run_hop(h->hop_launch(lat, P, HOP_P1, 1, EPI_NONE, nrhs), a, s));
+    a.in = tv; a.in2 = uv; a.out = nullptr; a.p = 0;
+    a.ep_x = xs; a.ep_x_stride = (long)hX;
+    a.ep_p = pv; a.ep_p_stride = (long)hP;
+    a.ep_r = rv; a.ep_r_stride = (long)hP;
+    a.red = h->red_args(FIN_BETA, MODE_RUN);
+    RK(h->run_hop(h->hop_launch(lat, P, HOP_P2, 1, EPI_CG, nrhs), a, s));
+    KL(cg_update_p(P, pv, rv, Vh, (long)hP, nrhs, h->cg_dev, s));
+    return OQ_OK;
+  };
+
+  int pending = decide(false);
+  RK(upload());
+  if (pending) RK(restart());
+  for (;;) {
+    RK(download());
+    int run = 0, rst = 0;
+    for (int k = 0; k < nrhs; ++k) {
+      run += cs[k].mode == MODE_RUN;
+      rst += cs[k].mode == MODE_RESET;
+    }
+    if (rst) {
+      RK(reset_step());
+      RK(download());
+      pending = decide(true);
+      RK(upload());
+      if (pending) RK(restart());
+      continue;
+    }
+    if (!run) break;
+    for (int k = 0; k < CHUNK; ++k) RK(iteration());
+  }
+
+  // psi = x_d on the even sites, zero on the odd sites
+  CK(cudaMemsetAsync(psi_dev, 0, canon_field * nrhs, s));
+  KL(unpack_spinor(L.g, P_F64, OQ_EVEN, xd, psi_dev, 1.0, nrhs, (long)h64, 2 * Vh * 12, s));
+  CK(cudaStreamSynchronize(s));
+  int ret = OQ_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    st[k].steps = cs[k].steps;
+    st[k].resets = resets[k];
+    st[k].restarts = 0;
+    st[k].true_rel_res = eta_n[k] > 0.0 ? sqrt(cs[k].rd2) / eta_n[k] : 0.0;
+    st[k].converged = (isfinite(cs[k].rd2) && st[k].true_rel_res <= prm->res) ? 1 : 0;
+    if (!isfinite(cs[k].rd2)) ret = OQ_ERR_NONFINITE;
+    else if (!st[k].converged && ret == OQ_OK) ret = OQ_ERR_NOCONV;
+  }
+  return ret;
+#undef CK
+#undef RK
+#undef KL
+}

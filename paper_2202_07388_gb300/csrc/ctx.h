@@ -1,0 +1,260 @@
+// The handle behind the C ABI: per-lattice packed gauge/clover state, a
+// grow-only workspace of named device buffers, the reduction scratch, the
+// per-kernel launch shapes chosen by the tuner, and optional CUDA-event
+// timing of every stencil launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/oq.h"
+#include "oq_internal.h"
+
+namespace oq {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct LatCtx {
+  Geom g;
+  int link_fmt = -1;
+  bool has_gauge = false, has_clover = false;
+  double kappa = 0.0, csw = 0.0;
+  DevBuf u64, u32, a64, a32, i64, i32;
+  std::map<std::string, DevBuf> ws;
+};
+
+// one timed stencil launch
+struct ProfRec {
+  cudaEvent_t e0, e1;
+  int mode, epi, prec;
+  double bytes;
+};
+
+// tuned CTA shape of one stencil variant
+struct TuneKey {
+  int lat, prec, mode, nrhs;
+  bool operator<(const TuneKey& o) const {
+    if (lat != o.lat) return lat < o.lat;
+    if (prec != o.prec) return prec < o.prec;
+    if (mode != o.mode) return mode < o.mode;
+    return nrhs < o.nrhs;
+  }
+};
+
+}  // namespace oq
+
+struct oq_ctx {
+  int device = 0;
+  std::vector<oq::LatCtx> lats;
+  // reduction scratch
+  double* partials = nullptr;
+  size_t partials_n = 0;
+  unsigned* counters = nullptr;
+  size_t counters_n = 0;
+  double* results = nullptr;
+  double* results_host = nullptr;  // pinned
+  size_t results_n = 0;
+  int* status_dev = nullptr;
+  oq::CgState* cg_dev = nullptr;
+  oq::CgState* cg_host = nullptr;  // pinned mirror
+  size_t cg_n = 0;
+  // launch shapes
+  std::map<oq::TuneKey, std::pair<int, int>> tuned;
+  // kernels launched by this handle so far
+  long long launches = 0;
+  // profiling
+  bool prof_on = false;
+  std::vector<oq::ProfRec> prof;
+  std::vector<cudaEvent_t> event_pool;
+
+  int alloc(oq::DevBuf* b, size_t n) {
+    if (b->n >= n && b->p) return OQ_OK;
+    if (b->p) {
+      cudaDeviceSynchronize();
+      cudaFree(b->p);
+      b->p = nullptr;
+      b->n = 0;
+    }
+    if (cudaMalloc(&b->p, n) != cudaSuccess) {
+      cudaGetLastError();
+      return OQ_ERR_NOMEM;
+    }
+    b->n = n;
+    return OQ_OK;
+  }
+
+  int workspace(int lat, const char* name, size_t n, void** out) {
+    oq::DevBuf& b = lats[lat].ws[name];
+    int rc = alloc(&b, n);
+    *out = b.p;
+    return rc;
+  }
+
+  int ensure_scratch() {
+    if (!status_dev && cudaMalloc(&status_dev, 64) != cudaSuccess) return OQ_ERR_NOMEM;
+    return OQ_OK;
+  }
+
+  // room for `slots` reductions of `grid` partials each
+  int ensure_reduce(int slots, long grid) {
+    int rc = ensure_scratch();
+    if (rc) return rc;
+    size_t np = (size_t)slots * (size_t)grid;
+    if (np > partials_n) {
+      cudaDeviceSynchronize();
+      cudaFree(partials);
+      partials = nullptr;
+      if (cudaMalloc(&partials, np * sizeof(double)) != cudaSuccess) return OQ_ERR_NOMEM;
+      partials_n = np;
+    }
+    if ((size_t)slots > counters_n) {
+      cudaDeviceSynchronize();
+      cudaFree(counters);
+      cudaFree(results);
+      cudaFreeHost(results_host);
+      counters = nullptr;
+      results = nullptr;
+      results_host = nullptr;
+      size_t n = (size_t)slots < 64 ? 64 : (size_t)slots;
+      if (cudaMalloc(&counters, n * sizeof(unsigned)) != cudaSuccess) return OQ_ERR_NOMEM;
+      if (cudaMemset(counters, 0, n * sizeof(unsigned)) != cudaSuccess) return OQ_ERR_CUDA;
+      if (cudaMalloc(&results, 2 * n * sizeof(double)) != cudaSuccess) return OQ_ERR_NOMEM;
+      if (cudaMallocHost(&results_host, 2 * n * sizeof(double)) != cudaSuccess) return OQ_ERR_NOMEM;
+      counters_n = n;
+      results_n = 2 * n;
+    }
+    return OQ_OK;
+  }
+
+  int ensure_cg(int nrhs) {
+    if ((size_t)nrhs <= cg_n) return OQ_OK;
+    cudaDeviceSynchronize();
+    cudaFree(cg_dev);
+    cudaFreeHost(cg_host);
+    cg_dev = nullptr;
+    cg_host = nullptr;
+    if (cudaMalloc(&cg_dev, nrhs * sizeof(oq::CgState)) != cudaSuccess) return OQ_ERR_NOMEM;
+    if (cudaMallocHost(&cg_host, nrhs * sizeof(oq::CgState)) != cudaSuccess) return OQ_ERR_NOMEM;
+    cg_n = nrhs;
+    return OQ_OK;
+  }
+
+  oq::RedArgs red_args(int fin, int gate) {
+    oq::RedArgs r;
+    r.partials = partials;
+    r.counters = counters;
+    r.result = results;
+    r.cg = cg_dev;
+    r.fin = fin;
+    r.gate = gate;
+    return r;
+  }
+
+  oq::HopArgs hop_args(int lat, int prec) {
+    oq::LatCtx& L = lats[lat];
+    oq::HopArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = L.g;
+    const bool f64 = prec == oq::P_F64;
+    a.links = f64 ? L.u64.p : L.u32.p;
+    a.clov = f64 ? L.a64.p : L.a32.p;
+    a.cinv = f64 ? L.i64.p : L.i32.p;
+    a.nrhs = 1;
+    return a;
+  }
+
+  oq::HopLaunch hop_launch(int lat, int prec, int mode, int dagger, int epi, int nrhs) {
+    oq::HopLaunch l;
+    l.prec = prec;
+    l.link_fmt = lats[lat].link_fmt;
+    l.mode = mode;
+    l.dagger = dagger;
+    l.epi = epi;
+    auto it = tuned.find(oq::TuneKey{lat, prec, mode, nrhs});
+    if (it != tuned.end()) {
+      l.bx = it->second.first;
+      l.by = it->second.second;
+    } else {
+      l.bx = 128;
+      l.by = 1;
+    }
+    if (l.by > nrhs) l.by = nrhs;
+    return l;
+  }
+
+  // algorithmic bytes of one stencil launch (each operand counted once)
+  double hop_bytes(const oq::HopLaunch& l, const oq::HopArgs& a) {
+    const double sp = oq::prec_bytes(l.prec);
+    const double su = l.prec == oq::P_F64 ? 8.0 : 4.0;
+    const double ru = (l.prec != oq::P_F64 && l.link_fmt == oq::LINK_12) ? 12.0 : 18.0;
+    const double sites = (double)a.g.Vh * (l.mode == oq::HOP_DW ? 2.0 : 1.0);
+    double spin = 0.0;
+    double links = 0.0;
+    if (l.mode == oq::HOP_DW) {
+      spin = 48.0 * sp;          // in + out
+      links = 4.0 * ru * su;     // every link once for the full lattice
+    } else {
+      spin = (l.mode == oq::HOP_P1 ? 48.0 : 72.0) * sp;
+      links = 8.0 * ru * su;     // all links once per half-lattice pass
+    }
+    if (l.epi == oq::EPI_CG) spin += (24.0 + 24.0 + 48.0 - 24.0) * sp + 48.0 * (l.prec == oq::P_F64 ? 8.0 : 4.0);
+    if (l.epi == oq::EPI_RESID64) spin += 24.0 * sp;
+    const double clov = 72.0 * su;
+    return sites * (spin * a.nrhs + links + clov);
+  }
+
+  int run_hop(const oq::HopLaunch& l, const oq::HopArgs& a, cudaStream_t s) {
+    oq::ProfRec rec;
+    if (prof_on) {
+      if (event_pool.size() < 2) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          if (cudaEventCreate(&e) != cudaSuccess) return OQ_ERR_CUDA;
+          event_pool.push_back(e);
+        }
+      }
+      rec.e1 = event_pool.back();
+      event_pool.pop_back();
+      rec.e0 = event_pool.back();
+      event_pool.pop_back();
+      rec.mode = l.mode;
+      rec.epi = l.epi;
+      rec.prec = l.prec;
+      rec.bytes = hop_bytes(l, a);
+      cudaEventRecord(rec.e0, s);
+    }
+    cudaError_t e = oq::launch_hop(l, a, s);
+    launches += 1;
+    if (prof_on) {
+      cudaEventRecord(rec.e1, s);
+      prof.push_back(rec);
+    }
+    return e == cudaSuccess ? OQ_OK : OQ_ERR_CUDA;
+  }
+
+  void release() {
+    for (auto& L : lats) {
+      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32};
+      for (auto* b : bs) cudaFree(b->p);
+      for (auto& kv : L.ws) cudaFree(kv.second.p);
+    }
+    cudaFree(partials);
+    cudaFree(counters);
+    cudaFree(results);
+    cudaFreeHost(results_host);
+    cudaFree(status_dev);
+    cudaFree(cg_dev);
+    cudaFreeHost(cg_host);
+    for (auto& r : prof) {
+      cudaEventDestroy(r.e0);
+      cudaEventDestroy(r.e1);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
+  }
+};

@@ -1,0 +1,197 @@
+// The Wilson-clover stencil on even-odd ordered half lattices.
+//
+// One thread computes one output site of parity p for one right-hand side:
+//
+//   H psi(x) = sum_mu [ U_mu(x) (1 - g_mu) psi(x+mu) + U_mu(x-mu)^dag (1 + g_mu) psi(x-mu) ]
+//
+// (projectors swapped for the adjoint, since g5 (1 -/+ g_mu) g5 = (1 +/- g_mu)),
+// with the two-component spin projection so that only half spinors are
+// transported by the links, and the time-boundary factor on hops that cross
+// x0 = T-1 <-> 0.  The mode picks what is done with H psi:
+//
+//   HOP_DW : out = A in2 - 1/2 H in                  (one parity of D psi)
+//   HOP_P1 : out = A^{-1} (-1/2 H in)                (D_oo^{-1} D_oe psi_e)
+//   HOP_P2 : out = A in2 + 1/2 H in                  (D_ee psi_e - D_eo t_o)
+//
+// and the epilogue fuses the vector work of the solvers into the store
+// (norm of the output, the CG update of x and r, or the binary64 residual
+// eta - out of a reset step) with a deterministic binary64 grid reduction.
+#pragma once
+#include "reduce.cuh"
+
+namespace oq {
+
+template <int P, int FMT, int MU, bool DAG>
+__device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p, long i, const int x[4],
+                                        Spinor<typename PrecTraits<P>::R>& acc,
+                                        typename PrecTraits<P>::R w) {
+  typedef typename PrecTraits<P>::R R;
+  constexpr int SF = DAG ? +1 : -1;  // projector sign of the forward hop
+  bool cr;
+  // forward: U_mu(x) (1 -/+ g) psi(x + mu)
+  {
+    long j = eo_neighbour(a.g, x, MU, +1, &cr);
+    Spinor<R> nb;
+    load_spinor<P>(in, a.g.Vh, j, nb);
+    HalfSpinor<R> h, t;
+    project<MU, SF>(nb, h);
+    Su3<R> u;
+    load_link<R, FMT>(a.links, a.g.Vh, p, MU, i, u);
+    su3_mul(u, h, t);
+    accum_reconstruct<MU, SF>(acc, t, cr ? w * (R)a.g.bc_t : w);
+  }
+  // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
+  {
+    long j = eo_neighbour(a.g, x, MU, -1, &cr);
+    Spinor<R> nb;
+    load_spinor<P>(in, a.g.Vh, j, nb);
+    HalfSpinor<R> h, t;
+    project<MU, -SF>(nb, h);
+    Su3<R> u;
+    load_link<R, FMT>(a.links, a.g.Vh, 1 - p, MU, j, u);
+    su3_dag_mul(u, h, t);
+    accum_reconstruct<MU, -SF>(acc, t, cr ? w * (R)a.g.bc_t : w);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ double site_norm2(const Spinor<R>& s) {
+  R acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc += s.c[k][c].re * s.c[k][c].re + s.c[k][c].im * s.c[k][c].im;
+  return (double)acc;
+}
+
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+  typedef typename PrecTraits<P>::R R;
+  extern __shared__ double red_smem[];
+  // HOP_DW: the two parities of one site range run in neighbouring CTAs, so
+  // that a link read by the forward hop of one parity is still in L2 when
+  // the backward hop of the other parity needs it
+  const long blk = (MODE == HOP_DW) ? (long)(blockIdx.x >> 1) : (long)blockIdx.x;
+  const long i = blk * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
+  const int p = (MODE == HOP_DW) ? (int)(blockIdx.x & 1) : a.p;
+  bool live = (i < a.g.Vh) && (rhs < a.nrhs);
+  if (live && a.cg) live = (a.cg[rhs].mode == a.gate);
+  double red = 0.0;
+  if (live) {
+    int x[4];
+    eo_coords(a.g, p, i, x);
+    const long par_in = (MODE == HOP_DW) ? (long)(1 - p) * a.half_bytes : 0;
+    const long par_out = (MODE == HOP_DW) ? (long)p * a.half_bytes : 0;
+    const char* in = (const char*)a.in + rhs * a.in_stride + par_in;
+    Spinor<R> acc;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc.c[s][c] = cx<R>{0, 0};
+    const R w = (MODE == HOP_P2) ? (R)0.5 : (R)-0.5;
+    hop_dir<P, FMT, 0, DAG>(a, in, p, i, x, acc, w);
+    hop_dir<P, FMT, 1, DAG>(a, in, p, i, x, acc, w);
+    hop_dir<P, FMT, 2, DAG>(a, in, p, i, x, acc, w);
+    hop_dir<P, FMT, 3, DAG>(a, in, p, i, x, acc, w);
+
+    Spinor<R> res;
+    if constexpr (MODE == HOP_P1) {
+      clover_apply<R>(a.cinv, a.g.Vh, p, i, acc, res);
+    } else {
+      const char* in2 = (const char*)a.in2 + rhs * a.in2_stride + par_out;
+      Spinor<R> loc, al;
+      load_spinor<P>(in2, a.g.Vh, i, loc);
+      clover_apply<R>(a.clov, a.g.Vh, p, i, loc, al);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res.c[s][c] = al.c[s][c] + acc.c[s][c];
+    }
+
+    if constexpr (EPI == EPI_NONE || EPI == EPI_NORM) {
+      store_spinor<P>((char*)a.out + rhs * a.out_stride + par_out, a.g.Vh, i, res);
+      if constexpr (EPI == EPI_NORM) red = site_norm2(res);
+    } else if constexpr (EPI == EPI_CG) {
+      // q = res; x += alpha p; r -= alpha q  (x in F64 for F64 solves, else F32)
+      constexpr int XP = (P == P_F64) ? P_F64 : P_F32;
+      typedef typename PrecTraits<XP>::R RX;
+      const CgState& st = a.cg[rhs];
+      const R al = (R)st.alpha;
+      Spinor<R> pv, rv;
+      Spinor<RX> xv;
+      load_spinor<P>((const char*)a.ep_p + rhs * a.ep_p_stride, a.g.Vh, i, pv);
+      load_spinor<P>((const char*)a.ep_r + rhs * a.ep_r_stride, a.g.Vh, i, rv);
+      load_spinor<XP>((const char*)a.ep_x + rhs * a.ep_x_stride, a.g.Vh, i, xv);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          xv.c[s][c].re = fma((RX)al, (RX)pv.c[s][c].re, xv.c[s][c].re);
+          xv.c[s][c].im = fma((RX)al, (RX)pv.c[s][c].im, xv.c[s][c].im);
+          rv.c[s][c].re = fma(-al, res.c[s][c].re, rv.c[s][c].re);
+          rv.c[s][c].im = fma(-al, res.c[s][c].im, rv.c[s][c].im);
+        }
+      // the norm of what is stored (rounded to the storage type)
+      round_trip<P>(rv);
+      store_spinor<XP>((char*)a.ep_x + rhs * a.ep_x_stride, a.g.Vh, i, xv);
+      store_spinor<P>((char*)a.ep_r + rhs * a.ep_r_stride, a.g.Vh, i, rv);
+      red = site_norm2(rv);
+    } else if constexpr (EPI == EPI_RESID64) {
+      Spinor<R> e;
+      load_spinor<P>((const char*)a.ep_eta + rhs * a.ep_eta_stride, a.g.Vh, i, e);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res.c[s][c] = e.c[s][c] - res.c[s][c];
+      store_spinor<P>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, res);
+      double acc2 = 0.0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          acc2 += (double)res.c[s][c].re * res.c[s][c].re + (double)res.c[s][c].im * res.c[s][c].im;
+      red = acc2;
+    }
+  }
+  if constexpr (EPI != EPI_NONE) {
+    grid_reduce(red, a.red, rhs, a.nrhs, red_smem);
+  }
+}
+
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+static cudaError_t launch_one(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  dim3 block(L.bx, L.by, 1);
+  const unsigned nb = (unsigned)((a.g.Vh + L.bx - 1) / L.bx);
+  dim3 grid(MODE == HOP_DW ? 2u * nb : nb, (unsigned)((a.nrhs + L.by - 1) / L.by), 1u);
+  size_t smem = (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32) * L.by;
+  hop_kernel<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int FMT, bool DAG>
+static cudaError_t dispatch_mode_epi(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  switch (L.mode) {
+    case HOP_DW:
+      if (L.epi == EPI_NONE) return launch_one<P, FMT, HOP_DW, DAG, EPI_NONE>(L, a, s);
+      break;
+    case HOP_P1:
+      if (L.epi == EPI_NONE) return launch_one<P, FMT, HOP_P1, DAG, EPI_NONE>(L, a, s);
+      break;
+    case HOP_P2:
+      if (L.epi == EPI_NONE) return launch_one<P, FMT, HOP_P2, DAG, EPI_NONE>(L, a, s);
+      if (L.epi == EPI_NORM) return launch_one<P, FMT, HOP_P2, DAG, EPI_NORM>(L, a, s);
+      if (L.epi == EPI_CG) return launch_one<P, FMT, HOP_P2, DAG, EPI_CG>(L, a, s);
+      if constexpr (P == P_F64)
+        if (L.epi == EPI_RESID64) return launch_one<P, FMT, HOP_P2, DAG, EPI_RESID64>(L, a, s);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int FMT>
+static cudaError_t dispatch_dag(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  return L.dagger ? dispatch_mode_epi<P, FMT, true>(L, a, s) : dispatch_mode_epi<P, FMT, false>(L, a, s);
+}
+
+}  // namespace oq

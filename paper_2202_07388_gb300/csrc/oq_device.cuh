@@ -1,0 +1,413 @@
+// Device-side building blocks: complex numbers, lattice geometry on the
+// even-odd ordered half lattices, and the packed (chunk-major SoA) storage
+// of spinors, links and clover blocks in every supported precision.
+//
+// Packed layouts (Vh = V/2 sites per parity; eo index i = lex(x) >> 1):
+//   spinor  : 24 reals/site, stored as chunks of 16 bytes, chunk-major:
+//             chunk c of site i at base[c*Vh + i].  Real index r of the site
+//             vector = 2*(3*spin + colour) + (0 re | 1 im).
+//             F64: 12 chunks (double2), F32: 6 chunks (float4),
+//             BF16/F16: 3 chunks (8 halves each).
+//   links   : U_mu(x) at [parity(x)][mu][chunk][Vh];
+//             18-real: 9 chunks (F64 double2 / F32 float2), element a*3+b;
+//             12-real (F32, SU(3) only): 3 float4 chunks holding rows 0 and 1,
+//             row 2 = conj(row0 x row1).
+//   clover  : per site two Hermitian 6x6 blocks (chirality +, -), each as
+//             6 real diagonal entries then the 15 upper off-diagonal complex
+//             entries in row-major order (36 reals/block, 72 reals/site);
+//             F64: 36 double2 chunks, F32: 18 float4 chunks, [parity][chunk][Vh].
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace oq {
+
+enum Prec : int { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3 };
+enum LinkFmt : int { LINK_18 = 0, LINK_12 = 1 };
+
+// ---------------------------------------------------------------------------
+// complex
+// ---------------------------------------------------------------------------
+template <typename R>
+struct cx {
+  R re, im;
+};
+template <typename R>
+__device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> times_i(cx<R> a) { return {-a.im, a.re}; }
+template <typename R>
+__device__ __forceinline__ cx<R> times_mi(cx<R> a) { return {a.im, -a.re}; }
+// acc += a * b
+template <typename R>
+__device__ __forceinline__ void cfma(cx<R>& acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+// acc += conj(a) * b
+template <typename R>
+__device__ __forceinline__ void cfmac(cx<R>& acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+
+template <typename R>
+struct Spinor {
+  cx<R> c[4][3];  // [spin][colour]
+};
+template <typename R>
+struct HalfSpinor {
+  cx<R> c[2][3];
+};
+template <typename R>
+struct Su3 {
+  cx<R> m[3][3];
+};
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+struct Geom {
+  int L[4];   // L[0] = T (slowest) ... L[3] (fastest); all even
+  int Lh3;    // L[3] / 2
+  long Vh;    // V / 2
+  float bc_t; // fermion factor for hops across the time boundary (-1 antiperiodic)
+};
+
+// coordinates of eo site i of parity p
+__device__ __forceinline__ void eo_coords(const Geom& g, int p, long i, int x[4]) {
+  long t = i;
+  int k = (int)(t % g.Lh3);
+  t /= g.Lh3;
+  x[2] = (int)(t % g.L[2]);
+  t /= g.L[2];
+  x[1] = (int)(t % g.L[1]);
+  x[0] = (int)(t / g.L[1]);
+  x[3] = 2 * k + ((p + x[0] + x[1] + x[2]) & 1);
+}
+
+__device__ __forceinline__ long eo_index(const Geom& g, const int x[4]) {
+  long lex = (((long)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
+  return lex >> 1;
+}
+
+// eo index of x + d*mu (periodic wrap); *crossed = 1 if the hop crosses the
+// time boundary
+__device__ __forceinline__ long eo_neighbour(const Geom& g, const int x[4], int mu, int d, bool* crossed) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  int v = y[mu] + d;
+  bool c = false;
+  if (v == g.L[mu]) { v = 0; c = true; }
+  if (v < 0) { v = g.L[mu] - 1; c = true; }
+  y[mu] = v;
+  *crossed = c && (mu == 0);
+  return eo_index(g, y);
+}
+
+// ---------------------------------------------------------------------------
+// storage types
+// ---------------------------------------------------------------------------
+template <int P> struct PrecTraits;
+template <> struct PrecTraits<P_F64> { typedef double R; typedef double2 Chunk; static const int nchunk = 12; static const int bytes = 8; };
+template <> struct PrecTraits<P_F32> { typedef float R;  typedef float4 Chunk;  static const int nchunk = 6;  static const int bytes = 4; };
+template <> struct PrecTraits<P_BF16> { typedef float R; typedef uint4 Chunk;   static const int nchunk = 3;  static const int bytes = 2; };
+template <> struct PrecTraits<P_F16> { typedef float R;  typedef uint4 Chunk;   static const int nchunk = 3;  static const int bytes = 2; };
+
+template <typename T>
+__device__ __forceinline__ T ldg_nc(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t w) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+  return __bfloat1622float2(h);
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_f16x2(uint32_t w) {
+  __half2 h = *reinterpret_cast<__half2*>(&w);
+  return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Load the 12 complex components of site i from a packed spinor field.
+template <int P>
+__device__ __forceinline__ void load_spinor(const void* base, long Vh, long i,
+                                            Spinor<typename PrecTraits<P>::R>& s) {
+  typedef typename PrecTraits<P>::R R;
+  cx<R>* f = &s.c[0][0];
+  if constexpr (P == P_F64) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double2 v = ldg_nc(b + c * Vh + i);
+      f[c] = cx<R>{v.x, v.y};
+    }
+  } else if constexpr (P == P_F32) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float4 v = ldg_nc(b + c * Vh + i);
+      f[2 * c] = cx<R>{v.x, v.y};
+      f[2 * c + 1] = cx<R>{v.z, v.w};
+    }
+  } else {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint4 v = ldg_nc(b + c * Vh + i);
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 z = (P == P_BF16) ? unpack_bf16x2(w[k]) : unpack_f16x2(w[k]);
+        f[4 * c + k] = cx<R>{z.x, z.y};
+      }
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void store_spinor(void* base, long Vh, long i,
+                                             const Spinor<typename PrecTraits<P>::R>& s) {
+  typedef typename PrecTraits<P>::R R;
+  const cx<R>* f = &s.c[0][0];
+  if constexpr (P == P_F64) {
+    double2* b = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) b[c * Vh + i] = make_double2(f[c].re, f[c].im);
+  } else if constexpr (P == P_F32) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      b[c * Vh + i] = make_float4(f[2 * c].re, f[2 * c].im, f[2 * c + 1].re, f[2 * c + 1].im);
+  } else {
+    uint4* b = reinterpret_cast<uint4*>(base);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        w[k] = (P == P_BF16) ? pack_bf16x2(f[4 * c + k].re, f[4 * c + k].im)
+                             : pack_f16x2(f[4 * c + k].re, f[4 * c + k].im);
+      b[c * Vh + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// Round a binary32 spinor held in registers to the storage type P and back,
+// i.e. the value a store_spinor<P> / load_spinor<P> pair would give, without
+// re-reading memory written by the same kernel.
+template <int P, typename R>
+__device__ __forceinline__ void round_trip(Spinor<R>& s) {
+  if constexpr (P == P_BF16) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 z = unpack_bf16x2(pack_bf16x2(s.c[a][c].re, s.c[a][c].im));
+        s.c[a][c] = cx<R>{z.x, z.y};
+      }
+  } else if constexpr (P == P_F16) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 z = unpack_f16x2(pack_f16x2(s.c[a][c].re, s.c[a][c].im));
+        s.c[a][c] = cx<R>{z.x, z.y};
+      }
+  }
+}
+
+// Load link U_mu at eo site i of parity p.  R = float for F32 storage,
+// double for F64 storage.
+template <typename R, int FMT>
+__device__ __forceinline__ void load_link(const void* base, long Vh, int p, int mu, long i, Su3<R>& u) {
+  if constexpr (sizeof(R) == 8) {
+    const double2* b = reinterpret_cast<const double2*>(base) + ((long)(p * 4 + mu) * 9) * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = ldg_nc(b + k * Vh + i);
+      u.m[k / 3][k % 3] = cx<R>{v.x, v.y};
+    }
+  } else if constexpr (FMT == LINK_18) {
+    const float2* b = reinterpret_cast<const float2*>(base) + ((long)(p * 4 + mu) * 9) * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float2 v = ldg_nc(b + k * Vh + i);
+      u.m[k / 3][k % 3] = cx<R>{v.x, v.y};
+    }
+  } else {
+    const float4* b = reinterpret_cast<const float4*>(base) + ((long)(p * 4 + mu) * 3) * Vh;
+    float4 a0 = ldg_nc(b + i), a1 = ldg_nc(b + Vh + i), a2 = ldg_nc(b + 2 * Vh + i);
+    u.m[0][0] = {a0.x, a0.y};
+    u.m[0][1] = {a0.z, a0.w};
+    u.m[0][2] = {a1.x, a1.y};
+    u.m[1][0] = {a1.z, a1.w};
+    u.m[1][1] = {a2.x, a2.y};
+    u.m[1][2] = {a2.z, a2.w};
+    // row 2 = conj(row0 x row1)
+    u.m[2][0] = conj(u.m[0][1] * u.m[1][2] - u.m[0][2] * u.m[1][1]);
+    u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
+    u.m[2][2] = conj(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
+  }
+}
+
+// y = U h  (colour matvec on both spin components of a half spinor)
+template <typename R>
+__device__ __forceinline__ void su3_mul(const Su3<R>& u, const HalfSpinor<R>& h, HalfSpinor<R>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> acc = u.m[a][0] * h.c[s][0];
+      cfma(acc, u.m[a][1], h.c[s][1]);
+      cfma(acc, u.m[a][2], h.c[s][2]);
+      y.c[s][a] = acc;
+    }
+}
+
+// y = U^dag h
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul(const Su3<R>& u, const HalfSpinor<R>& h, HalfSpinor<R>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> acc = cmulc(u.m[0][a], h.c[s][0]);
+      cfmac(acc, u.m[1][a], h.c[s][1]);
+      cfmac(acc, u.m[2][a], h.c[s][2]);
+      y.c[s][a] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// clover blocks
+// ---------------------------------------------------------------------------
+// Multiply the two Hermitian 6x6 blocks of site i (parity p) onto psi:
+// out = A psi.  Block b acts on spins 2b, 2b+1 (index 3*spin_local+colour).
+template <typename R>
+__device__ __forceinline__ void clover_apply(const void* base, long Vh, int p, long i,
+                                             const Spinor<R>& in, Spinor<R>& out) {
+  const cx<R>* v = &in.c[0][0];
+  cx<R>* o = &out.c[0][0];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    R d[6];
+    cx<R> off[15];
+    if constexpr (sizeof(R) == 8) {
+      const double2* q = reinterpret_cast<const double2*>(base) + (long)p * 36 * Vh;
+      // block b occupies chunks 18b .. 18b+17: 3 chunks of diagonal, 15 off
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double2 w = ldg_nc(q + (18 * b + k) * Vh + i);
+        d[2 * k] = w.x;
+        d[2 * k + 1] = w.y;
+      }
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        double2 w = ldg_nc(q + (18 * b + 3 + k) * Vh + i);
+        off[k] = cx<R>{w.x, w.y};
+      }
+    } else {
+      const float4* q = reinterpret_cast<const float4*>(base) + (long)p * 18 * Vh;
+      float r[36];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        float4 w = ldg_nc(q + (9 * b + k) * Vh + i);
+        r[4 * k] = w.x;
+        r[4 * k + 1] = w.y;
+        r[4 * k + 2] = w.z;
+        r[4 * k + 3] = w.w;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) d[k] = r[k];
+#pragma unroll
+      for (int k = 0; k < 15; ++k) off[k] = cx<R>{r[6 + 2 * k], r[7 + 2 * k]};
+    }
+    const cx<R>* x = v + 6 * b;
+    cx<R>* y = o + 6 * b;
+#pragma unroll
+    for (int r0 = 0; r0 < 6; ++r0) y[r0] = d[r0] * x[r0];
+    int k = 0;
+#pragma unroll
+    for (int r0 = 0; r0 < 6; ++r0)
+#pragma unroll
+      for (int c0 = r0 + 1; c0 < 6; ++c0) {
+        cfma(y[r0], off[k], x[c0]);
+        cfmac(y[c0], off[k], x[r0]);
+        ++k;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spin projection (chiral basis) for the hop along direction mu.
+// S = -1: (1 - g_mu) psi, S = +1: (1 + g_mu) psi.  The projected spinor is
+// (h0, h1, l0, l1) with the half spinor h and lower components l fixed
+// linear functions of h; only h is transported.
+// ---------------------------------------------------------------------------
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const Spinor<R>& p, HalfSpinor<R>& h) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx<R> p0 = p.c[0][a], p1 = p.c[1][a], p2 = p.c[2][a], p3 = p.c[3][a];
+    if constexpr (MU == 0) {
+      if constexpr (S < 0) { h.c[0][a] = p0 + p2; h.c[1][a] = p1 + p3; }
+      else                 { h.c[0][a] = p0 - p2; h.c[1][a] = p1 - p3; }
+    } else if constexpr (MU == 1) {
+      if constexpr (S < 0) { h.c[0][a] = p0 + times_i(p3); h.c[1][a] = p1 + times_i(p2); }
+      else                 { h.c[0][a] = p0 - times_i(p3); h.c[1][a] = p1 - times_i(p2); }
+    } else if constexpr (MU == 2) {
+      if constexpr (S < 0) { h.c[0][a] = p0 + p3; h.c[1][a] = p1 - p2; }
+      else                 { h.c[0][a] = p0 - p3; h.c[1][a] = p1 + p2; }
+    } else {
+      if constexpr (S < 0) { h.c[0][a] = p0 + times_i(p2); h.c[1][a] = p1 - times_i(p3); }
+      else                 { h.c[0][a] = p0 - times_i(p2); h.c[1][a] = p1 + times_i(p3); }
+    }
+  }
+}
+
+// acc += w * (1 -/+ g_mu)-reconstruction of the transported half spinor h
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accum_reconstruct(Spinor<R>& acc, const HalfSpinor<R>& h, R w) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx<R> h0 = w * h.c[0][a], h1 = w * h.c[1][a];
+    acc.c[0][a] = acc.c[0][a] + h0;
+    acc.c[1][a] = acc.c[1][a] + h1;
+    cx<R> l0, l1;
+    if constexpr (MU == 0) { l0 = h0; l1 = h1; }
+    else if constexpr (MU == 1) { l0 = times_mi(h1); l1 = times_mi(h0); }
+    else if constexpr (MU == 2) { l0 = -h1; l1 = h0; }
+    else { l0 = times_mi(h0); l1 = times_i(h1); }
+    if constexpr (S > 0) { l0 = -l0; l1 = -l1; }
+    acc.c[2][a] = acc.c[2][a] + l0;
+    acc.c[3][a] = acc.c[3][a] + l1;
+  }
+}
+
+}  // namespace oq

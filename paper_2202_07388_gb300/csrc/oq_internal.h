@@ -1,0 +1,89 @@
+// Host/device shared declarations of the library internals (not part of the
+// public C ABI in include/oq.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "oq_device.cuh"
+
+namespace oq {
+
+// Per right-hand-side state of the CGNE solver, resident in device memory so
+// that the regular steps never wait for the host.
+struct CgState {
+  double rr;        // ||r_s||^2 of the small-type residual
+  double rr_start;  // ||r_s||^2 at the last (re)start
+  double pAp;       // ||Dhat p||^2
+  double alpha, beta;
+  double tol2;      // stop threshold on rr (scaled units)
+  double delta2;    // reset threshold factor delta^2
+  double scale;     // s: the small-type system is A x_s = r_d / s
+  double rd2;       // ||r_d||^2 of the binary64 residual after a reset
+  int mode;         // MODE_RUN, MODE_RESET, MODE_DONE
+  int reason;       // why regular steps stopped
+  int steps;        // regular steps so far
+  int nmx;
+};
+enum { MODE_RUN = 0, MODE_RESET = 1, MODE_DONE = 2 };
+enum { WHY_NONE = 0, WHY_DELTA = 1, WHY_TOL = 2, WHY_NMX = 3, WHY_NONFINITE = 4, WHY_BREAKDOWN = 5 };
+
+// reduction finishers run by the last CTA of a grid reduction
+enum Fin : int { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_RESTART = 3, FIN_RD2 = 4 };
+
+struct RedArgs {
+  double* partials;    // [nrhs][gridDim.x]
+  unsigned* counters;  // [nrhs]
+  double* result;      // [nrhs] (FIN_STORE)
+  CgState* cg;         // [nrhs]
+  int fin;
+  int gate;            // CG finishers act only on rhs with cg[rhs].mode == gate
+};
+
+enum HopMode : int { HOP_DW = 0, HOP_P1 = 1, HOP_P2 = 2 };
+enum HopEpi : int { EPI_NONE = 0, EPI_NORM = 1, EPI_CG = 2, EPI_RESID64 = 3 };
+
+struct HopArgs {
+  Geom g;
+  const void* in;      // neighbour field (parity 1-p), packed
+  const void* in2;     // site-local field (parity p) for the clover term
+  void* out;           // output field (parity p)
+  const void* links;   // packed links
+  const void* clov;    // packed A
+  const void* cinv;    // packed A^{-1}
+  long in_stride;      // bytes between right-hand sides
+  long in2_stride;
+  long out_stride;
+  long half_bytes;     // bytes of one packed half field (HOP_DW: parity offset)
+  int p;               // output parity (ignored for HOP_DW: blockIdx.z)
+  int nrhs;
+  int gate;            // run only right-hand sides with cg[rhs].mode == gate (cg != null)
+  // epilogue operands (EPI_CG: x += alpha p, r -= alpha q; EPI_RESID64: r = eta - out)
+  void* ep_x;
+  const void* ep_p;
+  void* ep_r;
+  const void* ep_eta;
+  long ep_x_stride, ep_p_stride, ep_r_stride, ep_eta_stride;
+  RedArgs red;
+  CgState* cg;
+};
+
+struct HopLaunch {
+  int prec;      // Prec of in/in2/out
+  int link_fmt;  // LINK_18 / LINK_12 (F32/BF16/F16 only)
+  int mode;      // HopMode
+  int dagger;
+  int epi;       // HopEpi
+  int bx, by;    // CTA shape: bx sites x by right-hand sides
+};
+
+cudaError_t launch_hop(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_f64(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_f32(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+
+__host__ __device__ inline int prec_bytes(int prec) { return prec == P_F64 ? 8 : prec == P_F32 ? 4 : 2; }
+__host__ __device__ inline long spinor_half_bytes(long Vh, int prec) { return 24L * Vh * prec_bytes(prec); }
+
+}  // namespace oq

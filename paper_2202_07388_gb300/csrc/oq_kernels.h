@@ -1,0 +1,32 @@
+// Host-side launchers of the kernels, shared between translation units.
+#pragma once
+#include "oq_internal.h"
+
+namespace oq {
+
+cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, cudaStream_t s);
+cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
+                        int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s);
+cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
+                          int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s);
+cudaError_t build_clover(const Geom& g, const double* u64, double kappa, double csw, double* a64, float* a32,
+                         double* i64, float* i32, int* status_dev, cudaStream_t s);
+
+// binary64 reductions over packed half fields of Vh sites per rhs
+cudaError_t reduce_norm2(int prec, const void* x, long Vh, long stride_bytes, int nrhs, const RedArgs& ra,
+                         cudaStream_t s);
+cudaError_t reduce_dot(int prec, const void* x, const void* y, long Vh, long stride_bytes, int nrhs,
+                       const RedArgs& ra, cudaStream_t s);
+int reduce_grid(long nsites);
+
+// CGNE vector kernels (gated on CgState::mode)
+cudaError_t cg_update_p(int prec, void* p, const void* r, long Vh, long stride, int nrhs, const CgState* cg,
+                        cudaStream_t s);
+cudaError_t cg_accumulate_x(int xprec, double* xd, const void* xs, long Vh, long stride_xd, long stride_xs,
+                            int nrhs, const CgState* cg, cudaStream_t s);
+cudaError_t cg_restart(int prec, const double* rd, void* rs, void* p, void* xs, int xprec, long Vh,
+                       long stride_d, long stride_s, long stride_xs, int nrhs, const RedArgs& ra, cudaStream_t s);
+cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride, int nrhs, const CgState* cg,
+                          int gate, cudaStream_t s);
+
+}  // namespace oq

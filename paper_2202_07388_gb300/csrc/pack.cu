@@ -1,0 +1,144 @@
+// Layout conversion kernels: canonical binary64 links and spinors (site
+// lexicographic, time slowest) to the packed even-odd chunk-major device
+// layouts, with rounding to the storage precision (round to nearest even)
+// and an optional per-field scale for the 16-bit formats.
+#include "oq_internal.h"
+#include "oq_kernels.h"
+
+namespace oq {
+
+__device__ __forceinline__ long lex_of(const Geom& g, const int x[4]) {
+  return (((long)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
+}
+
+// one thread per (eo site, parity, mu)
+__global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, double2* __restrict__ u64,
+                                  void* __restrict__ u32, int fmt) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  const int mu = blockIdx.z;
+  if (i >= g.Vh) return;
+  int x[4];
+  eo_coords(g, p, i, x);
+  const double2* src = canon + (lex_of(g, x) * 4 + mu) * 9;
+  double2 m[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = src[k];
+  double2* d64 = u64 + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d64[k * g.Vh + i] = m[k];
+  if (fmt == LINK_18) {
+    float2* d = reinterpret_cast<float2*>(u32) + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k * g.Vh + i] = make_float2((float)m[k].x, (float)m[k].y);
+  } else {
+    float4* d = reinterpret_cast<float4*>(u32) + ((long)(p * 4 + mu) * 3) * g.Vh;
+    d[i] = make_float4((float)m[0].x, (float)m[0].y, (float)m[1].x, (float)m[1].y);
+    d[g.Vh + i] = make_float4((float)m[2].x, (float)m[2].y, (float)m[3].x, (float)m[3].y);
+    d[2 * g.Vh + i] = make_float4((float)m[4].x, (float)m[4].y, (float)m[5].x, (float)m[5].y);
+  }
+}
+
+cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, cudaStream_t s) {
+  dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), 2, 4);
+  pack_links_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<const double2*>(canon),
+                                           reinterpret_cast<double2*>(u64), u32, fmt);
+  return cudaGetLastError();
+}
+
+// one thread per (eo site, parity, rhs).  blockIdx.y = parity index within
+// the subset, blockIdx.z = rhs.
+template <int P>
+__global__ void pack_spinor_kernel(Geom g, const double2* __restrict__ canon, char* __restrict__ out,
+                                   int subset, long canon_stride, long out_stride, double scale) {
+  typedef typename PrecTraits<P>::R R;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.Vh) return;
+  const int p = (subset == 2) ? (int)blockIdx.y : subset;
+  const int rhs = blockIdx.z;
+  int x[4];
+  eo_coords(g, p, i, x);
+  const double2* src = canon + rhs * canon_stride + lex_of(g, x) * 12;
+  Spinor<R> s;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 v = src[k];
+    s.c[k / 3][k % 3] = cx<R>{(R)(v.x * scale), (R)(v.y * scale)};
+  }
+  char* dst = out + rhs * out_stride + ((subset == 2) ? (long)p * spinor_half_bytes(g.Vh, P) : 0);
+  if constexpr (P == P_BF16 || P == P_F16) {
+    // round binary64 -> 16-bit directly (no intermediate binary32 rounding)
+    uint4* b = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double2 v = src[4 * c + k];
+        double re = v.x * scale, im = v.y * scale;
+        if constexpr (P == P_BF16) {
+          __nv_bfloat16 a = __double2bfloat16(re), bb = __double2bfloat16(im);
+          w[k] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(bb) << 16);
+        } else {
+          __half a = __double2half(re), bb = __double2half(im);
+          w[k] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(bb) << 16);
+        }
+      }
+      b[c * g.Vh + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    store_spinor<P>(dst, g.Vh, i, s);
+  }
+}
+
+template <int P>
+__global__ void unpack_spinor_kernel(Geom g, const char* __restrict__ in, double2* __restrict__ canon,
+                                     int subset, long in_stride, long canon_stride, double inv_scale) {
+  typedef typename PrecTraits<P>::R R;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.Vh) return;
+  const int p = (subset == 2) ? (int)blockIdx.y : subset;
+  const int rhs = blockIdx.z;
+  int x[4];
+  eo_coords(g, p, i, x);
+  const char* src = in + rhs * in_stride + ((subset == 2) ? (long)p * spinor_half_bytes(g.Vh, P) : 0);
+  Spinor<R> s;
+  load_spinor<P>(src, g.Vh, i, s);
+  double2* dst = canon + rhs * canon_stride + lex_of(g, x) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k)
+    dst[k] = make_double2((double)s.c[k / 3][k % 3].re * inv_scale, (double)s.c[k / 3][k % 3].im * inv_scale);
+}
+
+cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
+                        int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s) {
+  dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), subset == 2 ? 2 : 1, nrhs);
+  const double2* c = reinterpret_cast<const double2*>(canon);
+  char* o = reinterpret_cast<char*>(out);
+  switch (prec) {
+    case P_F64: pack_spinor_kernel<P_F64><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+    case P_F32: pack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+    case P_BF16: pack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+    case P_F16: pack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
+                          int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s) {
+  dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), subset == 2 ? 2 : 1, nrhs);
+  double2* c = reinterpret_cast<double2*>(canon);
+  const char* i = reinterpret_cast<const char*>(in);
+  const double inv = 1.0 / scale;
+  switch (prec) {
+    case P_F64: unpack_spinor_kernel<P_F64><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
+    case P_F32: unpack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
+    case P_BF16: unpack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
+    case P_F16: unpack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace oq

@@ -1,0 +1,106 @@
+// Deterministic grid reductions in binary64 with a fused "finisher".
+//
+// Every CTA reduces its threads' double partial sums per right-hand side
+// (warp shuffles, then shared memory), writes one partial per (rhs, CTA),
+// and the last CTA to arrive (atomic ticket) sums the partials of that rhs
+// in a fixed order with one warp and runs the finisher that turns the sum
+// into solver scalars (CG alpha / beta, restart norms).  The order of the
+// additions never depends on timing, so results are bitwise reproducible.
+#pragma once
+#include "oq_internal.h"
+
+namespace oq {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void run_finisher(const RedArgs& ra, int rhs, double sum) {
+  CgState* st = ra.cg ? ra.cg + rhs : nullptr;
+  if (ra.fin != FIN_STORE && st->mode != ra.gate) return;  // rhs was not live in this launch
+  switch (ra.fin) {
+    case FIN_STORE:
+      ra.result[rhs] = sum;
+      break;
+    case FIN_ALPHA:
+      st->pAp = sum;
+      if (!(sum > 0.0) || !isfinite(sum)) {
+        st->alpha = 0.0;
+        st->mode = MODE_RESET;
+        st->reason = isfinite(sum) ? WHY_BREAKDOWN : WHY_NONFINITE;
+      } else {
+        st->alpha = st->rr / sum;
+      }
+      break;
+    case FIN_BETA: {
+      double rr_new = sum;
+      st->steps += 1;
+      if (!isfinite(rr_new)) {
+        st->mode = MODE_RESET;
+        st->reason = WHY_NONFINITE;
+      } else if (rr_new <= st->tol2) {
+        st->mode = MODE_RESET;
+        st->reason = WHY_TOL;
+      } else if (rr_new <= st->delta2 * st->rr_start) {
+        st->mode = MODE_RESET;
+        st->reason = WHY_DELTA;
+      } else if (st->steps >= st->nmx) {
+        st->mode = MODE_RESET;
+        st->reason = WHY_NMX;
+      } else {
+        st->beta = rr_new / st->rr;
+      }
+      st->rr = rr_new;
+      break;
+    }
+    case FIN_RESTART:
+      st->rr = sum;
+      st->rr_start = sum;
+      st->mode = MODE_RUN;
+      st->reason = WHY_NONE;
+      break;
+    case FIN_RD2:
+      st->rd2 = sum;
+      break;
+  }
+}
+
+// Called by all threads of a CTA of shape (bx, by): thread (tx, ty) holds v
+// for right-hand side rhs = blockIdx.y * by + ty.  smem needs bx*by/32 doubles.
+__device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs, int nrhs,
+                                            double* smem) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int nw = blockDim.x >> 5;  // warps per rhs row (blockDim.x % 32 == 0)
+  v = warp_sum(v);
+  if ((tx & 31) == 0) smem[ty * nw + (tx >> 5)] = v;
+  __syncthreads();
+  if (tx < 32) {
+    bool last = false;
+    double s = 0.0;
+    if (rhs < nrhs) {
+      if (tx == 0) {
+        for (int w = 0; w < nw; ++w) s += smem[ty * nw + w];
+        ra.partials[(long)rhs * gridDim.x + blockIdx.x] = s;
+        __threadfence();
+        unsigned t = atomicAdd(ra.counters + rhs, 1u);
+        last = (t == gridDim.x - 1);
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        __threadfence();
+        double acc = 0.0;
+        const volatile double* part = ra.partials + (long)rhs * gridDim.x;
+        for (unsigned b = tx; b < gridDim.x; b += 32) acc += part[b];
+        acc = warp_sum(acc);
+        if (tx == 0) {
+          ra.counters[rhs] = 0u;
+          run_finisher(ra, rhs, acc);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace oq

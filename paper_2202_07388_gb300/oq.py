@@ -1,0 +1,243 @@
+"""Thin ctypes binding of the C ABI in ``include/oq.h``.
+
+Only argument marshalling happens here: every step of every operator and
+solver runs in ``liboq.so``.  Device buffers are torch tensors (PyTorch is
+used for memory and streams only); a tensor is passed by its data pointer
+and the current torch CUDA stream is passed as the library's stream.
+
+The shared library is loaded on first use.  If it has not been built the
+load raises: there is no fallback to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liboq.so")
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+LINK_18, LINK_12 = 0, 1
+EVEN, ODD, FULL = 0, 1, 2
+PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16}
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_NOCONV, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
+
+
+class OqLattice(C.Structure):
+    _fields_ = [("L", C.c_int * 4), ("bc_t", C.c_int)]
+
+
+class OqSolverParams(C.Structure):
+    _fields_ = [
+        ("res", C.c_double), ("nmx", C.c_int), ("nkv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
+        ("bs", C.c_int * 4), ("sdtype", C.c_int), ("delta", C.c_double), ("adaptive", C.c_int),
+        ("alpha", C.c_double),
+    ]
+
+
+class OqStatus(C.Structure):
+    _fields_ = [("steps", C.c_int), ("resets", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("true_rel_res", C.c_double)]
+
+
+class OqKernelTime(C.Structure):
+    _fields_ = [("mode", C.c_int), ("epi", C.c_int), ("prec", C.c_int), ("launches", C.c_int),
+                ("total_ms", C.c_double), ("bytes", C.c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P = C.c_void_p
+_SIGS = {
+    "oq_create": (C.c_int, [C.POINTER(_P), C.POINTER(OqLattice), C.c_int]),
+    "oq_destroy": (C.c_int, [_P]),
+    "oq_error_string": (C.c_char_p, [C.c_int]),
+    "oq_spinor_bytes": (C.c_size_t, [_P, C.c_int, C.c_int, C.c_int]),
+    "oq_gauge_upload": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),
+    "oq_clover_build": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _P]),
+    "oq_spinor_pack": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
+    "oq_spinor_unpack": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
+    "oq_dw_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P]),
+    "oq_dw_hat_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P]),
+    "oq_norm2": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.POINTER(C.c_double), _P]),
+    "oq_dot": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_double), _P]),
+    "oq_cgne_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
+                                C.POINTER(OqStatus), _P]),
+    "oq_profile_start": (C.c_int, [_P]),
+    "oq_kernel_launches": (C.c_longlong, [_P]),
+    "oq_profile_stop": (C.c_int, [_P, C.POINTER(OqKernelTime), C.c_int, C.POINTER(C.c_int)]),
+}
+
+
+def lib():
+    """Load liboq.so (once).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2202_07388_gb300.build.build() "
+                               "(the CUDA library is required, there is no fallback)")
+        handle = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(handle, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+class OqError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {lib().oq_error_string(code).decode()} ({code})")
+
+
+def _check(code, where):
+    if code != OK:
+        raise OqError(code, where)
+    return code
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class SolverParams:
+    res: float = 1e-10
+    nmx: int = 10000
+    nkv: int = 16
+    ncy: int = 4
+    nmr: int = 5
+    bs: tuple = (4, 4, 4, 4)
+    sdtype: int = F32
+    delta: float = 0.0
+    adaptive: int = 0
+    alpha: float = 0.9
+
+    def c(self):
+        p = OqSolverParams()
+        p.res, p.nmx, p.nkv, p.ncy, p.nmr = self.res, self.nmx, self.nkv, self.ncy, self.nmr
+        for k in range(4):
+            p.bs[k] = self.bs[k]
+        p.sdtype, p.delta, p.adaptive, p.alpha = self.sdtype, self.delta, self.adaptive, self.alpha
+        return p
+
+
+def status_dict(s: OqStatus) -> dict:
+    return {"steps": s.steps, "resets": s.resets, "restarts": s.restarts, "converged": bool(s.converged),
+            "true_rel_res": s.true_rel_res}
+
+
+class Handle:
+    """One library handle over one or more lattices (``dims`` tuples)."""
+
+    def __init__(self, lattices, bc_t=-1):
+        if isinstance(lattices[0], int):
+            lattices = [lattices]
+        n = len(lattices)
+        arr = (OqLattice * n)()
+        for k, d in enumerate(lattices):
+            for mu in range(4):
+                arr[k].L[mu] = int(d[mu])
+            arr[k].bc_t = bc_t
+        h = C.c_void_p()
+        _check(lib().oq_create(C.byref(h), arr, n), "oq_create")
+        self.h = h
+        self.dims = [tuple(int(v) for v in d) for d in lattices]
+
+    def close(self):
+        if self.h:
+            lib().oq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # sizes -------------------------------------------------------------
+    def spinor_bytes(self, prec, subset=FULL, lat=0):
+        return int(lib().oq_spinor_bytes(self.h, lat, prec, subset))
+
+    def new_packed(self, prec, subset=FULL, nrhs=1, lat=0):
+        import torch
+        n = self.spinor_bytes(prec, subset, lat) * nrhs
+        return torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    # setup -------------------------------------------------------------
+    def gauge_upload(self, u_dev, link_fmt=LINK_12, lat=0, stream=None):
+        _check(lib().oq_gauge_upload(self.h, lat, _ptr(u_dev), link_fmt, _stream(stream)), "oq_gauge_upload")
+
+    def clover_build(self, kappa, csw, lat=0, stream=None):
+        _check(lib().oq_clover_build(self.h, lat, kappa, csw, _stream(stream)), "oq_clover_build")
+
+    # layouts -----------------------------------------------------------
+    def pack(self, canon_dev, packed_dev, prec, subset=FULL, scale=1.0, nrhs=1, lat=0, stream=None):
+        _check(lib().oq_spinor_pack(self.h, lat, prec, subset, _ptr(canon_dev), _ptr(packed_dev), scale, nrhs,
+                                    _stream(stream)), "oq_spinor_pack")
+
+    def unpack(self, packed_dev, canon_dev, prec, subset=FULL, scale=1.0, nrhs=1, lat=0, stream=None):
+        _check(lib().oq_spinor_unpack(self.h, lat, prec, subset, _ptr(packed_dev), _ptr(canon_dev), scale, nrhs,
+                                      _stream(stream)), "oq_spinor_unpack")
+
+    # operators ---------------------------------------------------------
+    def dw(self, in_dev, out_dev, prec, nrhs=1, dagger=False, lat=0, stream=None):
+        _check(lib().oq_dw_apply(self.h, lat, prec, _ptr(in_dev), _ptr(out_dev), nrhs, int(dagger),
+                                 _stream(stream)), "oq_dw_apply")
+
+    def dw_hat(self, in_dev, out_dev, prec, nrhs=1, dagger=False, lat=0, stream=None):
+        _check(lib().oq_dw_hat_apply(self.h, lat, prec, _ptr(in_dev), _ptr(out_dev), nrhs, int(dagger),
+                                     _stream(stream)), "oq_dw_hat_apply")
+
+    def norm2(self, x_dev, prec, subset=FULL, nrhs=1, lat=0, stream=None):
+        out = (C.c_double * nrhs)()
+        _check(lib().oq_norm2(self.h, lat, prec, subset, _ptr(x_dev), nrhs, out, _stream(stream)), "oq_norm2")
+        return np.array(out[:])
+
+    def dot(self, x_dev, y_dev, prec, subset=FULL, nrhs=1, lat=0, stream=None):
+        out = (C.c_double * (2 * nrhs))()
+        _check(lib().oq_dot(self.h, lat, prec, subset, _ptr(x_dev), _ptr(y_dev), nrhs, out, _stream(stream)),
+               "oq_dot")
+        v = np.array(out[:])
+        return v[0::2] + 1j * v[1::2]
+
+    # solvers -----------------------------------------------------------
+    def cgne(self, eta_dev, psi_dev, params: SolverParams, nrhs=1, lat=0, stream=None, check=True):
+        st = (OqStatus * nrhs)()
+        p = params.c()
+        rc = lib().oq_cgne_solve(self.h, lat, C.byref(p), _ptr(eta_dev), _ptr(psi_dev), nrhs, st, _stream(stream))
+        if check and rc not in (OK, ERR_NOCONV):
+            _check(rc, "oq_cgne_solve")
+        return rc, [status_dict(s) for s in st]
+
+    # instrumentation ---------------------------------------------------
+    def profile_start(self):
+        _check(lib().oq_profile_start(self.h), "oq_profile_start")
+
+    def kernel_launches(self):
+        return int(lib().oq_kernel_launches(self.h))
+
+    def profile_stop(self):
+        buf = (OqKernelTime * 64)()
+        n = C.c_int()
+        _check(lib().oq_profile_stop(self.h, buf, 64, C.byref(n)), "oq_profile_stop")
+        return [{"mode": b.mode, "epi": b.epi, "prec": b.prec, "launches": b.launches, "total_ms": b.total_ms,
+                 "bytes": b.bytes} for b in buf[: n.value]]

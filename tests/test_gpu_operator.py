@@ -1,0 +1,136 @@
+"""GPU parity of the Wilson-clover stencil against the FP64 oracle.
+
+Full Dw, the even-odd Schur operator Dhat and their adjoints, at every
+storage precision and both link formats, on lattices whose half volume is a
+multiple of the CTA width, and ragged ones (Vh not a multiple of 128).
+Tolerances (relative L2 error against the oracle on the exact FP64 input):
+binary64 1e-12, binary32 1e-5, bfloat16 5e-3, binary16 2e-3."""
+import numpy as np
+import pytest
+
+from oracle import dirac
+from paper_2202_07388_gb300 import synth
+from tests.gpu_cases import TOL, oracle_case, make_handle, to_dev, from_dev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((4, 4, 4, 4), 0.3, 1, 0.13, 1.0),       # Vh = 128: one full tile
+         ((6, 4, 2, 6), 0.5, 2, 0.135, 1.0),      # Vh = 144: ragged tail
+         ((8, 6, 4, 10), 0.5, 3, 0.1365, 1.3)]    # Vh = 960, several tiles + ragged
+
+
+def _oq():
+    from paper_2202_07388_gb300 import oq
+    return oq
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("link_fmt", [0, 1])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dw_full(case, prec, link_fmt, dagger):
+    oq = _oq()
+    if prec == oq.F64 and link_fmt == oq.LINK_12:
+        pytest.skip("binary64 always uses 18-real links")
+    dims, eps, seed, kappa, csw = case
+    u, a, ainv = oracle_case(dims, eps, seed, kappa, csw)
+    psi = synth.make_source(dims, seed + 100)
+    ref = dirac.dw_dagger(u, a, psi) if dagger else dirac.dw(u, a, psi)
+    h = make_handle(dims, u, kappa, csw, link_fmt)
+    pin = h.new_packed(prec)
+    pout = h.new_packed(prec)
+    h.pack(to_dev(psi), pin, prec)
+    h.dw(pin, pout, prec, dagger=dagger)
+    out = to_dev(np.zeros_like(psi))
+    h.unpack(pout, out, prec)
+    got = from_dev(out, psi.shape)
+    assert rel_err(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dw_hat(case, prec, dagger):
+    oq = _oq()
+    dims, eps, seed, kappa, csw = case
+    u, a, ainv = oracle_case(dims, eps, seed, kappa, csw)
+    psi = dirac.even_part(synth.make_source(dims, seed + 200))
+    ref = dirac.dw_hat_dagger(u, a, ainv, psi) if dagger else dirac.dw_hat(u, a, ainv, psi)
+    h = make_handle(dims, u, kappa, csw, oq.LINK_12)
+    pin = h.new_packed(prec, oq.EVEN)
+    pout = h.new_packed(prec, oq.EVEN)
+    h.pack(to_dev(psi), pin, prec, oq.EVEN)
+    h.dw_hat(pin, pout, prec, dagger=dagger)
+    out = to_dev(np.zeros_like(psi))
+    h.unpack(pout, out, prec, oq.EVEN)
+    got = from_dev(out, psi.shape)
+    assert rel_err(got, ref) < TOL[prec]
+
+
+def test_pack_roundtrip_and_reductions():
+    oq = _oq()
+    dims = (6, 4, 2, 6)
+    u, a, ainv = oracle_case(dims, 0.5, 2, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_18)
+    x = synth.make_source(dims, 5)
+    y = synth.make_source(dims, 6)
+    for prec in (0, 1, 2, 3):
+        px, py = h.new_packed(prec), h.new_packed(prec)
+        h.pack(to_dev(x), px, prec, scale=4.0)
+        h.pack(to_dev(y), py, prec, scale=4.0)
+        back = to_dev(np.zeros_like(x))
+        h.unpack(px, back, prec, scale=4.0)
+        xr = from_dev(back, x.shape)
+        assert rel_err(xr, x) < TOL[prec]
+        n2 = h.norm2(px, prec)[0] / 16.0
+        assert abs(n2 - np.vdot(xr, xr).real) < 1e-12 * n2
+        d = h.dot(px, py, prec)[0] / 16.0
+        assert abs(d - np.vdot(x, y)) < 4 * TOL[prec] * np.linalg.norm(x) * np.linalg.norm(y)
+    if True:  # binary64 pack/unpack is exact
+        px = h.new_packed(0)
+        h.pack(to_dev(x), px, 0)
+        back = to_dev(np.zeros_like(x))
+        h.unpack(px, back, 0)
+        assert np.array_equal(from_dev(back, x.shape), x)
+
+
+def test_u3_links_and_periodic_time():
+    """QCD+QED links U(3) = SU(3) x exp(i q A) (18-real storage), both time
+    boundary conditions."""
+    oq = _oq()
+    dims = (4, 4, 6, 4)
+    u = synth.make_gauge(dims, 0.5, 41)
+    u = synth.apply_u1(u, synth.make_u1_field(dims, 0.2, 42), 2.0 / 3.0)
+    kappa, csw = 0.135, 1.0
+    a = dirac.clover_field(u, dirac.kappa_to_m0(kappa), csw)
+    psi = synth.make_source(dims, 43)
+    for bc in (-1, +1):
+        ref = dirac.dw(u, a, psi, bc_t=float(bc))
+        h = oq.Handle(dims, bc_t=bc)
+        h.gauge_upload(to_dev(u), oq.LINK_18)
+        h.clover_build(kappa, csw)
+        for prec in (0, 1):
+            pin, pout = h.new_packed(prec), h.new_packed(prec)
+            h.pack(to_dev(psi), pin, prec)
+            h.dw(pin, pout, prec)
+            out = to_dev(np.zeros_like(psi))
+            h.unpack(pout, out, prec)
+            assert rel_err(from_dev(out, psi.shape), ref) < TOL[prec]
+
+
+def test_multi_rhs_matches_single():
+    oq = _oq()
+    dims = (6, 4, 2, 6)
+    u, a, ainv = oracle_case(dims, 0.5, 2, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+    n = 3
+    psi = synth.make_source(dims, 7, nrhs=n)
+    for prec in (1, 2):
+        pin, pout = h.new_packed(prec, nrhs=n), h.new_packed(prec, nrhs=n)
+        h.pack(to_dev(psi), pin, prec, nrhs=n)
+        h.dw(pin, pout, prec, nrhs=n)
+        out = to_dev(np.zeros_like(psi))
+        h.unpack(pout, out, prec, nrhs=n)
+        got = from_dev(out, psi.shape)
+        for k in range(n):
+            assert rel_err(got[k], dirac.dw(u, a, psi[k])) < TOL[prec]

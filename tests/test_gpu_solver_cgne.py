@@ -1,0 +1,74 @@
+"""GPU CGNE with reset steps against the oracle: the binary64 solver agrees
+with the oracle's binary64 CGNE, and every storage type reaches a binary64
+true residual of 1e-10 checked with the oracle's own operator (Sec. 2)."""
+import numpy as np
+import pytest
+
+from oracle import dirac, solvers
+from paper_2202_07388_gb300 import synth
+from tests.gpu_cases import oracle_case, make_handle, to_dev, from_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _oq():
+    from paper_2202_07388_gb300 import oq
+    return oq
+
+
+def _normal_residual(u, a, ainv, eta, x):
+    ax = dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, x))
+    return np.linalg.norm((eta - ax).reshape(-1)) / np.linalg.norm(eta.reshape(-1))
+
+
+@pytest.mark.parametrize("dims,eps,seed,kappa", [((4, 4, 4, 4), 0.3, 1, 0.13), ((8, 6, 4, 10), 0.5, 3, 0.135)])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_cgne_true_residual(dims, eps, seed, kappa, prec):
+    oq = _oq()
+    u, a, ainv = oracle_case(dims, eps, seed, kappa, 1.0)
+    eta = dirac.even_part(synth.make_source(dims, seed + 300))
+    h = make_handle(dims, u, kappa, 1.0, oq.LINK_12)
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5000, sdtype=prec))
+    assert rc == oq.OK and st[0]["converged"]
+    x = from_dev(psi, eta.shape)
+    assert np.max(np.abs(dirac.odd_part(x))) == 0.0
+    assert _normal_residual(u, a, ainv, eta, x) <= 1.2e-10
+    assert st[0]["true_rel_res"] <= 1e-10
+    if prec == oq.F64:
+        ref = solvers.cgne(lambda v: dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, v)),
+                           eta, 1e-10, 5000, "fp64")
+        assert abs(st[0]["steps"] - ref.status) <= 2
+        assert np.linalg.norm((x - ref.x).reshape(-1)) <= 1e-8 * np.linalg.norm(ref.x.reshape(-1))
+    else:
+        assert st[0]["resets"] >= 2
+
+
+def test_cgne_multi_rhs_and_reset_ordering():
+    oq = _oq()
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.135, 1.0)
+    n = 3
+    eta = np.stack([dirac.even_part(e) for e in synth.make_source(dims, 77, nrhs=n)])
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+    resets = {}
+    for prec in (1, 2, 3):
+        psi = to_dev(np.zeros_like(eta))
+        rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5000, sdtype=prec), nrhs=n)
+        assert rc == oq.OK
+        x = from_dev(psi, eta.shape)
+        for k in range(n):
+            assert _normal_residual(u, a, ainv, eta[k], x[k]) <= 1.2e-10
+        resets[prec] = np.mean([s["resets"] for s in st])
+    assert resets[2] > resets[3] > resets[1]   # bf16 > fp16 > fp32 (Sec. 2)
+
+
+def test_cgne_nmx_reports_no_convergence():
+    oq = _oq()
+    dims = (4, 4, 4, 4)
+    u, a, ainv = oracle_case(dims, 0.3, 1, 0.13, 1.0)
+    eta = dirac.even_part(synth.make_source(dims, 9))
+    h = make_handle(dims, u, 0.13, 1.0, oq.LINK_12)
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5, sdtype=1))
+    assert rc == oq.ERR_NOCONV and not st[0]["converged"] and st[0]["steps"] == 5
