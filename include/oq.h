@@ -139,6 +139,34 @@ int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_de
 int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs,
                     int dagger, void* stream);
 
+/* Same result as oq_dw_hat_apply, for callers that cannot allocate device
+ * memory.  No counterpart in the paper: this is a service of the library.
+ *
+ * oq_dw_hat_apply keeps its odd-site intermediate in handle-owned scratch
+ * that it allocates with cudaMalloc the first time it needs more (and growing
+ * it synchronises the device).  Some callers cannot allow that: a host
+ * program that hands out all device memory through its own pool allocator
+ * and forbids allocations behind its back, or one that must keep a fixed
+ * device-memory footprint once it has started.  This variant allocates
+ * nothing: the intermediate lives in one file-scope device array of
+ * OQ_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
+ * holds until the process exits.  The caller still passes the input and
+ * output fields (packed even half fields, as for oq_dw_hat_apply) and the
+ * handle must already hold the gauge field and clover term.
+ *  - nrhs * oq_spinor_bytes(h, lat, prec, OQ_EVEN) must not exceed
+ *    OQ_NOALLOC_SCRATCH_BYTES, else the call returns OQ_ERR_ARG and enqueues
+ *    nothing (binary32: up to 174,762 even sites for one right-hand side).
+ *  - The first call made while a given device is current looks up the
+ *    array's device address on that device (cudaGetSymbolAddress); make that
+ *    first call before any stream capture.
+ *  - Every call, from any handle, uses the same array, and the array keeps
+ *    the last call's contents (each call overwrites what it reads, so nothing
+ *    needs clearing).  Calls that overlap on the GPU (e.g. on two streams at
+ *    once) race on it: order them on one stream or with events. */
+#define OQ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs,
+                            int dagger, void* stream);
+
 /* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and
  * out[2k], out[2k+1] = Re, Im <x_k, y_k> (host arrays of nrhs / 2 nrhs). */
 int oq_norm2(oq_handle h, int lat, int prec, int subset, const void* x_dev, int nrhs,

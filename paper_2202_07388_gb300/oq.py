@@ -65,6 +65,7 @@ _SIGS = {
     "oq_spinor_unpack": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
     "oq_dw_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P]),
     "oq_dw_hat_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P]),
+    "oq_dw_hat_apply_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P]),
     "oq_norm2": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.POINTER(C.c_double), _P]),
     "oq_dot": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_double), _P]),
     "oq_cgne_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
