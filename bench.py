@@ -265,6 +265,12 @@ def run_ours(args):
     del pk, pk2, src_d
     psi = torch.zeros_like(eta)
     prm = oq.SolverParams(res=RES, nmx=20000, sdtype=oq.F16)
+    tuned = {}
+    for pname, pc, nr in (("f16", oq.F16, NRHS), ("f64", oq.F64, NRHS)):
+        tuned[f"{pname}x{nr}"] = {MODE_NAMES[m]: v for m, v in h.autotune(pc, nrhs=nr).items()}
+    if not args.no_tts:
+        for pname, pc in (("f64", oq.F64), ("f32", oq.F32), ("bf16", oq.BF16), ("f16", oq.F16)):
+            tuned[f"{pname}x1"] = {MODE_NAMES[m]: v for m, v in h.autotune(pc, nrhs=1).items()}
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
 
@@ -367,7 +373,7 @@ def run_ours(args):
             "kernels": [{"kernel": f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}",
                          "launches": p["launches"], "ms": p["total_ms"],
                          "gbs": p["bytes"] / (p["total_ms"] * 1e-3) / 1e9} for p in prof],
-            "tts": tts, "setup_s": setup_s,
+            "tts": tts, "setup_s": setup_s, "tuned_shapes": tuned,
         }
         print(json.dumps(line), flush=True)
     h.close()
@@ -376,8 +382,40 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small case for ncu captures of the stencil kernels: 32 x 32^3 lattice
+    (links + clover 0.5 GB, larger than L2), 12 rhs in F16 storage, a few Dhat and
+    Dhat^dag applications with the tuned launch shapes."""
+    import torch
+    from paper_2202_07388_gb300 import oq, synth
+    from paper_2202_07388_gb300 import build as _build
+    _build.build()
+    dims = (32, 32, 32, 32)
+    u = synth.make_gauge(dims, EPS, SEED)
+    h = oq.Handle(dims)
+    h.gauge_upload(to_dev(u), oq.LINK_12)
+    h.clover_build(KAPPA, CSW)
+    prec = oq.PREC[args.profile_prec]
+    nrhs = args.profile_nrhs
+    h.autotune(prec, nrhs=nrhs)
+    src = torch.randn(nrhs * int(np.prod(dims)) * 24, dtype=torch.float64, device="cuda")
+    a, b = h.new_packed(prec, oq.EVEN, nrhs=nrhs), h.new_packed(prec, oq.EVEN, nrhs=nrhs)
+    h.pack(src, a, prec, oq.EVEN, nrhs=nrhs)
+    for _ in range(3):
+        h.dw_hat(a, b, prec, nrhs=nrhs)
+        h.dw_hat(b, a, prec, nrhs=nrhs, dagger=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "x".join(map(str, dims)), "prec": args.profile_prec, "nrhs": nrhs,
+                      "launches": h.kernel_launches()}))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-prec", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
+    ap.add_argument("--profile-nrhs", type=int, default=12)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -387,6 +425,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tts", action="store_true")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -96,6 +96,8 @@ typedef struct {
   int restarts;        /* GCR restarts */
   int converged;       /* 1 if true_rel_res <= res */
   double true_rel_res; /* binary64 ||eta - A psi|| / ||eta|| at exit */
+  int cycles;          /* SAP-GCR: Schwarz cycles run in total */
+  double mr_avg;       /* SAP-GCR: mean MR steps per block solve */
 } oq_status;
 
 /* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no
@@ -167,6 +169,17 @@ int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* ou
 int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs,
                             int dagger, void* stream);
 
+/* Autotuner (no counterpart in the paper): time every admissible CTA shape
+ * (bx sites x by right-hand sides per CTA, bx a multiple of 32, bx*by <= 256)
+ * of the full Dw and of both Dhat passes for this (lattice, precision, nrhs)
+ * on handle-owned scratch fields with CUDA events, and keep the fastest per
+ * pass in the handle; every later stencil launch of that variant, including
+ * those inside the solvers, uses it.  Synchronises `stream`.
+ * oq_tune_get reports the chosen shape and its time per launch (mode 0 = Dw,
+ * 1 = Dhat pass 1, 2 = Dhat pass 2); OQ_ERR_STATE if not tuned. */
+int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* stream);
+int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms);
+
 /* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and
  * out[2k], out[2k+1] = Re, Im <x_k, y_k> (host arrays of nrhs / 2 nrhs). */
 int oq_norm2(oq_handle h, int lat, int prec, int subset, const void* x_dev, int nrhs,
@@ -184,6 +197,43 @@ int oq_dot(oq_handle h, int lat, int prec, int subset, const void* x_dev, const 
  * of nrhs entries. */
 int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
                   double* psi_dev, int nrhs, oq_status* st, void* stream);
+
+/* The CGNE of oq_cgne_solve over an uneven batch: nsys systems, system k on
+ * lattice lats[k] of the handle (lattices of different sizes and operators,
+ * e.g. the QCD+QED charges of a U(3) ensemble), one right-hand side each
+ * (eta_dev[k], psi_dev[k]: host arrays of device pointers to canonical
+ * binary64 full-lattice fields).  Every stencil pass of all systems is one
+ * launch of a persistent grid over a (system, site block) tile list; chunks
+ * of regular iterations are captured once into a CUDA graph and replayed.
+ * All systems must use the same link format.  Runs on a library-owned
+ * stream after synchronising `stream`; returns when done.  st: nsys entries. */
+int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const oq_solver_params* p,
+                        const double* const* eta_dev, double* const* psi_dev, oq_status* st, void* stream);
+
+/* Flexible GCR preconditioned by the Schwarz alternating procedure (Sec. 3,
+ * 3.1, Table 2): solves D psi = eta on the full lattice.  eta_dev / psi_dev:
+ * canonical binary64 full-lattice fields (nrhs consecutive, solved one after
+ * the other); psi_dev is overwritten.  Each GCR step applies p->ncy Schwarz
+ * cycles (all blocks of colour 0 then of colour 1, each block solved by
+ * p->nmr minimal-residual steps on the block operator with Dirichlet
+ * boundaries; blocks of p->bs sites, an even number per direction, at most
+ * 256 sites); ncy = 0 means no preconditioner.  p->adaptive selects the
+ * adaptive variant of Sec. 3.2 (ncy, nmr become maxima; MR exits after >= 4
+ * steps when ||r|| > alpha ||r_prev||, when ||r|| grows, or below
+ * res ||eta|| / n_blocks; cycles end when one does not lower the SAP
+ * residual).  Krylov vectors, SAP and regular steps: binary32 (p->sdtype
+ * must be OQ_F32); solution, restart residuals and reductions: binary64.
+ * nkv (<= 64) vectors per restart, nmx GCR steps at most. */
+int oq_sap_gcr_solve(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
+                     double* psi_dev, int nrhs, oq_status* st, void* stream);
+
+/* The SAP preconditioner alone (Sec. 3): phi = M_SAP rho, starting from
+ * phi = 0, p->ncy cycles of p->nmr block MR steps (blocks p->bs; p->adaptive
+ * switches on the MR exit rules of Sec. 3.2 with exit-3 tolerance mr_tol; the
+ * cycle test needs the global residual and is applied by oq_sap_gcr_solve
+ * only).  rho_dev, phi_dev: packed binary32 full fields. */
+int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* p, const void* rho_dev, void* phi_dev,
+                 double mr_tol, void* stream);
 
 /* Instrumentation: while profiling is on, every stencil launch is bracketed
  * by CUDA events on its own stream.  oq_profile_stop() synchronises the

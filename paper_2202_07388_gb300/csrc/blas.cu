@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(RED_BX) norm2_kernel(const char* x, long Vh, l
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc += (double)s.c[a][c].re * s.c[a][c].re + (double)s.c[a][c].im * s.c[a][c].im;
   }
-  grid_reduce(acc, ra, rhs, nrhs, smem);
+  grid_reduce(acc, ra, rhs, nrhs, smem, blockIdx.x, gridDim.x);
 }
 
 template <int P>
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(RED_BX) dot_kernel(const char* x, const char* 
         im += (double)a.c[s][c].re * b.c[s][c].im - (double)a.c[s][c].im * b.c[s][c].re;
       }
   }
-  grid_reduce(re, ra, 2 * rhs, 2 * nrhs, smem);
+  grid_reduce(re, ra, 2 * rhs, 2 * nrhs, smem, blockIdx.x, gridDim.x);
   __syncthreads();
-  grid_reduce(im, ra, 2 * rhs + 1, 2 * nrhs, smem);
+  grid_reduce(im, ra, 2 * rhs + 1, 2 * nrhs, smem, blockIdx.x, gridDim.x);
 }
 
 // nsites = number of sites of the field (Vh for a half field, 2 Vh for a full one:
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) cg_restart_kernel(const char* rd, char* r
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc += (double)v.c[s][c].re * v.c[s][c].re + (double)v.c[s][c].im * v.c[s][c].im;
   }
-  grid_reduce(acc, ra, rhs, nrhs, smem);
+  grid_reduce(acc, ra, rhs, nrhs, smem, blockIdx.x, gridDim.x);
 }
 
 cudaError_t cg_restart(int prec, const double* rd, void* rs, void* p, void* xs, int xprec, long Vh, long stride_d,

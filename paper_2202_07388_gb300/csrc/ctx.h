@@ -66,6 +66,7 @@ struct oq_ctx {
   size_t cg_n = 0;
   // launch shapes
   std::map<oq::TuneKey, std::pair<int, int>> tuned;
+  std::map<oq::TuneKey, float> tuned_ms;
   // kernels launched by this handle so far
   long long launches = 0;
   // profiling
@@ -94,6 +95,22 @@ struct oq_ctx {
     int rc = alloc(&b, n);
     *out = b.p;
     return rc;
+  }
+
+  // library-owned stream for graph capture and replay (the caller's stream
+  // may be the legacy default stream, which cannot be captured)
+  cudaStream_t work_stream = nullptr;
+  int ensure_work_stream() {
+    if (!work_stream && cudaStreamCreateWithFlags(&work_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return OQ_ERR_CUDA;
+    return OQ_OK;
+  }
+
+  // pinned host staging for small coefficient uploads (4 KiB)
+  void* stage_host = nullptr;
+  int ensure_stage() {
+    if (!stage_host && cudaMallocHost(&stage_host, 4096) != cudaSuccess) return OQ_ERR_NOMEM;
+    return OQ_OK;
   }
 
   int ensure_scratch() {
@@ -180,9 +197,18 @@ struct oq_ctx {
     if (it != tuned.end()) {
       l.bx = it->second.first;
       l.by = it->second.second;
-    } else {
+    } else if (nrhs == 1) {
       l.bx = 128;
       l.by = 1;
+    } else {
+      // several right-hand sides: 32 sites x (largest divisor of nrhs <= 8) rows
+      l.bx = 32;
+      l.by = 1;
+      for (int d = 8; d >= 1; --d)
+        if (nrhs % d == 0) {
+          l.by = d;
+          break;
+        }
     }
     if (l.by > nrhs) l.by = nrhs;
     return l;
@@ -251,6 +277,8 @@ struct oq_ctx {
     cudaFree(status_dev);
     cudaFree(cg_dev);
     cudaFreeHost(cg_host);
+    cudaFreeHost(stage_host);
+    if (work_stream) cudaStreamDestroy(work_stream);
     for (auto& r : prof) {
       cudaEventDestroy(r.e0);
       cudaEventDestroy(r.e1);

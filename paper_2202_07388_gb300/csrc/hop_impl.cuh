@@ -54,31 +54,13 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p,
   }
 }
 
-template <typename R>
-__device__ __forceinline__ double site_norm2(const Spinor<R>& s) {
-  R acc = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc += s.c[k][c].re * s.c[k][c].re + s.c[k][c].im * s.c[k][c].im;
-  return (double)acc;
-}
-
+// One output site i (parity p) of right-hand side rhs: the stencil, the
+// clover term and the epilogue.  Returns the site's contribution to the
+// epilogue's reduction (0 if none).
 template <int P, int FMT, int MODE, bool DAG, int EPI>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+__device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, int p) {
   typedef typename PrecTraits<P>::R R;
-  extern __shared__ double red_smem[];
-  // HOP_DW: the two parities of one site range run in neighbouring CTAs, so
-  // that a link read by the forward hop of one parity is still in L2 when
-  // the backward hop of the other parity needs it
-  const long blk = (MODE == HOP_DW) ? (long)(blockIdx.x >> 1) : (long)blockIdx.x;
-  const long i = blk * blockDim.x + threadIdx.x;
-  const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
-  const int p = (MODE == HOP_DW) ? (int)(blockIdx.x & 1) : a.p;
-  bool live = (i < a.g.Vh) && (rhs < a.nrhs);
-  if (live && a.cg) live = (a.cg[rhs].mode == a.gate);
   double red = 0.0;
-  if (live) {
     int x[4];
     eo_coords(a.g, p, i, x);
     const long par_in = (MODE == HOP_DW) ? (long)(1 - p) * a.half_bytes : 0;
@@ -153,9 +135,56 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
           acc2 += (double)res.c[s][c].re * res.c[s][c].re + (double)res.c[s][c].im * res.c[s][c].im;
       red = acc2;
     }
-  }
+  return red;
+}
+
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+  extern __shared__ double red_smem[];
+  // CTA = blockDim.x sites x blockDim.y right-hand sides (one rhs per row:
+  // the rows read the same links and clover blocks, served by L1).  The
+  // grid index runs fastest over the rhs tiles of one site block, then (for
+  // HOP_DW) over the two parities, then over site blocks, so that CTAs that
+  // read the same links are resident at the same time and share them in L2.
+  const unsigned ntile = (a.nrhs + blockDim.y - 1) / blockDim.y;
+  const unsigned tile = blockIdx.x % ntile;
+  const unsigned rest = blockIdx.x / ntile;
+  const long blk = (MODE == HOP_DW) ? (long)(rest >> 1) : (long)rest;
+  const long i = blk * blockDim.x + threadIdx.x;
+  const int rhs = tile * blockDim.y + threadIdx.y;
+  const int p = (MODE == HOP_DW) ? (int)(rest & 1) : a.p;
+  bool live = (i < a.g.Vh) && (rhs < a.nrhs);
+  if (live && a.cg) live = (a.cg[rhs].mode == a.gate);
+  double red = 0.0;
+  if (live) red = hop_site<P, FMT, MODE, DAG, EPI>(a, i, rhs, p);
   if constexpr (EPI != EPI_NONE) {
-    grid_reduce(red, a.red, rhs, a.nrhs, red_smem);
+    grid_reduce(red, a.red, rhs, a.nrhs, red_smem, (unsigned)blk, gridDim.x / ntile);
+  }
+}
+
+// Batched form over several systems (lattices / operators of any size, one
+// right-hand side each): a persistent grid walks a list of tiles
+// (system, site block); every system has its own arguments, solver state and
+// reduction scratch in device memory.  For HOP_DW the block index carries
+// the parity in its lowest bit.
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+__global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs* __restrict__ sys,
+                                                        const int2* __restrict__ tiles, int ntiles) {
+  extern __shared__ double red_smem[];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    const HopArgs& a = sys[tl.x];
+    const long blk = (MODE == HOP_DW) ? (long)(tl.y >> 1) : (long)tl.y;
+    const int p = (MODE == HOP_DW) ? (tl.y & 1) : a.p;
+    const long i = blk * blockDim.x + threadIdx.x;
+    bool live = i < a.g.Vh;
+    if (live && a.cg) live = (a.cg[0].mode == a.gate);
+    double red = 0.0;
+    if (live) red = hop_site<P, FMT, MODE, DAG, EPI>(a, i, 0, p);
+    if constexpr (EPI != EPI_NONE) {
+      const unsigned nblk = (unsigned)((a.g.Vh + blockDim.x - 1) / blockDim.x);
+      grid_reduce(red, a.red, 0, 1, red_smem, (unsigned)blk, nblk);
+    }
   }
 }
 
@@ -163,8 +192,15 @@ template <int P, int FMT, int MODE, bool DAG, int EPI>
 static cudaError_t launch_one(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
   dim3 block(L.bx, L.by, 1);
   const unsigned nb = (unsigned)((a.g.Vh + L.bx - 1) / L.bx);
-  dim3 grid(MODE == HOP_DW ? 2u * nb : nb, (unsigned)((a.nrhs + L.by - 1) / L.by), 1u);
+  const unsigned ntile = (unsigned)((a.nrhs + L.by - 1) / L.by);
+  dim3 grid((MODE == HOP_DW ? 2u * nb : nb) * ntile, 1u, 1u);
   size_t smem = (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32) * L.by;
+  if (L.sys) {
+    dim3 bblock(L.bx, 1, 1);
+    hop_batch_kernel<P, FMT, MODE, DAG, EPI><<<L.grid, bblock, (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32),
+                                                s>>>(L.sys, L.tiles, L.ntiles);
+    return cudaGetLastError();
+  }
   hop_kernel<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -218,6 +218,17 @@ __device__ __forceinline__ void store_spinor(void* base, long Vh, long i,
   }
 }
 
+// sum of the 24 squares of one site (in the arithmetic type), as binary64
+template <typename R>
+__device__ __forceinline__ double site_norm2(const Spinor<R>& s) {
+  R acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc += s.c[k][c].re * s.c[k][c].re + s.c[k][c].im * s.c[k][c].im;
+  return (double)acc;
+}
+
 // Round a binary32 spinor held in registers to the storage type P and back,
 // i.e. the value a store_spinor<P> / load_spinor<P> pair would give, without
 // re-reading memory written by the same kernel.

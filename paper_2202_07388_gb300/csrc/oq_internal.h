@@ -75,6 +75,12 @@ struct HopLaunch {
   int dagger;
   int epi;       // HopEpi
   int bx, by;    // CTA shape: bx sites x by right-hand sides
+  // batched launch over several systems (hop_batch_kernel) when sys != null:
+  // per-system arguments and the (system, site block) tile list in device memory
+  const HopArgs* sys = nullptr;
+  const int2* tiles = nullptr;
+  int ntiles = 0;
+  int grid = 0;
 };
 
 cudaError_t launch_hop(const HopLaunch& L, const HopArgs& a, cudaStream_t s);

@@ -29,4 +29,9 @@ cudaError_t cg_restart(int prec, const double* rd, void* rs, void* p, void* xs, 
 cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride, int nrhs, const CgState* cg,
                           int gate, cudaStream_t s);
 
+// one SAP half cycle: every block of `colour` (binary32 fields)
+cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
+                       const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
+                       unsigned* mr_steps, cudaStream_t s);
+
 }  // namespace oq

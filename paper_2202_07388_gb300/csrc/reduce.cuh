@@ -68,9 +68,10 @@ __device__ __forceinline__ void run_finisher(const RedArgs& ra, int rhs, double 
 }
 
 // Called by all threads of a CTA of shape (bx, by): thread (tx, ty) holds v
-// for right-hand side rhs = blockIdx.y * by + ty.  smem needs bx*by/32 doubles.
+// for right-hand side `rhs` (one rhs per row).  `cta` numbers this CTA among
+// the `ncta` CTAs that contribute to the same rhs.  smem needs bx*by/32 doubles.
 __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs, int nrhs,
-                                            double* smem) {
+                                            double* smem, unsigned cta, unsigned ncta) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nw = blockDim.x >> 5;  // warps per rhs row (blockDim.x % 32 == 0)
   v = warp_sum(v);
@@ -82,17 +83,17 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs
     if (rhs < nrhs) {
       if (tx == 0) {
         for (int w = 0; w < nw; ++w) s += smem[ty * nw + w];
-        ra.partials[(long)rhs * gridDim.x + blockIdx.x] = s;
+        ra.partials[(long)rhs * ncta + cta] = s;
         __threadfence();
         unsigned t = atomicAdd(ra.counters + rhs, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == ncta - 1);
       }
       last = __shfl_sync(0xffffffffu, last, 0);
       if (last) {
         __threadfence();
         double acc = 0.0;
-        const volatile double* part = ra.partials + (long)rhs * gridDim.x;
-        for (unsigned b = tx; b < gridDim.x; b += 32) acc += part[b];
+        const volatile double* part = ra.partials + (long)rhs * ncta;
+        for (unsigned b = tx; b < ncta; b += 32) acc += part[b];
         acc = warp_sum(acc);
         if (tx == 0) {
           ra.counters[rhs] = 0u;

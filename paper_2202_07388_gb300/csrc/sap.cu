@@ -1,0 +1,278 @@
+// Schwarz alternating procedure (Sec. 3, Figs. 2-3) as one kernel per colour.
+//
+// The lattice is cut into blocks of bs[0] x ... x bs[3] sites; block colour =
+// parity of the sum of its block coordinates (an even number of blocks per
+// direction, so blocks of one colour never touch).  One CTA handles one block
+// of the requested colour, one thread per block site:
+//
+//   1. r_i = (rho - D phi)_i with the full stencil (neighbours in the
+//      other-colour blocks carry the latest boundary values; phi of this
+//      colour is only written by this CTA, at the end);
+//   2. MR steps on the block operator D_i (Dirichlet: hops leaving the block
+//      dropped, clover kept), with r_i in shared memory ([component][site]
+//      for conflict-free neighbour reads), p = D_i r in registers:
+//      omega = <p, r> / <p, p>, x += omega r, r -= omega p;
+//      the adaptive variant (Sec. 3.2) leaves the loop when, after at least
+//      4 steps, ||r|| > alpha ||r_prev||, when ||r|| grew, or when ||r|| fell
+//      below tol = res ||eta|| / n_blocks; every decision is block-uniform;
+//   3. phi_i += x.
+// Block reductions are binary64.  Arithmetic and storage binary32.
+#include "oq_internal.h"
+#include "oq_kernels.h"
+#include "hop_impl.cuh"
+
+namespace oq {
+
+struct SapArgs {
+  Geom g;
+  int bs[4];
+  int nb[4];
+  int colour;
+  const void* links;   // binary32 packed links
+  const void* clov;    // binary32 packed clover
+  const char* rho;     // packed binary32 full field
+  char* phi;           // packed binary32 full field, updated in place
+  long half_bytes;
+  int nmr;
+  int adaptive;
+  float alpha;
+  double tol;          // adaptive exit 3 (absolute block norm)
+  unsigned* mr_steps;  // accumulated MR steps over all blocks (may be null)
+};
+
+__device__ __forceinline__ void load_smem(const float* sm, int nsite, int t, Spinor<float>& s) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s.c[k / 3][k % 3] = cx<float>{sm[(2 * k) * nsite + t], sm[(2 * k + 1) * nsite + t]};
+}
+__device__ __forceinline__ void store_smem(float* sm, int nsite, int t, const Spinor<float>& s) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sm[(2 * k) * nsite + t] = s.c[k / 3][k % 3].re;
+    sm[(2 * k + 1) * nsite + t] = s.c[k / 3][k % 3].im;
+  }
+}
+
+// sum of up to 3 doubles over the CTA, result in every thread
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[3 * w] = a;
+    red[3 * w + 1] = b;
+    red[3 * w + 2] = c;
+  }
+  __syncthreads();
+  a = b = c = 0.0;
+  for (int k = 0; k < nw; ++k) {
+    a += red[3 * k];
+    b += red[3 * k + 1];
+    c += red[3 * k + 2];
+  }
+}
+
+// in-block hop along +mu / -mu from smem (Dirichlet: outside neighbours dropped)
+template <int FMT, int MU>
+__device__ __forceinline__ void block_hop(const SapArgs& a, const float* sm, int nsite, int t, const int l[4],
+                                          const int x[4], int p, long i, Spinor<float>& acc) {
+  int stride = 1;
+  for (int nu = 3; nu > MU; --nu) stride *= a.bs[nu];
+  if (l[MU] + 1 < a.bs[MU]) {
+    Spinor<float> nb;
+    load_smem(sm, nsite, t + stride, nb);
+    HalfSpinor<float> h, r;
+    project<MU, -1>(nb, h);
+    Su3<float> u;
+    load_link<float, FMT>(a.links, a.g.Vh, p, MU, i, u);
+    su3_mul(u, h, r);
+    accum_reconstruct<MU, -1>(acc, r, -0.5f);
+  }
+  if (l[MU] > 0) {
+    Spinor<float> nb;
+    load_smem(sm, nsite, t - stride, nb);
+    HalfSpinor<float> h, r;
+    project<MU, +1>(nb, h);
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[MU] -= 1;
+    Su3<float> u;
+    load_link<float, FMT>(a.links, a.g.Vh, 1 - p, MU, eo_index(a.g, y), u);
+    su3_dag_mul(u, h, r);
+    accum_reconstruct<MU, +1>(acc, r, -0.5f);
+  }
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) sap_kernel(const SapArgs a) {
+  extern __shared__ float sm[];
+  const int nsite = a.bs[0] * a.bs[1] * a.bs[2] * a.bs[3];
+  double* red = reinterpret_cast<double*>(sm + 24 * nsite);
+  const int t = threadIdx.x;
+  const bool act = t < nsite;
+  // which block: the blockIdx.x-th block of colour a.colour
+  const int half3 = a.nb[3] / 2;
+  int row = blockIdx.x / half3;
+  const int m = blockIdx.x % half3;
+  const int bc2 = row % a.nb[2];
+  row /= a.nb[2];
+  const int bc1 = row % a.nb[1];
+  const int bc0 = row / a.nb[1];
+  const int bc3 = 2 * m + ((a.colour + bc0 + bc1 + bc2) & 1);
+  int l[4], x[4];
+  {
+    int tt = act ? t : 0;
+    l[3] = tt % a.bs[3];
+    tt /= a.bs[3];
+    l[2] = tt % a.bs[2];
+    tt /= a.bs[2];
+    l[1] = tt % a.bs[1];
+    l[0] = tt / a.bs[1];
+  }
+  x[0] = bc0 * a.bs[0] + l[0];
+  x[1] = bc1 * a.bs[1] + l[1];
+  x[2] = bc2 * a.bs[2] + l[2];
+  x[3] = bc3 * a.bs[3] + l[3];
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const long i = eo_index(a.g, x);
+
+  // 1. block residual r = rho - D phi (full stencil)
+  Spinor<float> r;
+  if (act) {
+    HopArgs ha;
+    ha.g = a.g;
+    ha.links = a.links;
+    const char* nbf = a.phi + (long)(1 - p) * a.half_bytes;
+    Spinor<float> acc;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc.c[s][c] = cx<float>{0.f, 0.f};
+    hop_dir<P_F32, FMT, 0, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 1, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 2, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 3, false>(ha, nbf, p, i, x, acc, -0.5f);
+    Spinor<float> ph, aph, rh;
+    load_spinor<P_F32>(a.phi + (long)p * a.half_bytes, a.g.Vh, i, ph);
+    clover_apply<float>(a.clov, a.g.Vh, p, i, ph, aph);
+    load_spinor<P_F32>(a.rho + (long)p * a.half_bytes, a.g.Vh, i, rh);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r.c[s][c] = rh.c[s][c] - (aph.c[s][c] + acc.c[s][c]);
+    store_smem(sm, nsite, t, r);
+  }
+  double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+  if (act) n0 = site_norm2(r);
+  block_sum3(n0, z1, z2, red);
+  double rn_prev = sqrt(n0);
+
+  // 2. MR on D_i
+  Spinor<float> xs;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xs.c[s][c] = cx<float>{0.f, 0.f};
+  int steps = 0;
+  for (int k = 1; k <= a.nmr; ++k) {
+    Spinor<float> pv;
+    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
+    if (act) {
+      Spinor<float> own;
+      load_smem(sm, nsite, t, own);
+      clover_apply<float>(a.clov, a.g.Vh, p, i, own, pv);
+      block_hop<FMT, 0>(a, sm, nsite, t, l, x, p, i, pv);
+      block_hop<FMT, 1>(a, sm, nsite, t, l, x, p, i, pv);
+      block_hop<FMT, 2>(a, sm, nsite, t, l, x, p, i, pv);
+      block_hop<FMT, 3>(a, sm, nsite, t, l, x, p, i, pv);
+      float ar = 0.f, ai = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cx<float> q = pv.c[s][c], v = own.c[s][c];
+          ar += q.re * v.re + q.im * v.im;
+          ai += q.re * v.im - q.im * v.re;
+          a2 += q.re * q.re + q.im * q.im;
+        }
+      pr_re = ar;
+      pr_im = ai;
+      pp = a2;
+    }
+    block_sum3(pr_re, pr_im, pp, red);  // contains __syncthreads: all neighbour reads done
+    float om_re = 0.f, om_im = 0.f;
+    if (pp > 0.0) {
+      om_re = (float)(pr_re / pp);
+      om_im = (float)(pr_im / pp);
+    }
+    const cx<float> om{om_re, om_im};
+    double n1 = 0.0, y1 = 0.0, y2 = 0.0;
+    if (act) {
+      Spinor<float> own;
+      load_smem(sm, nsite, t, own);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cfma(xs.c[s][c], om, own.c[s][c]);
+          own.c[s][c] = own.c[s][c] - om * pv.c[s][c];
+        }
+      store_smem(sm, nsite, t, own);
+      n1 = site_norm2(own);
+    }
+    block_sum3(n1, y1, y2, red);
+    steps = k;
+    const double rn_new = sqrt(n1);
+    if (a.adaptive) {
+      if ((k >= 4 && rn_new > (double)a.alpha * rn_prev) || rn_new > rn_prev || rn_new < a.tol) break;
+    }
+    rn_prev = rn_new;
+  }
+  // 3. phi_i += x
+  if (act) {
+    char* pp = a.phi + (long)p * a.half_bytes;
+    Spinor<float> ph;
+    load_spinor<P_F32>(pp, a.g.Vh, i, ph);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ph.c[s][c] = ph.c[s][c] + xs.c[s][c];
+    store_spinor<P_F32>(pp, a.g.Vh, i, ph);
+  }
+  if (a.mr_steps && t == 0) atomicAdd(a.mr_steps, (unsigned)steps);
+}
+
+cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
+                       const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
+                       unsigned* mr_steps, cudaStream_t s) {
+  SapArgs a;
+  a.g = g;
+  int nblk = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    a.bs[mu] = bs[mu];
+    a.nb[mu] = g.L[mu] / bs[mu];
+    nblk *= a.nb[mu];
+  }
+  a.colour = colour;
+  a.links = links;
+  a.clov = clov;
+  a.rho = (const char*)rho;
+  a.phi = (char*)phi;
+  a.half_bytes = spinor_half_bytes(g.Vh, P_F32);
+  a.nmr = nmr;
+  a.adaptive = adaptive;
+  a.alpha = alpha;
+  a.tol = tol;
+  a.mr_steps = mr_steps;
+  const int nsite = bs[0] * bs[1] * bs[2] * bs[3];
+  const int threads = (nsite + 31) / 32 * 32;
+  const size_t smem = sizeof(float) * 24 * nsite + sizeof(double) * 3 * (threads / 32);
+  dim3 grid(nblk / 2), block(threads);
+  if (fmt == LINK_12)
+    sap_kernel<LINK_12><<<grid, block, smem, s>>>(a);
+  else
+    sap_kernel<LINK_18><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace oq

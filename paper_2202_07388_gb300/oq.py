@@ -42,7 +42,7 @@ class OqSolverParams(C.Structure):
 
 class OqStatus(C.Structure):
     _fields_ = [("steps", C.c_int), ("resets", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
-                ("true_rel_res", C.c_double)]
+                ("true_rel_res", C.c_double), ("cycles", C.c_int), ("mr_avg", C.c_double)]
 
 
 class OqKernelTime(C.Structure):
@@ -70,6 +70,14 @@ _SIGS = {
     "oq_dot": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_double), _P]),
     "oq_cgne_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
                                 C.POINTER(OqStatus), _P]),
+    "oq_sap_gcr_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
+                                   C.POINTER(OqStatus), _P]),
+    "oq_sap_apply": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_double, _P]),
+    "oq_cgne_solve_batch": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(OqSolverParams),
+                                      C.POINTER(_P), C.POINTER(_P), C.POINTER(OqStatus), _P]),
+    "oq_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
+    "oq_tune_get": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                              C.POINTER(C.c_float)]),
     "oq_profile_start": (C.c_int, [_P]),
     "oq_kernel_launches": (C.c_longlong, [_P]),
     "oq_profile_stop": (C.c_int, [_P, C.POINTER(OqKernelTime), C.c_int, C.POINTER(C.c_int)]),
@@ -143,7 +151,7 @@ class SolverParams:
 
 def status_dict(s: OqStatus) -> dict:
     return {"steps": s.steps, "resets": s.resets, "restarts": s.restarts, "converged": bool(s.converged),
-            "true_rel_res": s.true_rel_res}
+            "true_rel_res": s.true_rel_res, "cycles": s.cycles, "mr_avg": s.mr_avg}
 
 
 class Handle:
@@ -228,6 +236,43 @@ class Handle:
         if check and rc not in (OK, ERR_NOCONV):
             _check(rc, "oq_cgne_solve")
         return rc, [status_dict(s) for s in st]
+
+    def cgne_batch(self, lats, etas, psis, params: SolverParams, stream=None, check=True):
+        n = len(lats)
+        la = (C.c_int * n)(*lats)
+        ep = (_P * n)(*[t.data_ptr() for t in etas])
+        pp = (_P * n)(*[t.data_ptr() for t in psis])
+        st = (OqStatus * n)()
+        p = params.c()
+        rc = lib().oq_cgne_solve_batch(self.h, n, la, C.byref(p), ep, pp, st, _stream(stream))
+        if check and rc not in (OK, ERR_NOCONV):
+            _check(rc, "oq_cgne_solve_batch")
+        return rc, [status_dict(s) for s in st]
+
+    def sap_gcr(self, eta_dev, psi_dev, params: SolverParams, nrhs=1, lat=0, stream=None, check=True):
+        st = (OqStatus * nrhs)()
+        p = params.c()
+        rc = lib().oq_sap_gcr_solve(self.h, lat, C.byref(p), _ptr(eta_dev), _ptr(psi_dev), nrhs, st,
+                                    _stream(stream))
+        if check and rc not in (OK, ERR_NOCONV):
+            _check(rc, "oq_sap_gcr_solve")
+        return rc, [status_dict(s) for s in st]
+
+    def sap_apply(self, rho_packed, phi_packed, params: SolverParams, mr_tol=0.0, lat=0, stream=None):
+        p = params.c()
+        _check(lib().oq_sap_apply(self.h, lat, C.byref(p), _ptr(rho_packed), _ptr(phi_packed), mr_tol,
+                                  _stream(stream)), "oq_sap_apply")
+
+    # tuning ------------------------------------------------------------
+    def autotune(self, prec, nrhs=1, lat=0, stream=None):
+        _check(lib().oq_autotune(self.h, lat, prec, nrhs, _stream(stream)), "oq_autotune")
+        out = {}
+        for mode in (0, 1, 2):
+            bx, by, ms = C.c_int(), C.c_int(), C.c_float()
+            _check(lib().oq_tune_get(self.h, lat, prec, mode, nrhs, C.byref(bx), C.byref(by), C.byref(ms)),
+                   "oq_tune_get")
+            out[mode] = (bx.value, by.value, ms.value)
+        return out
 
     # instrumentation ---------------------------------------------------
     def profile_start(self):
