@@ -50,8 +50,12 @@ extern "C" {
 
 typedef struct oq_ctx* oq_handle;
 
-/* storage precision of spinor fields (arithmetic is binary32 for F32/BF16/F16) */
-enum { OQ_F64 = 0, OQ_F32 = 1, OQ_BF16 = 2, OQ_F16 = 3 };
+/* storage precision of spinor fields (arithmetic is binary32 for F32/BF16/F16).
+ * OQ_DF64: binary64 storage (the OQ_F64 layout) with double-float arithmetic
+ * (hi + lo pairs of binary32, ~48 significant bits) on the binary32 pipes,
+ * accepted by oq_dw_apply, oq_dw_hat_apply, oq_autotune and the packing
+ * calls; the CGNE uses it for intermediate reset steps. */
+enum { OQ_F64 = 0, OQ_F32 = 1, OQ_BF16 = 2, OQ_F16 = 3, OQ_DF64 = 4 };
 /* storage of the binary32 link copy: 18 reals, or 12 reals with the third
  * row rebuilt as conj(row0 x row1) (SU(3) links only) */
 enum { OQ_LINK_18 = 0, OQ_LINK_12 = 1 };
@@ -180,6 +184,20 @@ int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, 
 int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* stream);
 int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms);
 
+/* Handle options (no counterpart in the paper).
+ * OQ_OPT_DF64_RESETS: 1 = the intermediate CGNE reset steps of a
+ *   low-precision solve recompute the residual with OQ_DF64 arithmetic; a
+ *   residual that meets the target is confirmed in binary64 before the solve
+ *   stops, and a double-float value found too optimistic switches the solve
+ *   back to binary64 resets.  Default 0 (binary64 resets): on GB300 the
+ *   double-float stencil measured slower than the native binary64 one.
+ * OQ_OPT_TEST_TC_SKIP_MMA: testing aid for failure detection; 1 = the
+ *   tensor-core PTC layer issues no MMA, so its bounded (1 s) wait for the
+ *   tensor core runs out and oq_nnprec_apply_tc returns OQ_ERR_TIMEOUT with
+ *   the device still usable.  Default 0. */
+enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2 };
+int oq_set_option(oq_handle h, int key, int value);
+
 /* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and
  * out[2k], out[2k+1] = Re, Im <x_k, y_k> (host arrays of nrhs / 2 nrhs). */
 int oq_norm2(oq_handle h, int lat, int prec, int subset, const void* x_dev, int nrhs,
@@ -226,6 +244,43 @@ int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const oq_solver_
  * nkv (<= 64) vectors per restart, nmx GCR steps at most. */
 int oq_sap_gcr_solve(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
                      double* psi_dev, int nrhs, oq_status* st, void* stream);
+
+/* Learned preconditioner (not in the paper): a gauge-equivariant
+ * parallel-transport network of two linear layers, 1 -> 2 -> 1 spinor
+ * fields (12 -> 24 -> 12 complex channels per site),
+ *   out_c'(x) = sum_q sum_c W[q][c'][c] (T_q in_c)(x),
+ * over the 9 paths q = 0 (identity), 1+2mu (U_mu(x) in(x+mu)),
+ * 2+2mu (U_mu(x-mu)^dag in(x-mu)) with the time-boundary factor, W a
+ * complex 4x4 spin matrix.  weights_dev: binary32 master weights, 1152
+ * floats = layer 1 W1[9][2][1][4][4] then layer 2 W2[9][1][2][4][4],
+ * complex (re, im) interleaved; the layers use them rounded to bfloat16
+ * with binary32 accumulation.  Fields: packed binary32 full fields.
+ *
+ * oq_nnprec_apply: out = M in.
+ * oq_nnprec_grad:  gradient (binary64, 1152 doubles, d/dRe + i d/dIm of
+ *   the loss) and loss = mean_k ||M r_k - e_k||^2 / ||e_k||^2 over n pairs
+ *   (r_dev, e_dev: n consecutive packed binary32 full fields).
+ * oq_nnprec_train: `steps` Adam steps (learning rate lr) on the mean loss,
+ *   updating weights_dev in place; loss_host[step] (may be null) gets the
+ *   loss before each step.  Synchronises `stream`.
+ * oq_nn_gcr_solve: oq_sap_gcr_solve with M as the preconditioner of the
+ *   flexible GCR instead of SAP (the network is the only preconditioner). */
+int oq_nnprec_apply(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
+                    void* stream);
+int oq_nnprec_grad(oq_handle h, int lat, const float* weights_dev, const void* r_dev, const void* e_dev,
+                   int n, double* grad_dev, double* loss_host, void* stream);
+int oq_nnprec_train(oq_handle h, int lat, float* weights_dev, const void* r_dev, const void* e_dev, int n,
+                    double lr, int steps, double* loss_host, void* stream);
+int oq_nn_gcr_solve(oq_handle h, int lat, const oq_solver_params* p, const float* weights_dev,
+                    const double* eta_dev, double* psi_dev, int nrhs, oq_status* st, void* stream);
+
+/* oq_nnprec_apply with the channel contraction on the 5th-generation tensor
+ * cores (tcgen05.mma, bfloat16 operands: weights and transported inputs,
+ * binary32 accumulation in tensor memory), 128 sites per CTA.  The
+ * transports stay on the CUDA cores.  Synchronises `stream`; returns
+ * OQ_ERR_TIMEOUT if a bounded wait for the tensor core gave up. */
+int oq_nnprec_apply_tc(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
+                       void* stream);
 
 /* The SAP preconditioner alone (Sec. 3): phi = M_SAP rho, starting from
  * phi = 0, p->ncy cycles of p->nmr block MR steps (blocks p->bs; p->adaptive

@@ -21,6 +21,7 @@ cudaError_t launch_hop(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
     case P_F32: return launch_hop_f32(L, a, s);
     case P_BF16: return launch_hop_bf16(L, a, s);
     case P_F16: return launch_hop_f16(L, a, s);
+    case P_DF64: return launch_hop_df64(L, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -75,7 +76,7 @@ extern "C" int oq_destroy(oq_handle h) {
 }
 
 extern "C" size_t oq_spinor_bytes(oq_handle h, int lat, int prec, int subset) {
-  if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 3 || subset < 0 || subset > 2) return 0;
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 4 || subset < 0 || subset > 2) return 0;
   size_t half = (size_t)spinor_half_bytes(h->lats[lat].g.Vh, prec);
   return subset == OQ_FULL ? 2 * half : half;
 }
@@ -128,6 +129,7 @@ static bool valid_lat(oq_handle h, int lat) { return h && lat >= 0 && lat < (int
 
 extern "C" int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const double* canon_dev, void* packed_dev,
                               double scale, int nrhs, void* stream) {
+  if (prec == P_DF64) prec = P_F64;  // same binary64 storage
   if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 3 || subset < 0 || subset > 2 ||
       nrhs < 1 || !(scale != 0.0) || !isfinite(scale))
     return OQ_ERR_ARG;
@@ -142,6 +144,7 @@ extern "C" int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const 
 
 extern "C" int oq_spinor_unpack(oq_handle h, int lat, int prec, int subset, const void* packed_dev, double* canon_dev,
                                 double scale, int nrhs, void* stream) {
+  if (prec == P_DF64) prec = P_F64;  // same binary64 storage
   if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 3 || subset < 0 || subset > 2 ||
       nrhs < 1 || !(scale != 0.0) || !isfinite(scale))
     return OQ_ERR_ARG;
@@ -162,7 +165,7 @@ static bool overlap(const void* a, const void* b, size_t n) {
 
 extern "C" int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs, int dagger,
                            void* stream) {
-  if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 3 || nrhs < 1) return OQ_ERR_ARG;
+  if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 4 || nrhs < 1) return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
   const size_t full = oq_spinor_bytes(h, lat, prec, OQ_FULL);
@@ -180,7 +183,7 @@ extern "C" int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, v
 
 extern "C" int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs, int dagger,
                                void* stream) {
-  if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 3 || nrhs < 1) return OQ_ERR_ARG;
+  if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 4 || nrhs < 1) return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
   const size_t half = oq_spinor_bytes(h, lat, prec, OQ_EVEN);
@@ -288,3 +291,12 @@ extern "C" int oq_profile_stop(oq_handle h, oq_kernel_time* out, int max_entries
 }
 
 extern "C" long long oq_kernel_launches(oq_handle h) { return h ? h->launches : -1; }
+
+extern "C" int oq_set_option(oq_handle h, int key, int value) {
+  if (!h) return OQ_ERR_ARG;
+  switch (key) {
+    case OQ_OPT_DF64_RESETS: h->df64_resets = value != 0; return OQ_OK;
+    case OQ_OPT_TEST_TC_SKIP_MMA: h->hook_tc_skip_commit = value != 0; return OQ_OK;
+  }
+  return OQ_ERR_ARG;
+}

@@ -147,10 +147,12 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     return OQ_OK;
   };
 
-  // the binary64 reset step for all rhs in MODE_RESET
-  auto reset_step = [&]() -> int {
-    KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
-    HopArgs a = h->hop_args(lat, P_F64);
+  // the reset step for all rhs in MODE_RESET.  rp: arithmetic of the residual
+  // recomputation (binary64 storage either way); accumulate: add s x_s to x_d
+  // first (false re-checks the same x_d)
+  auto reset_step = [&](int rp, bool accumulate) -> int {
+    if (accumulate) KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
+    HopArgs a = h->hop_args(lat, rp);
     a.nrhs = nrhs;
     a.cg = h->cg_dev;
     a.gate = MODE_RESET;
@@ -158,16 +160,16 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     a.half_bytes = (long)h64;
     // t = A_oo^-1 D_oe x_d ; u = Dhat x_d
     a.in = xd; a.out = t64; a.p = 1;
-    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P1, 0, EPI_NONE, nrhs), a, s));
+    RK(h->run_hop(h->hop_launch(lat, rp, HOP_P1, 0, EPI_NONE, nrhs), a, s));
     a.in = t64; a.in2 = xd; a.out = u64v; a.p = 0;
-    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P2, 0, EPI_NONE, nrhs), a, s));
+    RK(h->run_hop(h->hop_launch(lat, rp, HOP_P2, 0, EPI_NONE, nrhs), a, s));
     // t = ..., r_d = eta - Dhat^dag u, ||r_d||^2
     a.in = u64v; a.out = t64; a.p = 1;
-    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P1, 1, EPI_NONE, nrhs), a, s));
+    RK(h->run_hop(h->hop_launch(lat, rp, HOP_P1, 1, EPI_NONE, nrhs), a, s));
     a.in = t64; a.in2 = u64v; a.out = rd; a.p = 0;
     a.ep_eta = eta64; a.ep_eta_stride = (long)h64;
     a.red = h->red_args(FIN_RD2, MODE_RESET);
-    RK(h->run_hop(h->hop_launch(lat, P_F64, HOP_P2, 1, EPI_RESID64, nrhs), a, s));
+    RK(h->run_hop(h->hop_launch(lat, rp, HOP_P2, 1, EPI_RESID64, nrhs), a, s));
     return OQ_OK;
   };
 
@@ -198,6 +200,10 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     return OQ_OK;
   };
 
+  // Reset residuals use binary64 arithmetic; optionally (OQ_OPT_DF64_RESETS)
+  // the intermediate resets of a low-precision solve use double-float
+  // arithmetic, and every convergence decision is still taken in binary64.
+  int reset_prec = (P != P_F64 && h->df64_resets) ? P_DF64 : P_F64;
   int pending = decide(false);
   RK(upload());
   if (pending) RK(restart());
@@ -209,8 +215,26 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
       rst += cs[k].mode == MODE_RESET;
     }
     if (rst) {
-      RK(reset_step());
+      RK(reset_step(reset_prec, true));
       RK(download());
+      if (reset_prec == P_DF64) {
+        // a double-float residual may only propose convergence: confirm it with
+        // binary64 arithmetic before deciding (and keep binary64 from then on if
+        // the double-float value was too optimistic)
+        bool claims = false;
+        for (int k = 0; k < nrhs; ++k)
+          if (cs[k].mode == MODE_RESET && sqrt(cs[k].rd2) <= prm->res * eta_n[k]) claims = true;
+        if (claims) {
+          std::vector<double> df(nrhs);
+          for (int k = 0; k < nrhs; ++k) df[k] = cs[k].rd2;
+          RK(reset_step(P_F64, false));
+          RK(download());
+          for (int k = 0; k < nrhs; ++k)
+            if (cs[k].mode == MODE_RESET && sqrt(df[k]) <= prm->res * eta_n[k] &&
+                sqrt(cs[k].rd2) > prm->res * eta_n[k])
+              reset_prec = P_F64;
+        }
+      }
       pending = decide(true);
       RK(upload());
       if (pending) RK(restart());

@@ -69,6 +69,11 @@ struct oq_ctx {
   std::map<oq::TuneKey, float> tuned_ms;
   // kernels launched by this handle so far
   long long launches = 0;
+  // CGNE: intermediate reset residuals in double-float arithmetic (off by
+  // default: measured slower than native binary64 on GB300)
+  bool df64_resets = false;
+  // test hook: the tensor-core PTC layer issues no MMA, so its bounded wait runs out
+  bool hook_tc_skip_commit = false;
   // profiling
   bool prof_on = false;
   std::vector<oq::ProfRec> prof;
@@ -178,7 +183,7 @@ struct oq_ctx {
     oq::HopArgs a;
     memset(&a, 0, sizeof(a));
     a.g = L.g;
-    const bool f64 = prec == oq::P_F64;
+    const bool f64 = prec == oq::P_F64 || prec == oq::P_DF64;
     a.links = f64 ? L.u64.p : L.u32.p;
     a.clov = f64 ? L.a64.p : L.a32.p;
     a.cinv = f64 ? L.i64.p : L.i32.p;
@@ -217,8 +222,9 @@ struct oq_ctx {
   // algorithmic bytes of one stencil launch (each operand counted once)
   double hop_bytes(const oq::HopLaunch& l, const oq::HopArgs& a) {
     const double sp = oq::prec_bytes(l.prec);
-    const double su = l.prec == oq::P_F64 ? 8.0 : 4.0;
-    const double ru = (l.prec != oq::P_F64 && l.link_fmt == oq::LINK_12) ? 12.0 : 18.0;
+    const bool wide = l.prec == oq::P_F64 || l.prec == oq::P_DF64;  // binary64 links and clover
+    const double su = wide ? 8.0 : 4.0;
+    const double ru = (!wide && l.link_fmt == oq::LINK_12) ? 12.0 : 18.0;
     const double sites = (double)a.g.Vh * (l.mode == oq::HOP_DW ? 2.0 : 1.0);
     double spin = 0.0;
     double links = 0.0;

@@ -233,8 +233,22 @@ extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, c
   return OQ_OK;
 }
 
+static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const float* nn_w, const double* eta_dev,
+                    double* psi_dev, int nrhs, oq_status* st, void* stream);
+
 extern "C" int oq_sap_gcr_solve(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev,
                                 double* psi_dev, int nrhs, oq_status* st, void* stream) {
+  return gcr_impl(h, lat, prm, nullptr, eta_dev, psi_dev, nrhs, st, stream);
+}
+
+extern "C" int oq_nn_gcr_solve(oq_handle h, int lat, const oq_solver_params* prm, const float* weights_dev,
+                               const double* eta_dev, double* psi_dev, int nrhs, oq_status* st, void* stream) {
+  if (!weights_dev) return OQ_ERR_ARG;
+  return gcr_impl(h, lat, prm, weights_dev, eta_dev, psi_dev, nrhs, st, stream);
+}
+
+static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const float* nn_w, const double* eta_dev,
+                    double* psi_dev, int nrhs, oq_status* st, void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
   if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nkv < 1 || prm->nkv > 64 || prm->ncy < 0 || prm->nmr < 0)
     return OQ_ERR_ARG;
@@ -270,6 +284,10 @@ extern "C" int oq_sap_gcr_solve(oq_handle h, int lat, const oq_solver_params* pr
   void* mrc = nullptr;
   rc |= h->workspace(lat, "gcr_mrsteps", sizeof(unsigned) * 4, &mrc);
   if (rc) return OQ_ERR_NOMEM;
+  if (nn_w) {
+    rc = nnprec_prepare(h, lat, nn_w, (cudaStream_t)stream);
+    if (rc) return rc;
+  }
   const int grid = reduce_grid(2 * Vh);
   rc = h->ensure_reduce(2 * 64, grid);
   if (rc) return rc;
@@ -342,7 +360,10 @@ extern "C" int oq_sap_gcr_solve(oq_handle h, int lat, const oq_solver_params* pr
         char* phik = (char*)Phi + (long)k * f32;
         char* chik = (char*)Chi + (long)k * f32;
         // phi_k = M rho
-        if (prm->ncy == 0) {
+        if (nn_w) {
+          RK(nnprec_forward(h, lat, rho, phik, s));
+          precs += 1;
+        } else if (prm->ncy == 0) {
           CK(cudaMemcpyAsync(phik, rho, f32, cudaMemcpyDeviceToDevice, s));
         } else {
           CK(cudaMemsetAsync(phik, 0, f32, s));

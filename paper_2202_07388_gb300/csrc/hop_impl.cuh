@@ -132,7 +132,10 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
       for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          acc2 += (double)res.c[s][c].re * res.c[s][c].re + (double)res.c[s][c].im * res.c[s][c].im;
+        {
+          const double re = (double)res.c[s][c].re, im = (double)res.c[s][c].im;
+          acc2 += re * re + im * im;
+        }
       red = acc2;
     }
   return red;
@@ -216,9 +219,11 @@ static cudaError_t dispatch_mode_epi(const HopLaunch& L, const HopArgs& a, cudaS
       break;
     case HOP_P2:
       if (L.epi == EPI_NONE) return launch_one<P, FMT, HOP_P2, DAG, EPI_NONE>(L, a, s);
-      if (L.epi == EPI_NORM) return launch_one<P, FMT, HOP_P2, DAG, EPI_NORM>(L, a, s);
-      if (L.epi == EPI_CG) return launch_one<P, FMT, HOP_P2, DAG, EPI_CG>(L, a, s);
-      if constexpr (P == P_F64)
+      if constexpr (P != P_DF64) {
+        if (L.epi == EPI_NORM) return launch_one<P, FMT, HOP_P2, DAG, EPI_NORM>(L, a, s);
+        if (L.epi == EPI_CG) return launch_one<P, FMT, HOP_P2, DAG, EPI_CG>(L, a, s);
+      }
+      if constexpr (P == P_F64 || P == P_DF64)
         if (L.epi == EPI_RESID64) return launch_one<P, FMT, HOP_P2, DAG, EPI_RESID64>(L, a, s);
       break;
   }

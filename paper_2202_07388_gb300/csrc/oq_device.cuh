@@ -24,7 +24,63 @@
 
 namespace oq {
 
-enum Prec : int { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3 };
+// P_DF64 (internal): binary64 storage, "double-float" arithmetic (a value is
+// an unevaluated sum hi + lo of two binary32 numbers, ~48 significant bits)
+// on the binary32 pipes, for the reset-step residuals on a GPU whose binary64
+// rate is far below its binary32 rate.
+enum Prec : int { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3, P_DF64 = 4 };
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic: error-free transformations (Knuth's two-sum,
+// Dekker's fast two-sum, the FMA two-product) combined into the accurate
+// double-word addition and multiplication of Joldes, Muller and Popescu
+// (ACM TOMS 44, 2017).  Explicit _rn intrinsics keep the compiler from
+// contracting or reassociating the compensated steps.
+// ---------------------------------------------------------------------------
+struct dfloat {
+  float hi, lo;
+  dfloat() = default;
+  __host__ __device__ dfloat(float a) : hi(a), lo(0.f) {}
+  __host__ __device__ dfloat(int a) : hi((float)a), lo(0.f) {}
+  __device__ dfloat(double a) {
+    hi = __double2float_rn(a);
+    lo = __double2float_rn(a - (double)hi);
+  }
+  __device__ dfloat(float h, float l) : hi(h), lo(l) {}
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dfloat(s, e);
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  const dfloat t = df_two_sum(x.lo, y.lo);
+  s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
+__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) {
+  x = x + y;
+  return x;
+}
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+using ::fma;  // keep the float / double overloads visible next to the dfloat one
 enum LinkFmt : int { LINK_18 = 0, LINK_12 = 1 };
 
 // ---------------------------------------------------------------------------
@@ -133,6 +189,7 @@ template <> struct PrecTraits<P_F64> { typedef double R; typedef double2 Chunk; 
 template <> struct PrecTraits<P_F32> { typedef float R;  typedef float4 Chunk;  static const int nchunk = 6;  static const int bytes = 4; };
 template <> struct PrecTraits<P_BF16> { typedef float R; typedef uint4 Chunk;   static const int nchunk = 3;  static const int bytes = 2; };
 template <> struct PrecTraits<P_F16> { typedef float R;  typedef uint4 Chunk;   static const int nchunk = 3;  static const int bytes = 2; };
+template <> struct PrecTraits<P_DF64> { typedef dfloat R; typedef double2 Chunk; static const int nchunk = 12; static const int bytes = 8; };
 
 template <typename T>
 __device__ __forceinline__ T ldg_nc(const T* p) { return __ldg(p); }
@@ -160,12 +217,12 @@ __device__ __forceinline__ void load_spinor(const void* base, long Vh, long i,
                                             Spinor<typename PrecTraits<P>::R>& s) {
   typedef typename PrecTraits<P>::R R;
   cx<R>* f = &s.c[0][0];
-  if constexpr (P == P_F64) {
+  if constexpr (P == P_F64 || P == P_DF64) {
     const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       double2 v = ldg_nc(b + c * Vh + i);
-      f[c] = cx<R>{v.x, v.y};
+      f[c] = cx<R>{R(v.x), R(v.y)};
     }
   } else if constexpr (P == P_F32) {
     const float4* b = reinterpret_cast<const float4*>(base);
@@ -195,10 +252,10 @@ __device__ __forceinline__ void store_spinor(void* base, long Vh, long i,
                                              const Spinor<typename PrecTraits<P>::R>& s) {
   typedef typename PrecTraits<P>::R R;
   const cx<R>* f = &s.c[0][0];
-  if constexpr (P == P_F64) {
+  if constexpr (P == P_F64 || P == P_DF64) {
     double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) b[c * Vh + i] = make_double2(f[c].re, f[c].im);
+    for (int c = 0; c < 12; ++c) b[c * Vh + i] = make_double2((double)f[c].re, (double)f[c].im);
   } else if constexpr (P == P_F32) {
     float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll

@@ -88,8 +88,11 @@ cudaError_t launch_hop_f64(const HopLaunch& L, const HopArgs& a, cudaStream_t s)
 cudaError_t launch_hop_f32(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_df64(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 
-__host__ __device__ inline int prec_bytes(int prec) { return prec == P_F64 ? 8 : prec == P_F32 ? 4 : 2; }
+__host__ __device__ inline int prec_bytes(int prec) {
+  return (prec == P_F64 || prec == P_DF64) ? 8 : prec == P_F32 ? 4 : 2;
+}
 __host__ __device__ inline long spinor_half_bytes(long Vh, int prec) { return 24L * Vh * prec_bytes(prec); }
 
 }  // namespace oq

@@ -2,6 +2,8 @@
 #pragma once
 #include "oq_internal.h"
 
+struct oq_ctx;
+
 namespace oq {
 
 cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, cudaStream_t s);
@@ -28,6 +30,11 @@ cudaError_t cg_restart(int prec, const double* rd, void* rs, void* p, void* xs, 
                        long stride_d, long stride_s, long stride_xs, int nrhs, const RedArgs& ra, cudaStream_t s);
 cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride, int nrhs, const CgState* cg,
                           int gate, cudaStream_t s);
+
+// learned preconditioner (ptc.cu): round the binary32 master weights to the
+// bfloat16 forward weights held by the handle, and apply M = L2 L1
+int nnprec_prepare(struct ::oq_ctx* h, int lat, const float* master, cudaStream_t s);
+int nnprec_forward(struct ::oq_ctx* h, int lat, const void* r, void* y, cudaStream_t s);
 
 // one SAP half cycle: every block of `colour` (binary32 fields)
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,

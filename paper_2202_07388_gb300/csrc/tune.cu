@@ -31,7 +31,7 @@ std::vector<std::pair<int, int>> candidates(int nrhs) {
 }  // namespace
 
 extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* stream) {
-  if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 3 || nrhs < 1 || nrhs > 64)
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 4 || nrhs < 1 || nrhs > 64)
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;

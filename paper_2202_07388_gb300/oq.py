@@ -19,10 +19,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "liboq.so")
 
-F64, F32, BF16, F16 = 0, 1, 2, 3
+F64, F32, BF16, F16, DF64 = 0, 1, 2, 3, 4
 LINK_18, LINK_12 = 0, 1
 EVEN, ODD, FULL = 0, 1, 2
 PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16}
+OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA = 1, 2
 
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_NOCONV, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
@@ -75,6 +76,14 @@ _SIGS = {
     "oq_sap_apply": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_double, _P]),
     "oq_cgne_solve_batch": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(OqSolverParams),
                                       C.POINTER(_P), C.POINTER(_P), C.POINTER(OqStatus), _P]),
+    "oq_nnprec_apply": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "oq_nnprec_apply_tc": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "oq_nnprec_grad": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P, C.POINTER(C.c_double), _P]),
+    "oq_nnprec_train": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, C.c_double, C.c_int,
+                                  C.POINTER(C.c_double), _P]),
+    "oq_nn_gcr_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, _P, C.c_int,
+                                  C.POINTER(OqStatus), _P]),
+    "oq_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
     "oq_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
     "oq_tune_get": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                               C.POINTER(C.c_float)]),
@@ -258,10 +267,43 @@ class Handle:
             _check(rc, "oq_sap_gcr_solve")
         return rc, [status_dict(s) for s in st]
 
+    # learned preconditioner -------------------------------------------
+    def nnprec_apply(self, weights, in_packed, out_packed, lat=0, stream=None):
+        _check(lib().oq_nnprec_apply(self.h, lat, _ptr(weights), _ptr(in_packed), _ptr(out_packed),
+                                     _stream(stream)), "oq_nnprec_apply")
+
+    def nnprec_apply_tc(self, weights, in_packed, out_packed, lat=0, stream=None):
+        _check(lib().oq_nnprec_apply_tc(self.h, lat, _ptr(weights), _ptr(in_packed), _ptr(out_packed),
+                                        _stream(stream)), "oq_nnprec_apply_tc")
+
+    def nnprec_grad(self, weights, r_packed, e_packed, n, grad, lat=0, stream=None):
+        loss = C.c_double()
+        _check(lib().oq_nnprec_grad(self.h, lat, _ptr(weights), _ptr(r_packed), _ptr(e_packed), n, _ptr(grad),
+                                    C.byref(loss), _stream(stream)), "oq_nnprec_grad")
+        return loss.value
+
+    def nnprec_train(self, weights, r_packed, e_packed, n, lr, steps, lat=0, stream=None):
+        losses = (C.c_double * steps)()
+        _check(lib().oq_nnprec_train(self.h, lat, _ptr(weights), _ptr(r_packed), _ptr(e_packed), n, lr, steps,
+                                     losses, _stream(stream)), "oq_nnprec_train")
+        return np.array(losses[:])
+
+    def nn_gcr(self, weights, eta_dev, psi_dev, params: SolverParams, nrhs=1, lat=0, stream=None, check=True):
+        st = (OqStatus * nrhs)()
+        p = params.c()
+        rc = lib().oq_nn_gcr_solve(self.h, lat, C.byref(p), _ptr(weights), _ptr(eta_dev), _ptr(psi_dev), nrhs,
+                                   st, _stream(stream))
+        if check and rc not in (OK, ERR_NOCONV):
+            _check(rc, "oq_nn_gcr_solve")
+        return rc, [status_dict(s) for s in st]
+
     def sap_apply(self, rho_packed, phi_packed, params: SolverParams, mr_tol=0.0, lat=0, stream=None):
         p = params.c()
         _check(lib().oq_sap_apply(self.h, lat, C.byref(p), _ptr(rho_packed), _ptr(phi_packed), mr_tol,
                                   _stream(stream)), "oq_sap_apply")
+
+    def set_option(self, key, value):
+        _check(lib().oq_set_option(self.h, key, int(value)), "oq_set_option")
 
     # tuning ------------------------------------------------------------
     def autotune(self, prec, nrhs=1, lat=0, stream=None):

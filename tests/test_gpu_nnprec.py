@@ -1,0 +1,165 @@
+"""The learned preconditioner on the GPU: forward layers and gradients
+against the FP64 oracle (with the same bfloat16-rounded weights), and the
+gain test: a network trained on the GPU (own forward/backward kernels, Adam)
+on (residual, error) pairs from the binary64 solver lowers its loss and cuts
+the flexible-GCR step count relative to GCR without it."""
+import numpy as np
+import pytest
+
+from oracle import dirac, ptc
+from paper_2202_07388_gb300 import synth
+from tests.gpu_cases import oracle_case, make_handle, to_dev, from_dev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+NW1 = 9 * 2 * 1 * 16
+NW2 = 9 * 1 * 2 * 16
+
+
+def _bf16(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _weights(seed, scale=0.2):
+    rng = np.random.default_rng(seed)
+    w = (rng.standard_normal(2 * (NW1 + NW2)) * scale).astype(np.float32)
+    return w
+
+
+def _split(w32):
+    """binary32 master (re, im interleaved) -> oracle complex arrays of the bf16-rounded weights."""
+    wr = _bf16(w32).astype(np.float64)
+    c = wr[0::2] + 1j * wr[1::2]
+    return c[:NW1].reshape(9, 2, 1, 4, 4), c[NW1:].reshape(9, 1, 2, 4, 4)
+
+
+def _wdev(w32):
+    import torch
+    return torch.from_numpy(w32.copy()).cuda()
+
+
+def _packed(h, oq, fields):
+    import torch
+    n = fields.shape[0]
+    out = h.new_packed(oq.F32, nrhs=n)
+    h.pack(to_dev(fields), out, oq.F32, nrhs=n)
+    return out
+
+
+@pytest.mark.parametrize("link_fmt", [0, 1])
+def test_ptc_forward_matches_oracle(link_fmt):
+    from paper_2202_07388_gb300 import oq
+    dims = (4, 4, 2, 6)
+    u, a, ainv = oracle_case(dims, 0.6, 81, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, link_fmt)
+    w = _weights(82)
+    w1, w2 = _split(w)
+    psi = synth.make_source(dims, 83)
+    ref, _ = ptc.forward(u, w1, w2, psi)
+    pin = _packed(h, oq, psi[None])
+    pout = h.new_packed(oq.F32)
+    h.nnprec_apply(_wdev(w), pin, pout)
+    out = to_dev(np.zeros_like(psi))
+    h.unpack(pout, out, oq.F32)
+    assert rel_err(from_dev(out, psi.shape), ref) < 1e-5
+
+
+@pytest.mark.parametrize("dims,link_fmt", [((4, 4, 2, 6), 0), ((4, 4, 2, 6), 1), ((8, 8, 4, 8), 1)])
+def test_ptc_tensor_core_forward_matches_oracle(dims, link_fmt):
+    """tcgen05 channel contraction (bfloat16 operands, binary32 accumulation
+    in tensor memory): 1e-2 relative, from rounding the transported inputs
+    and the hidden fields to bfloat16; V = 192 leaves a ragged 128-site tile."""
+    from paper_2202_07388_gb300 import oq
+    u, a, ainv = oracle_case(dims, 0.6, 81, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, link_fmt)
+    w = _weights(87)
+    w1, w2 = _split(w)
+    psi = synth.make_source(dims, 88)
+    ref, _ = ptc.forward(u, w1, w2, psi)
+    pin = _packed(h, oq, psi[None])
+    pout, pcc = h.new_packed(oq.F32), h.new_packed(oq.F32)
+    h.nnprec_apply_tc(_wdev(w), pin, pout)
+    h.nnprec_apply(_wdev(w), pin, pcc)
+    out, occ = to_dev(np.zeros_like(psi)), to_dev(np.zeros_like(psi))
+    h.unpack(pout, out, oq.F32)
+    h.unpack(pcc, occ, oq.F32)
+    got = from_dev(out, psi.shape)
+    assert rel_err(got, ref) < 1e-2
+    assert rel_err(got, from_dev(occ, psi.shape)) < 1e-2
+
+
+def test_ptc_gradient_matches_oracle():
+    import torch
+    from paper_2202_07388_gb300 import oq
+    dims = (4, 4, 2, 6)
+    u, a, ainv = oracle_case(dims, 0.6, 81, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+    w = _weights(84)
+    w1, w2 = _split(w)
+    n = 2
+    r = synth.make_source(dims, 85, nrhs=n)
+    e = synth.make_source(dims, 86, nrhs=n)
+    # oracle: mean loss and gradient over the pairs (inputs rounded to binary32 as the GPU sees them)
+    r32 = r.astype(np.complex64).astype(np.complex128)
+    e32 = e.astype(np.complex64).astype(np.complex128)
+    loss, g1, g2 = 0.0, 0.0, 0.0
+    for k in range(n):
+        lk, a1, a2 = ptc.backward(u, w1, w2, r32[k], e32[k])
+        loss += lk / n
+        g1 = g1 + a1 / n
+        g2 = g2 + a2 / n
+    grad = torch.zeros(2 * (NW1 + NW2), dtype=torch.float64, device="cuda")
+    gl = h.nnprec_grad(_wdev(w), _packed(h, oq, r), _packed(h, oq, e), n, grad)
+    gg = grad.cpu().numpy()
+    gc = gg[0::2] + 1j * gg[1::2]
+    assert abs(gl - loss) < 1e-5 * loss
+    assert rel_err(gc[:NW1].reshape(g1.shape), g1) < 1e-4
+    assert rel_err(gc[NW1:].reshape(g2.shape), g2) < 1e-4
+
+
+def test_trained_network_cuts_gcr_steps():
+    import torch
+    from paper_2202_07388_gb300 import oq
+    dims = (8, 8, 8, 8)
+    kappa = 0.1365
+    u, a, ainv = oracle_case(dims, 0.5, 91, kappa, 1.0)
+    h = make_handle(dims, u, kappa, 1.0, oq.LINK_12)
+    # training pairs from the binary64 solver: e = D^-1 r
+    ntrain = 12
+    r = synth.make_source(dims, 92, nrhs=ntrain)
+    e = np.zeros_like(r)
+    prm = oq.SolverParams(res=1e-10, nmx=2000, nkv=16, ncy=4, nmr=5, bs=(4, 4, 4, 4), sdtype=oq.F32)
+    for k in range(ntrain):
+        psi = to_dev(np.zeros_like(r[k]))
+        rc, _ = h.sap_gcr(to_dev(r[k]), psi, prm)
+        assert rc == oq.OK
+        e[k] = from_dev(psi, r[k].shape)
+    # start: M = identity / (4 + m0) on the direct path, small random elsewhere
+    w = _weights(93, scale=0.01)
+    c0 = 1.0 / (2 * kappa)
+    wc = w[0::2] + 1j * w[1::2]
+    W1 = wc[:NW1].reshape(9, 2, 1, 4, 4)
+    W2 = wc[NW1:].reshape(9, 1, 2, 4, 4)
+    W1[0, 0, 0] += np.eye(4)
+    W2[0, 0, 0] += np.eye(4) / c0
+    wc = np.concatenate([W1.reshape(-1), W2.reshape(-1)])
+    w = np.empty(2 * wc.size, np.float32)
+    w[0::2], w[1::2] = wc.real, wc.imag
+    wd = _wdev(w)
+    rp, ep = _packed(h, oq, r), _packed(h, oq, e)
+    losses = h.nnprec_train(wd, rp, ep, ntrain, 0.01, 150)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.8 * losses[0]
+    # held-out source: flexible GCR with the trained network vs without it
+    eta = synth.make_source(dims, 99)
+    gprm = oq.SolverParams(res=1e-10, nmx=2000, nkv=16, ncy=0, sdtype=oq.F32)
+    psi0 = to_dev(np.zeros_like(eta))
+    rc0, st0 = h.sap_gcr(to_dev(eta), psi0, gprm)
+    psi1 = to_dev(np.zeros_like(eta))
+    rc1, st1 = h.nn_gcr(wd, to_dev(eta), psi1, gprm)
+    assert rc0 == oq.OK and rc1 == oq.OK
+    x = from_dev(psi1, eta.shape)
+    res = np.linalg.norm(eta - dirac.dw(u, a, x)) / np.linalg.norm(eta)
+    assert res <= 1.2e-10
+    assert st1[0]["steps"] < st0[0]["steps"]

@@ -25,12 +25,12 @@ def _oq():
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("link_fmt", [0, 1])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dw_full(case, prec, link_fmt, dagger):
     oq = _oq()
-    if prec == oq.F64 and link_fmt == oq.LINK_12:
+    if prec in (0, 4) and link_fmt == oq.LINK_12:
         pytest.skip("binary64 always uses 18-real links")
     dims, eps, seed, kappa, csw = case
     u, a, ainv = oracle_case(dims, eps, seed, kappa, csw)
@@ -48,7 +48,7 @@ def test_dw_full(case, prec, link_fmt, dagger):
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dw_hat(case, prec, dagger):
     oq = _oq()
