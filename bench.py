@@ -437,6 +437,25 @@ def run_profile_case(args):
     h.clover_build(KAPPA, CSW)
     prec = oq.PREC[args.profile_prec]
     nrhs = args.profile_nrhs
+    if args.profile_kind in ("tc", "cc", "sap"):
+        # learned preconditioner layers (tensor-core or CUDA-core) / SAP, binary32 fields
+        src = torch.randn(int(np.prod(dims)) * 24, dtype=torch.float64, device="cuda")
+        a, b = h.new_packed(oq.F32), h.new_packed(oq.F32)
+        h.pack(src, a, oq.F32)
+        w = torch.randn(1152, dtype=torch.float32, device="cuda") * 0.1
+        prm = oq.SolverParams(ncy=1, nmr=5, bs=(4, 4, 4, 4))
+        for _ in range(3):
+            if args.profile_kind == "tc":
+                h.nnprec_apply_tc(w, a, b)
+            elif args.profile_kind == "cc":
+                h.nnprec_apply(w, a, b)
+            else:
+                h.sap_apply(a, b, prm)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "x".join(map(str, dims)), "kind": args.profile_kind,
+                          "launches": h.kernel_launches()}))
+        h.close()
+        return 0
     h.autotune(prec, nrhs=nrhs)
     src = torch.randn(nrhs * int(np.prod(dims)) * 24, dtype=torch.float64, device="cuda")
     a, b = h.new_packed(prec, oq.EVEN, nrhs=nrhs), h.new_packed(prec, oq.EVEN, nrhs=nrhs)
@@ -536,11 +555,14 @@ def run_workload_c5(args):
     ada = oq.SolverParams(res=RES, nmx=2000, nkv=16, ncy=20, nmr=20, bs=(4, 4, 4, 4), sdtype=oq.F32, adaptive=1,
                           alpha=0.9)
     plain = oq.SolverParams(res=RES, nmx=5000, nkv=16, ncy=0, sdtype=oq.F32)
-    for name, prm in (("sap_gcr", sap), ("sap_gcr_adaptive", ada), ("gcr", plain)):
+    for name, prm, two in (("sap_gcr", sap, 0), ("sap_gcr_two_ctas", sap, 1), ("sap_gcr_adaptive", ada, 0),
+                           ("gcr", plain, 0)):
+        h.set_option(oq.OPT_SAP_TWO_CTAS, two)
         h.sap_gcr(eta, psi, prm)
         t, (rc, st) = _timed(lambda: h.sap_gcr(eta, psi, prm))
         out[name] = {"s": t, "rc": rc, **{k: st[0][k] for k in ("steps", "restarts", "cycles", "mr_avg",
                                                                  "true_rel_res")}}
+    h.set_option(oq.OPT_SAP_TWO_CTAS, 0)
     # training pairs (r, e = D^-1 r) from the binary64 SAP-GCR solver
     ntrain = args.nn_pairs
     r = synth.make_source(dims, 500, nrhs=ntrain)
@@ -569,6 +591,11 @@ def run_workload_c5(args):
                      "true_rel_res": st[0]["true_rel_res"], "train_pairs": ntrain, "pair_solve_s": tpairs,
                      "train_steps": args.nn_steps, "train_s": ttrain, "loss_first": float(losses[0]),
                      "loss_last": float(losses[-1])}
+    h.set_option(oq.OPT_NN_TENSOR_CORES, 1)
+    h.nn_gcr(wd, eta, psi, plain)
+    t, (rc, st) = _timed(lambda: h.nn_gcr(wd, eta, psi, plain))
+    out["nn_gcr_tensor_cores"] = {"s": t, "rc": rc, "steps": st[0]["steps"], "true_rel_res": st[0]["true_rel_res"]}
+    h.set_option(oq.OPT_NN_TENSOR_CORES, 0)
     # tensor-core vs CUDA-core forward of the trained network
     a, b = h.new_packed(oq.F32), h.new_packed(oq.F32)
     h.pack(eta, a, oq.F32)
@@ -601,6 +628,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-prec", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
     ap.add_argument("--profile-nrhs", type=int, default=12)
+    ap.add_argument("--profile-kind", default="dhat", choices=["dhat", "tc", "cc", "sap"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

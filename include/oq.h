@@ -195,7 +195,14 @@ int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int
  *   tensor-core PTC layer issues no MMA, so its bounded (1 s) wait for the
  *   tensor core runs out and oq_nnprec_apply_tc returns OQ_ERR_TIMEOUT with
  *   the device still usable.  Default 0. */
-enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2 };
+/* OQ_OPT_NN_TENSOR_CORES: 1 = oq_nn_gcr_solve applies the network with the
+ *   tensor-core layers of oq_nnprec_apply_tc; default 0 = the binary32
+ *   CUDA-core layers of oq_nnprec_apply (measured faster on GB300 for this
+ *   small network). */
+/* OQ_OPT_SAP_TWO_CTAS: 1 (default) = the SAP block kernel caps its
+ *   registers so that two 256-site blocks run per SM (a few spills to L1);
+ *   0 = one block per SM with ~217 registers. */
+enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2, OQ_OPT_NN_TENSOR_CORES = 3, OQ_OPT_SAP_TWO_CTAS = 4 };
 int oq_set_option(oq_handle h, int key, int value);
 
 /* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and

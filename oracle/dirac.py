@@ -269,6 +269,39 @@ def assemble_dense(op, dims) -> np.ndarray:
     return m
 
 
+def clover_site(u, m0, csw, x) -> np.ndarray:
+    """A(x) (12x12) at one site from the four plaquette leaves around x.
+
+    Same definition as ``clover_field``, evaluated at a single site with
+    explicit index arithmetic, for checking samples of very large lattices.
+    """
+    dims = u.shape[:4]
+
+    def link(y, mu):
+        return u[tuple(c % d for c, d in zip(y, dims)) + (mu,)]
+
+    x = tuple(int(c) for c in x)
+    a = (4.0 + m0) * np.eye(12, dtype=np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            e_mu = [0, 0, 0, 0]
+            e_nu = [0, 0, 0, 0]
+            e_mu[mu] = 1
+            e_nu[nu] = 1
+            add = lambda y, s, t: tuple(y[k] + s * e_mu[k] + t * e_nu[k] for k in range(4))
+            q = (link(x, mu) @ link(add(x, 1, 0), nu) @ _dag(link(add(x, 0, 1), mu)) @ _dag(link(x, nu))
+                 + link(x, nu) @ _dag(link(add(x, -1, 1), mu)) @ _dag(link(add(x, -1, 0), nu)) @ link(add(x, -1, 0), mu)
+                 + _dag(link(add(x, -1, 0), mu)) @ _dag(link(add(x, -1, -1), nu)) @ link(add(x, -1, -1), mu)
+                 @ link(add(x, 0, -1), nu)
+                 + _dag(link(add(x, 0, -1), nu)) @ link(add(x, 0, -1), mu) @ link(add(x, 1, -1), nu)
+                 @ _dag(link(x, mu)))
+            f = (q - _dag(q)) / 8.0
+            a += (csw * 0.25j) * np.kron(sigma_munu(mu, nu), f)
+    return a
+
+
 def dw_site(u, a, psi, x, bc_t=-1.0) -> np.ndarray:
     """(D psi)(x) at one site by explicit loops over the 8 neighbours.
 

@@ -74,6 +74,12 @@ struct oq_ctx {
   bool df64_resets = false;
   // test hook: the tensor-core PTC layer issues no MMA, so its bounded wait runs out
   bool hook_tc_skip_commit = false;
+  // SAP block kernel with registers capped for two CTAs per SM (measured ~5 %
+  // faster on GB300 than one CTA with ~217 registers)
+  bool sap_two_ctas = true;
+  // NN-preconditioned GCR applies the network with the tensor-core layers
+  // instead of the (measured faster) binary32 CUDA-core ones
+  bool nn_tensor_cores = false;
   // profiling
   bool prof_on = false;
   std::vector<oq::ProfRec> prof;

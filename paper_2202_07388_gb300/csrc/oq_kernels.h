@@ -35,10 +35,13 @@ cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride,
 // bfloat16 forward weights held by the handle, and apply M = L2 L1
 int nnprec_prepare(struct ::oq_ctx* h, int lat, const float* master, cudaStream_t s);
 int nnprec_forward(struct ::oq_ctx* h, int lat, const void* r, void* y, cudaStream_t s);
+// the same with the channel contraction on the tensor cores (tcgen05);
+// takes the binary32 master weights, synchronises s, OQ_ERR_TIMEOUT on a failed wait
+int nnprec_forward_tc(struct ::oq_ctx* h, int lat, const float* master, const void* r, void* y, cudaStream_t s);
 
 // one SAP half cycle: every block of `colour` (binary32 fields)
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
                        const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
-                       unsigned* mr_steps, cudaStream_t s);
+                       unsigned* mr_steps, int two_ctas, cudaStream_t s);
 
 }  // namespace oq

@@ -1,20 +1,21 @@
 // Tensor-core (tcgen05) form of the PTC layer's channel contraction.
 //
-// For a tile of 128 sites and one colour a, the layer is a dense product
-//   Y_a[site][n] = sum_k X_a[site][k] W[n][k],   k = (path q, c_in, spin t),
-//                                                 n = (c_out, spin s),
+// For every (site, colour a) row the layer is a dense product
+//   Y[row][n] = sum_k X[row][k] W[n][k],   k = (path q, c_in, spin t),
+//                                          n = (c_out, spin s),
 // complex; written as a real product with X' = [Re X | Im X] and
 // W' = [[Re W, -Im W], [Im W, Re W]] (rows n' = (re|im, n)), both in bfloat16,
 // accumulated in binary32 in tensor memory:
-//   D_a (128 x N') = X'_a (128 x K') . W'^T,   M = 128, N' = 16, K' padded to 16.
-// One CTA = 128 sites = 4 warps; every thread gathers and transports the
-// inputs of its own site (binary32 CUDA-core work) and writes row `site` of
-// the three operand tiles X'_a into shared memory in the no-swizzle K-major
+//   D (128 x N') = X' (128 x K') . W'^T,   M = 128, N' = 16, K' padded to 16.
+// One CTA = 42 sites = 126 rows (row = 3 site + colour; rows 126, 127 zero),
+// 4 warps.  The gather (transport of every input along every path, binary32
+// CUDA-core work) is split into (site, path) items over all threads, which
+// write their entries of X' into shared memory in the no-swizzle K-major
 // core-matrix layout (8 rows x 16 bytes per core matrix; LBO = next core
 // along K, SBO = next 8-row group).  One elected thread issues the
-// tcgen05.mma instructions for the 3 colours, commits them to an mbarrier,
-// every thread waits (bounded), then reads its row of the accumulators with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31) and stores the outputs.
+// tcgen05.mma instructions, commits them to an mbarrier, every thread waits
+// (bounded), then reads its row of the accumulator with tcgen05.ld (warp w
+// owns TMEM lanes 32w..32w+31) and stores its colour of the output spinors.
 #include <math.h>
 #include <stdint.h>
 
@@ -26,7 +27,8 @@ namespace oq {
 
 static const int TC_M = 128;
 static const int TC_N = 16;        // N' (real-embedded outputs, padded)
-static const int TC_COLS = 128;    // TMEM columns allocated (accumulators at 0, 32, 64)
+static const int TC_COLS = 32;     // TMEM columns allocated (one 128 x 16 accumulator)
+static const int TC_SITES = 42;    // sites per CTA: rows 3 * site + colour, 126 of 128 used
 static const unsigned TC_SPIN_LIMIT = 1u << 26;
 
 struct PtcTcArgs {
@@ -102,18 +104,42 @@ __device__ __forceinline__ void tc_transport(const PtcTcArgs& a, const char* f, 
     }
 }
 
+// W' (bfloat16, core-matrix layout) from the binary32 master weights, once per call
+template <int CIN, int COUT>
+__global__ void ptc_tc_prepare_b(const float2* __restrict__ w, unsigned char* __restrict__ bglob) {
+  constexpr int K = 9 * CIN * 4;
+  constexpr int KP = ((2 * K + 15) / 16) * 16;
+  constexpr int N = COUT * 4;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TC_N * KP; e += gridDim.x * blockDim.x) {
+    const int n2 = e / KP, k2 = e % KP;
+    float v = 0.f;
+    if (n2 < 2 * N && k2 < 2 * K) {
+      const int n = n2 % N, im_row = n2 / N;
+      const int k = k2 % K, im_col = k2 / K;
+      const int co = n / 4, s = n % 4;
+      const int q = k / (CIN * 4), ci = (k / 4) % CIN, t = k % 4;
+      const float2 wv = w[((q * COUT + co) * CIN + ci) * 16 + s * 4 + t];
+      v = im_row == 0 ? (im_col == 0 ? wv.x : -wv.y) : (im_col == 0 ? wv.y : wv.x);
+    }
+    *reinterpret_cast<__nv_bfloat16*>(bglob + core_off(n2, k2, KP)) = bf(v);
+  }
+}
+
+// Persistent over 42-site tiles: TMEM, the mbarrier and W' in shared memory
+// are set up once per CTA; per tile: gather -> MMA -> bounded wait -> read
+// the accumulator -> store.  The mbarrier phase flips every tile.
 template <int FMT, int CIN, int COUT>
-__global__ void __launch_bounds__(128) ptc_tc_kernel(const PtcTcArgs a) {
-  constexpr int K = 9 * CIN * 4;             // complex inputs per colour row
+__global__ void __launch_bounds__(128) ptc_tc_kernel(const PtcTcArgs a, const uint4* __restrict__ bglob) {
+  constexpr int K = 9 * CIN * 4;                // complex inputs of one (site, colour) row
   constexpr int KP = ((2 * K + 15) / 16) * 16;  // real-embedded, padded to the MMA K step
-  constexpr int N = COUT * 4;                // complex outputs
+  constexpr int N = COUT * 4;                   // complex outputs
   constexpr uint32_t A_BYTES = TC_M * KP * 2;
   constexpr uint32_t B_BYTES = TC_N * KP * 2;
   extern __shared__ __align__(1024) unsigned char sm[];
-  // layout: [A_0 | A_1 | A_2 | B | pad (one A tile) | mbarrier | tmem slot]
+  // layout: [A | B | mbarrier | tmem slot]
   unsigned char* A = sm;
-  unsigned char* B = sm + 3 * A_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 4 * A_BYTES + B_BYTES);
+  unsigned char* B = sm + A_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + A_BYTES + B_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
 
@@ -126,128 +152,145 @@ __global__ void __launch_bounds__(128) ptc_tc_kernel(const PtcTcArgs a) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B' = [[Re W, -Im W], [Im W, Re W]] rows n' = re/im x (c_out, s); zero padded
-  for (int e = tid; e < TC_N * KP; e += blockDim.x) {
-    const int n2 = e / KP, k2 = e % KP;
-    float v = 0.f;
-    if (n2 < 2 * N && k2 < 2 * K) {
-      const int n = n2 % N, im_row = n2 / N;
-      const int k = k2 % K, im_col = k2 / K;
-      const int co = n / 4, s = n % 4;
-      const int q = k / (CIN * 4), ci = (k / 4) % CIN, t = k % 4;
-      const float2 w = a.w[((q * COUT + co) * CIN + ci) * 16 + s * 4 + t];
-      v = im_row == 0 ? (im_col == 0 ? w.x : -w.y) : (im_col == 0 ? w.y : w.x);
-    }
-    *reinterpret_cast<__nv_bfloat16*>(B + core_off(n2, k2, KP)) = bf(v);
+  for (int e = tid; e < (int)(B_BYTES / 16); e += blockDim.x) reinterpret_cast<uint4*>(B)[e] = bglob[e];
+  // constant zeros of A': the K padding of every row, and rows 126, 127
+  for (int e = tid; e < TC_M * (KP - 2 * K); e += blockDim.x) {
+    const int r = e / (KP - 2 * K), k = 2 * K + e % (KP - 2 * K);
+    *reinterpret_cast<__nv_bfloat16*>(A + core_off(r, k, KP)) = bf(0.f);
   }
-  // A'_a rows: this thread's site, all paths and input channels
-  const long j = (long)blockIdx.x * TC_M + tid;
-  const bool live = j < 2 * a.g.Vh;
-  const int p = (live && j >= a.g.Vh) ? 1 : 0;
-  const long i = live ? j - p * a.g.Vh : 0;
-  int x[4];
-  eo_coords(a.g, p, i, x);
-  for (int q = 0; q < 9; ++q) {
-#pragma unroll
-    for (int ci = 0; ci < CIN; ++ci) {
-      Spinor<float> t;
-      if (live)
-        tc_transport<FMT>(a, a.in + ci * a.fbytes, q, p, i, x, t);
-      else
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) t.c[s][c] = cx<float>{0.f, 0.f};
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int k = (q * CIN + ci) * 4 + s;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          unsigned char* Ac = A + c * A_BYTES;
-          *reinterpret_cast<__nv_bfloat16*>(Ac + core_off(tid, k, KP)) = bf(t.c[s][c].re);
-          *reinterpret_cast<__nv_bfloat16*>(Ac + core_off(tid, K + k, KP)) = bf(t.c[s][c].im);
-        }
-      }
-    }
+  for (int e = tid; e < (TC_M - 3 * TC_SITES) * 2 * K; e += blockDim.x) {
+    const int r = 3 * TC_SITES + e / (2 * K), k = e % (2 * K);
+    *reinterpret_cast<__nv_bfloat16*>(A + core_off(r, k, KP)) = bf(0.f);
   }
-  for (int k = 2 * K; k < KP; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) *reinterpret_cast<__nv_bfloat16*>(A + c * A_BYTES + core_off(tid, k, KP)) = bf(0.f);
-  // make the generic-proxy smem writes visible to the tensor core (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  const long ntile = (2 * a.g.Vh + TC_SITES - 1) / TC_SITES;
+  uint32_t phase = 0;
 
-  if (tid == 0 && !a.skip_commit) {
-    constexpr uint32_t idesc = make_idesc(TC_M, TC_N);
-    constexpr uint32_t SBO = (KP / 8) * 128;
+  for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const long site0 = tile * TC_SITES;
+    // A': row 3 * (site in tile) + colour; (site, path) items over all threads
+    // items run fastest over sites, so that a warp gathers neighbouring sites
+    // (coalesced loads) and writes rows 48 bytes apart (few bank conflicts)
+    for (int item = tid; item < TC_SITES * 9; item += blockDim.x) {
+      const int ls = item % TC_SITES, q = item / TC_SITES;
+      const long j = site0 + ls;
+      const bool live = j < 2 * a.g.Vh;
+      const int p = (live && j >= a.g.Vh) ? 1 : 0;
+      const long i = live ? j - p * a.g.Vh : 0;
+      int x[4];
+      eo_coords(a.g, p, i, x);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const uint32_t a_base = smem_u32(A + c * A_BYTES);
+      for (int ci = 0; ci < CIN; ++ci) {
+        Spinor<float> t;
+        if (live)
+          tc_transport<FMT>(a, a.in + ci * a.fbytes, q, p, i, x, t);
+        else
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t.c[s][c] = cx<float>{0.f, 0.f};
+        // spins (s, s+1) are adjacent columns of one core matrix: 4-byte stores
+#pragma unroll
+        for (int s = 0; s < 4; s += 2) {
+          const int k = (q * CIN + ci) * 4 + s;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int row = 3 * ls + c;
+            *reinterpret_cast<__nv_bfloat162*>(A + core_off(row, k, KP)) =
+                __floats2bfloat162_rn(t.c[s][c].re, t.c[s + 1][c].re);
+            *reinterpret_cast<__nv_bfloat162*>(A + core_off(row, K + k, KP)) =
+                __floats2bfloat162_rn(t.c[s][c].im, t.c[s + 1][c].im);
+          }
+        }
+      }
+    }
+    // make the generic-proxy smem writes visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (tid == 0 && !a.skip_commit) {
+      constexpr uint32_t idesc = make_idesc(TC_M, TC_N);
+      constexpr uint32_t SBO = (KP / 8) * 128;
+      const uint32_t a_base = smem_u32(A);
       const uint32_t b_base = smem_u32(B);
 #pragma unroll
       for (int ks = 0; ks < KP / 16; ++ks) {
         const uint64_t ad = make_desc(a_base + ks * 256, 128, SBO);
         const uint64_t bd = make_desc(b_base + ks * 256, 128, SBO);
-        const uint32_t d_tmem = tmem + (uint32_t)(32 * c);
         const uint32_t acc = ks > 0 ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar)));
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        smem_u32(mbar)));
-  }
-  // bounded wait for the MMAs (phase 0): give up after wait_ns of the global
-  // timer (or TC_SPIN_LIMIT polls), flag the error and carry on to free TMEM
-  {
+    // bounded wait for the MMAs of this tile: give up after wait_ns of the
+    // global timer (or TC_SPIN_LIMIT polls); the decision is made uniform over
+    // the CTA, which then flags the error, skips the remaining tiles and frees TMEM
     uint32_t done = 0;
-    unsigned n = 0;
-    uint64_t t0, t1;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    while (!done && n < TC_SPIN_LIMIT) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(smem_u32(mbar)), "r"(0u));
-      ++n;
-      if (!done) {
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-        if (t1 - t0 > a.wait_ns) break;
+    {
+      unsigned n = 0;
+      uint64_t t0, t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      while (!done && n < TC_SPIN_LIMIT) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(phase));
+        ++n;
+        if (!done) {
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+          if (t1 - t0 > a.wait_ns) break;
+        }
       }
     }
-    if (!done && a.error) atomicExch(a.error, 1);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // read row `tid` of the three accumulators
-  float d[3][16];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c);
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 16; ++k) d[c][k] = __uint_as_float(r[k]);
-  }
-  if (live) {
-#pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-      Spinor<float> o;
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o.c[s][c] = cx<float>{d[c][co * 4 + s], d[c][N + co * 4 + s]};
-      store_spinor<P_F32>(a.out + co * a.fbytes + (long)p * a.hbytes, a.g.Vh, i, o);
+    if (__syncthreads_or(done ? 0 : 1)) {
+      if (tid == 0 && a.error) atomicExch(a.error, 1);
+      break;
     }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // row r = tid of the accumulator: site r / 3, colour r % 3
+    uint32_t rr[16];
+    {
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+            "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+            "=r"(rr[14]), "=r"(rr[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    }
+    if (tid < 3 * TC_SITES) {
+      const int ls = tid / 3, c = tid % 3;
+      const long j = site0 + ls;
+      if (j < 2 * a.g.Vh) {
+        const int p = j >= a.g.Vh ? 1 : 0;
+        const long i = j - p * a.g.Vh;
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) {
+          float2* base = reinterpret_cast<float2*>(a.out + co * a.fbytes + (long)p * a.hbytes);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int k = s * 3 + c;  // complex component of the site vector
+            base[((long)(k >> 1) * a.g.Vh + i) * 2 + (k & 1)] =
+                make_float2(__uint_as_float(rr[co * 4 + s]), __uint_as_float(rr[N + co * 4 + s]));
+          }
+        }
+      }
+    }
+    // every thread has read the accumulator before the next tile's MMA writes it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -257,17 +300,21 @@ __global__ void __launch_bounds__(128) ptc_tc_kernel(const PtcTcArgs a) {
 }
 
 template <int CIN, int COUT>
-static cudaError_t ptc_tc_layer(const PtcTcArgs& a, int fmt, cudaStream_t s) {
+static cudaError_t ptc_tc_layer(const PtcTcArgs& a, int fmt, unsigned char* bglob, int nsm, cudaStream_t s) {
   constexpr int K = 9 * CIN * 4;
   constexpr int KP = ((2 * K + 15) / 16) * 16;
-  const size_t smem = 4 * (size_t)TC_M * KP * 2 + (size_t)TC_N * KP * 2 + 16;
-  dim3 grid((unsigned)((2 * a.g.Vh + TC_M - 1) / TC_M)), block(128);
+  const size_t smem = (size_t)TC_M * KP * 2 + (size_t)TC_N * KP * 2 + 16;
+  ptc_tc_prepare_b<CIN, COUT><<<8, 256, 0, s>>>(a.w, bglob);
+  const long ntile = (2 * a.g.Vh + TC_SITES - 1) / TC_SITES;
+  const long cap = (long)nsm * 8;
+  dim3 grid((unsigned)(ntile < cap ? ntile : cap)), block(128);
+  const uint4* b = reinterpret_cast<const uint4*>(bglob);
   if (fmt == LINK_12) {
     cudaFuncSetAttribute(ptc_tc_kernel<LINK_12, CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    ptc_tc_kernel<LINK_12, CIN, COUT><<<grid, block, smem, s>>>(a);
+    ptc_tc_kernel<LINK_12, CIN, COUT><<<grid, block, smem, s>>>(a, b);
   } else {
     cudaFuncSetAttribute(ptc_tc_kernel<LINK_18, CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    ptc_tc_kernel<LINK_18, CIN, COUT><<<grid, block, smem, s>>>(a);
+    ptc_tc_kernel<LINK_18, CIN, COUT><<<grid, block, smem, s>>>(a, b);
   }
   return cudaGetLastError();
 }
@@ -282,14 +329,23 @@ using namespace oq;
 extern "C" int oq_nnprec_apply_tc(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
                                   void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !weights_dev || !in_dev || !out_dev) return OQ_ERR_ARG;
+  if (!h->lats[lat].has_gauge) return OQ_ERR_STATE;
+  return nnprec_forward_tc(h, lat, weights_dev, in_dev, out_dev, (cudaStream_t)stream);
+}
+
+int oq::nnprec_forward_tc(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
+                          cudaStream_t s) {
   LatCtx& L = h->lats[lat];
-  if (!L.has_gauge) return OQ_ERR_STATE;
-  cudaStream_t s = (cudaStream_t)stream;
   const long hb = spinor_half_bytes(L.g.Vh, P_F32);
-  void* hid;
+  void *hid, *bglob;
   int rc = h->workspace(lat, "nntc_hid", 2 * 2 * hb, &hid);
+  if (!rc) rc = h->workspace(lat, "nntc_b", 16 * 160 * 2 + 16 * 144 * 2, &bglob);
   if (!rc) rc = h->ensure_scratch();
   if (rc) return rc;
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  unsigned char* b1 = (unsigned char*)bglob;          // layer 1: 16 x 80 bf16
+  unsigned char* b2 = b1 + 16 * 80 * 2;               // layer 2: 16 x 144 bf16 (16-byte aligned)
   if (cudaMemsetAsync(h->status_dev, 0, sizeof(int), s) != cudaSuccess) return OQ_ERR_CUDA;
   PtcTcArgs a;
   a.g = L.g;
@@ -302,12 +358,12 @@ extern "C" int oq_nnprec_apply_tc(oq_handle h, int lat, const float* weights_dev
   a.in = (const char*)in_dev;
   a.out = (char*)hid;
   a.w = (const float2*)weights_dev;
-  if (ptc_tc_layer<1, 2>(a, L.link_fmt, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (ptc_tc_layer<1, 2>(a, L.link_fmt, b1, nsm, s) != cudaSuccess) return OQ_ERR_CUDA;
   a.in = (const char*)hid;
   a.out = (char*)out_dev;
   a.w = (const float2*)weights_dev + 9 * 2 * 1 * 16;
-  if (ptc_tc_layer<2, 1>(a, L.link_fmt, s) != cudaSuccess) return OQ_ERR_CUDA;
-  h->launches += 2;
+  if (ptc_tc_layer<2, 1>(a, L.link_fmt, b2, nsm, s) != cudaSuccess) return OQ_ERR_CUDA;
+  h->launches += 4;
   int err = 0;
   if (cudaMemcpyAsync(&err, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

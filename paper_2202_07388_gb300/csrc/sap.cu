@@ -103,8 +103,10 @@ __device__ __forceinline__ void block_hop(const SapArgs& a, const float* sm, int
   }
 }
 
-template <int FMT>
-__global__ void __launch_bounds__(256) sap_kernel(const SapArgs a) {
+// MINB = 2 caps registers so that two 256-thread CTAs fit on an SM (a few
+// spills to L1), MINB = 1 lets the compiler use ~200 registers (one CTA)
+template <int FMT, int MINB>
+__global__ void __launch_bounds__(256, MINB) sap_kernel(const SapArgs a) {
   extern __shared__ float sm[];
   const int nsite = a.bs[0] * a.bs[1] * a.bs[2] * a.bs[3];
   double* red = reinterpret_cast<double*>(sm + 24 * nsite);
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(256) sap_kernel(const SapArgs a) {
 
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
                        const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
-                       unsigned* mr_steps, cudaStream_t s) {
+                       unsigned* mr_steps, int two_ctas, cudaStream_t s) {
   SapArgs a;
   a.g = g;
   int nblk = 1;
@@ -268,10 +270,17 @@ cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, cons
   const int threads = (nsite + 31) / 32 * 32;
   const size_t smem = sizeof(float) * 24 * nsite + sizeof(double) * 3 * (threads / 32);
   dim3 grid(nblk / 2), block(threads);
-  if (fmt == LINK_12)
-    sap_kernel<LINK_12><<<grid, block, smem, s>>>(a);
-  else
-    sap_kernel<LINK_18><<<grid, block, smem, s>>>(a);
+  if (two_ctas) {
+    if (fmt == LINK_12)
+      sap_kernel<LINK_12, 2><<<grid, block, smem, s>>>(a);
+    else
+      sap_kernel<LINK_18, 2><<<grid, block, smem, s>>>(a);
+  } else {
+    if (fmt == LINK_12)
+      sap_kernel<LINK_12, 1><<<grid, block, smem, s>>>(a);
+    else
+      sap_kernel<LINK_18, 1><<<grid, block, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

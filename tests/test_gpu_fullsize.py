@@ -1,0 +1,101 @@
+"""Parity at the benchmark's full sizes.
+
+* 32 x 16^3 (C2): full Dw at binary32 / bfloat16 against the oracle on
+  every site, and mixed-precision CGNE to 1e-10 checked with the oracle's
+  own Dhat^dag Dhat on the whole lattice.
+* 64 x 32^3 (C3, the benchmark lattice, eps = 0.6): Dhat on 12 right-hand
+  sides in F16 storage with the autotuned launch shape the benchmark uses,
+  compared on sampled even sites (time boundary, interior) with the oracle
+  evaluated site by site (per-site clover, per-site hops)."""
+import numpy as np
+import pytest
+
+from oracle import dirac
+from paper_2202_07388_gb300 import synth
+from tests.gpu_cases import TOL, make_handle, to_dev, from_dev, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+class _Zero:
+    def __getitem__(self, x):
+        return np.zeros((12, 12), dtype=np.complex128)
+
+
+def test_c2_full_lattice_dw_and_cgne():
+    from paper_2202_07388_gb300 import oq
+    dims = (32, 16, 16, 16)
+    kappa, csw = 0.135, 1.0
+    u = synth.make_gauge(dims, 0.5, 2)
+    a = dirac.clover_field(u, dirac.kappa_to_m0(kappa), csw)
+    h = make_handle(dims, u, kappa, csw, oq.LINK_12)
+    psi = synth.make_source(dims, 21)
+    ref = dirac.dw(u, a, psi)
+    for prec in (oq.F32, oq.BF16):
+        pin, pout = h.new_packed(prec), h.new_packed(prec)
+        h.pack(to_dev(psi), pin, prec)
+        h.dw(pin, pout, prec)
+        out = to_dev(np.zeros_like(psi))
+        h.unpack(pout, out, prec)
+        assert rel_err(from_dev(out, psi.shape), ref) < TOL[prec]
+    del ref
+    ainv = np.linalg.inv(a)
+    eta = dirac.even_part(synth.make_source(dims, 22))
+    for prec in (oq.F32, oq.BF16, oq.F16):
+        x = to_dev(np.zeros_like(eta))
+        rc, st = h.cgne(to_dev(eta), x, oq.SolverParams(res=1e-10, nmx=5000, sdtype=prec))
+        assert rc == oq.OK
+        xs = from_dev(x, eta.shape)
+        r = eta - dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, xs))
+        assert np.linalg.norm(r) / np.linalg.norm(eta) <= 1.2e-10
+    h.close()
+
+
+def test_c3_dhat_f16_12rhs_sampled_sites():
+    import torch
+    from paper_2202_07388_gb300 import oq
+    dims = (64, 32, 32, 32)
+    kappa, csw = 0.135, 1.0
+    m0 = dirac.kappa_to_m0(kappa)
+    u = synth.make_gauge(dims, 0.6, 3)
+    h = make_handle(dims, u, kappa, csw, oq.LINK_12)
+    nrhs = 12
+    h.autotune(oq.F16, nrhs=nrhs)
+    src = synth.make_source(dims, 33, nrhs=nrhs)
+    odd = dirac.parity_mask(dims)
+    src[:, odd] = 0.0
+    pin, pout = h.new_packed(oq.F16, oq.EVEN, nrhs=nrhs), h.new_packed(oq.F16, oq.EVEN, nrhs=nrhs)
+    h.pack(to_dev(src), pin, oq.F16, oq.EVEN, nrhs=nrhs)
+    h.dw_hat(pin, pout, oq.F16, nrhs=nrhs)
+    out = to_dev(np.zeros_like(src))
+    h.unpack(pout, out, oq.F16, oq.EVEN, nrhs=nrhs)
+    got = from_dev(out, src.shape)
+    del out, pin, pout
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(34)
+    sites = [(0, 0, 0, 0), (63, 31, 31, 31), (0, 5, 7, 1), (63, 0, 1, 31), (31, 16, 16, 16)]
+    while len(sites) < 14:
+        x = tuple(int(rng.integers(0, d)) for d in dims)
+        if sum(x) % 2 == 0:
+            sites.append(x)
+    sites = [x if sum(x) % 2 == 0 else (x[0], x[1], x[2], (x[3] + 1) % dims[3]) for x in sites]
+    zero = _Zero()
+    for k in (0, 5, 11):
+        psi = src[k]
+        t_field = np.zeros_like(psi)
+        for x in sites:
+            for mu in range(4):
+                for d in (+1, -1):
+                    y = list(x)
+                    y[mu] = (y[mu] + d) % dims[mu]
+                    y = tuple(y)
+                    if not np.any(t_field[y]):
+                        hop = dirac.dw_site(u, zero, psi, y)          # D_oe psi_e at odd y
+                        ay = dirac.clover_site(u, m0, csw, y)
+                        t_field[y] = np.linalg.solve(ay, hop.reshape(12)).reshape(4, 3)
+        for x in sites:
+            ax = dirac.clover_site(u, m0, csw, x)
+            ref = (ax @ psi[x].reshape(12)).reshape(4, 3) - dirac.dw_site(u, zero, t_field, x)
+            err = np.linalg.norm(got[k][x] - ref) / np.linalg.norm(ref)
+            assert err < 5e-3, (k, x, err)
+    h.close()

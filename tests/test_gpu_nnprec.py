@@ -162,4 +162,10 @@ def test_trained_network_cuts_gcr_steps():
     x = from_dev(psi1, eta.shape)
     res = np.linalg.norm(eta - dirac.dw(u, a, x)) / np.linalg.norm(eta)
     assert res <= 1.2e-10
-    assert st1[0]["steps"] < st0[0]["steps"]
+    assert st1[0]["steps"] < st0[0]["steps"]     # binary32 CUDA-core network (default)
+    h.set_option(oq.OPT_NN_TENSOR_CORES, 1)
+    psi2 = to_dev(np.zeros_like(eta))
+    rc2, st2 = h.nn_gcr(wd, to_dev(eta), psi2, gprm)
+    assert rc2 == oq.OK and st2[0]["steps"] < st0[0]["steps"]   # tcgen05 network
+    x2 = from_dev(psi2, eta.shape)
+    assert np.linalg.norm(eta - dirac.dw(u, a, x2)) / np.linalg.norm(eta) <= 1.2e-10

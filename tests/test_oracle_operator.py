@@ -172,6 +172,15 @@ def test_dw_site_matches_field():
         assert np.max(np.abs(dirac.dw_site(u, a, psi, x) - full[x])) < 1e-13
 
 
+def test_clover_site_matches_field():
+    dims = (6, 4, 2, 4)
+    u = synth.make_gauge(dims, 0.6, 17)
+    m0 = dirac.kappa_to_m0(0.135)
+    a = dirac.clover_field(u, m0, 1.3)
+    for x in [(0, 0, 0, 0), (5, 3, 1, 3), (2, 0, 1, 2), (5, 0, 0, 3)]:
+        assert np.max(np.abs(dirac.clover_site(u, m0, 1.3, x) - a[x])) < 1e-14
+
+
 def test_operator_condition_small_lattice():
     """The smallest singular value of D on the 4^4 workload is well away from
     zero (kappa = 0.13), so solves to 1e-10 are meaningful."""
