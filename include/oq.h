@@ -179,10 +179,14 @@ int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, 
  * on handle-owned scratch fields with CUDA events, and keep the fastest per
  * pass in the handle; every later stencil launch of that variant, including
  * those inside the solvers, uses it.  Synchronises `stream`.
- * oq_tune_get reports the chosen shape and its time per launch (mode 0 = Dw,
- * 1 = Dhat pass 1, 2 = Dhat pass 2); OQ_ERR_STATE if not tuned. */
+ * For binary32-arithmetic kernels on 12-real links the tuner also tries the
+ * 18-real copy the handle keeps (fewer instructions, more bytes) and keeps
+ * the faster format.  oq_tune_get reports the chosen shape, its time per
+ * launch and (link_fmt, nullable) the link format (mode 0 = Dw, 1 = Dhat
+ * pass 1, 2 = Dhat pass 2); OQ_ERR_STATE if not tuned. */
 int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* stream);
-int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms);
+int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
+                int* link_fmt);
 
 /* Handle options (no counterpart in the paper).
  * OQ_OPT_DF64_RESETS: 1 = the intermediate CGNE reset steps of a

@@ -92,8 +92,16 @@ extern "C" int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int li
   if (rc) return rc;
   rc = h->alloc(&L.u32, n32);
   if (rc) return rc;
+  // with 12-real links keep an 18-real binary32 copy as well: the tuner may
+  // prefer it where the stencil is instruction-bound (many right-hand sides)
+  if (link_fmt == OQ_LINK_12) {
+    rc = h->alloc(&L.u32_18, sizeof(float) * 2 * 4 * 18 * L.g.Vh);
+    if (rc) return rc;
+  }
   L.link_fmt = link_fmt;
-  if (pack_links(L.g, U_dev, (double*)L.u64.p, L.u32.p, link_fmt, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (pack_links(L.g, U_dev, (double*)L.u64.p, L.u32.p, link_fmt, link_fmt == OQ_LINK_12 ? L.u32_18.p : nullptr,
+                 s) != cudaSuccess)
+    return OQ_ERR_CUDA;
   L.has_gauge = true;
   L.has_clover = false;
   return OQ_OK;

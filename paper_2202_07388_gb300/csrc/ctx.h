@@ -26,6 +26,7 @@ struct LatCtx {
   bool has_gauge = false, has_clover = false;
   double kappa = 0.0, csw = 0.0;
   DevBuf u64, u32, a64, a32, i64, i32;
+  DevBuf u32_18;  // 18-real binary32 copy kept next to 12-real links
   std::map<std::string, DevBuf> ws;
 };
 
@@ -67,6 +68,7 @@ struct oq_ctx {
   // launch shapes
   std::map<oq::TuneKey, std::pair<int, int>> tuned;
   std::map<oq::TuneKey, float> tuned_ms;
+  std::map<oq::TuneKey, int> tuned_fmt;  // binary32 link format picked by the tuner
   // kernels launched by this handle so far
   long long launches = 0;
   // CGNE: intermediate reset residuals in double-float arithmetic (off by
@@ -194,6 +196,7 @@ struct oq_ctx {
     a.clov = f64 ? L.a64.p : L.a32.p;
     a.cinv = f64 ? L.i64.p : L.i32.p;
     a.nrhs = 1;
+    a.lat = lat;
     return a;
   }
 
@@ -208,6 +211,8 @@ struct oq_ctx {
     if (it != tuned.end()) {
       l.bx = it->second.first;
       l.by = it->second.second;
+      auto f = tuned_fmt.find(oq::TuneKey{lat, prec, mode, nrhs});
+      if (f != tuned_fmt.end()) l.link_fmt = f->second;
     } else if (nrhs == 1) {
       l.bx = 128;
       l.by = 1;
@@ -247,6 +252,16 @@ struct oq_ctx {
     return sites * (spin * a.nrhs + links + clov);
   }
 
+  // the binary32 link copy that matches the launch's link format
+  oq::HopArgs with_links(const oq::HopLaunch& l, const oq::HopArgs& a) {
+    oq::HopArgs b = a;
+    if (l.prec != oq::P_F64 && l.prec != oq::P_DF64 && a.lat >= 0 && a.lat < (int)lats.size()) {
+      const oq::LatCtx& L = lats[a.lat];
+      if (l.link_fmt == oq::LINK_18 && L.link_fmt == oq::LINK_12 && L.u32_18.p) b.links = L.u32_18.p;
+    }
+    return b;
+  }
+
   int run_hop(const oq::HopLaunch& l, const oq::HopArgs& a, cudaStream_t s) {
     oq::ProfRec rec;
     if (prof_on) {
@@ -267,7 +282,7 @@ struct oq_ctx {
       rec.bytes = hop_bytes(l, a);
       cudaEventRecord(rec.e0, s);
     }
-    cudaError_t e = oq::launch_hop(l, a, s);
+    cudaError_t e = oq::launch_hop(l, with_links(l, a), s);
     launches += 1;
     if (prof_on) {
       cudaEventRecord(rec.e1, s);
@@ -278,7 +293,7 @@ struct oq_ctx {
 
   void release() {
     for (auto& L : lats) {
-      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32};
+      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18};
       for (auto* b : bs) cudaFree(b->p);
       for (auto& kv : L.ws) cudaFree(kv.second.p);
     }

@@ -64,14 +64,14 @@ extern "C" int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const voi
   a.out = t;
   a.p = 1;
   HopLaunch l1 = h->hop_launch(lat, prec, HOP_P1, dagger ? 1 : 0, EPI_NONE, nrhs);
-  if (launch_hop(l1, a, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (launch_hop(l1, h->with_links(l1, a), s) != cudaSuccess) return OQ_ERR_CUDA;
   // pass 2: out_e = A_ee in_e + 1/2 H_eo t_o
   a.in = t;
   a.in2 = in_dev;
   a.out = out_dev;
   a.p = 0;
   HopLaunch l2 = h->hop_launch(lat, prec, HOP_P2, dagger ? 1 : 0, EPI_NONE, nrhs);
-  if (launch_hop(l2, a, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (launch_hop(l2, h->with_links(l2, a), s) != cudaSuccess) return OQ_ERR_CUDA;
   h->launches += 2;
   return OQ_OK;
 }

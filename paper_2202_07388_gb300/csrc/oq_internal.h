@@ -66,6 +66,7 @@ struct HopArgs {
   long ep_x_stride, ep_p_stride, ep_r_stride, ep_eta_stride;
   RedArgs red;
   CgState* cg;
+  int lat;             // host side: lattice of the handle these arguments belong to
 };
 
 struct HopLaunch {

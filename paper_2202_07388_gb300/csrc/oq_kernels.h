@@ -6,7 +6,8 @@ struct oq_ctx;
 
 namespace oq {
 
-cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, cudaStream_t s);
+cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, void* u18,
+                       cudaStream_t s);
 cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
                         int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s);
 cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,

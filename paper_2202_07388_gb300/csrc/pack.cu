@@ -11,9 +11,10 @@ __device__ __forceinline__ long lex_of(const Geom& g, const int x[4]) {
   return (((long)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
 }
 
-// one thread per (eo site, parity, mu)
+// one thread per (eo site, parity, mu); u18 (optional) receives an 18-real
+// binary32 copy next to a 12-real one
 __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, double2* __restrict__ u64,
-                                  void* __restrict__ u32, int fmt) {
+                                  void* __restrict__ u32, int fmt, float2* __restrict__ u18) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   const int mu = blockIdx.z;
@@ -36,13 +37,20 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, dou
     d[i] = make_float4((float)m[0].x, (float)m[0].y, (float)m[1].x, (float)m[1].y);
     d[g.Vh + i] = make_float4((float)m[2].x, (float)m[2].y, (float)m[3].x, (float)m[3].y);
     d[2 * g.Vh + i] = make_float4((float)m[4].x, (float)m[4].y, (float)m[5].x, (float)m[5].y);
+    if (u18) {
+      float2* e = u18 + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) e[k * g.Vh + i] = make_float2((float)m[k].x, (float)m[k].y);
+    }
   }
 }
 
-cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, cudaStream_t s) {
+cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, void* u18,
+                       cudaStream_t s) {
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), 2, 4);
   pack_links_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<const double2*>(canon),
-                                           reinterpret_cast<double2*>(u64), u32, fmt);
+                                           reinterpret_cast<double2*>(u64), u32, fmt,
+                                           reinterpret_cast<float2*>(u18));
   return cudaGetLastError();
 }
 

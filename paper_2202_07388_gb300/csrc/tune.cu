@@ -67,43 +67,55 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
     }
     float best = 1e30f;
     std::pair<int, int> best_shape{128, 1};
-    for (auto c : candidates(nrhs)) {
-      HopLaunch l = h->hop_launch(lat, prec, mode, 0, EPI_NONE, nrhs);
-      l.bx = c.first;
-      l.by = c.second;
-      for (int w = 0; w < 2; ++w)
-        if (launch_hop(l, a, s) != cudaSuccess) ret = OQ_ERR_CUDA;
-      const int reps = 5;
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < reps; ++r)
-        if (launch_hop(l, a, s) != cudaSuccess) ret = OQ_ERR_CUDA;
-      cudaEventRecord(e1, s);
-      h->launches += 2 + reps;
-      if (cudaEventSynchronize(e1) != cudaSuccess) ret = OQ_ERR_CUDA;
-      if (ret) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= reps;
-      if (ms < best) {
-        best = ms;
-        best_shape = c;
+    int best_fmt = L.link_fmt;
+    // binary32 kernels may also read the 18-real copy of 12-real links
+    const bool two_fmts = prec != P_F64 && prec != P_DF64 && L.link_fmt == LINK_12 && L.u32_18.p;
+    for (int fmt = L.link_fmt; fmt >= 0; fmt = (two_fmts && fmt == LINK_12) ? LINK_18 : -1) {
+      for (auto c : candidates(nrhs)) {
+        HopLaunch l = h->hop_launch(lat, prec, mode, 0, EPI_NONE, nrhs);
+        l.bx = c.first;
+        l.by = c.second;
+        l.link_fmt = fmt;
+        const HopArgs b = h->with_links(l, a);
+        for (int w = 0; w < 2; ++w)
+          if (launch_hop(l, b, s) != cudaSuccess) ret = OQ_ERR_CUDA;
+        const int reps = 5;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r)
+          if (launch_hop(l, b, s) != cudaSuccess) ret = OQ_ERR_CUDA;
+        cudaEventRecord(e1, s);
+        h->launches += 2 + reps;
+        if (cudaEventSynchronize(e1) != cudaSuccess) ret = OQ_ERR_CUDA;
+        if (ret) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best) {
+          best = ms;
+          best_shape = c;
+          best_fmt = fmt;
+        }
       }
+      if (ret) break;
     }
     if (ret) break;
     h->tuned[TuneKey{lat, prec, mode, nrhs}] = best_shape;
     h->tuned_ms[TuneKey{lat, prec, mode, nrhs}] = best;
+    h->tuned_fmt[TuneKey{lat, prec, mode, nrhs}] = best_fmt;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return ret;
 }
 
-extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms) {
+extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
+                           int* link_fmt) {
   if (!h || !bx || !by || !ms || lat < 0 || lat >= (int)h->lats.size()) return OQ_ERR_ARG;
   auto it = h->tuned.find(TuneKey{lat, prec, mode, nrhs});
   if (it == h->tuned.end()) return OQ_ERR_STATE;
   *bx = it->second.first;
   *by = it->second.second;
   *ms = h->tuned_ms[TuneKey{lat, prec, mode, nrhs}];
+  if (link_fmt) *link_fmt = h->tuned_fmt[TuneKey{lat, prec, mode, nrhs}];
   return OQ_OK;
 }

@@ -86,7 +86,7 @@ _SIGS = {
     "oq_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
     "oq_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
     "oq_tune_get": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                              C.POINTER(C.c_float)]),
+                              C.POINTER(C.c_float), C.POINTER(C.c_int)]),
     "oq_profile_start": (C.c_int, [_P]),
     "oq_kernel_launches": (C.c_longlong, [_P]),
     "oq_profile_stop": (C.c_int, [_P, C.POINTER(OqKernelTime), C.c_int, C.POINTER(C.c_int)]),
@@ -310,10 +310,10 @@ class Handle:
         _check(lib().oq_autotune(self.h, lat, prec, nrhs, _stream(stream)), "oq_autotune")
         out = {}
         for mode in (0, 1, 2):
-            bx, by, ms = C.c_int(), C.c_int(), C.c_float()
-            _check(lib().oq_tune_get(self.h, lat, prec, mode, nrhs, C.byref(bx), C.byref(by), C.byref(ms)),
-                   "oq_tune_get")
-            out[mode] = (bx.value, by.value, ms.value)
+            bx, by, ms, fmt = C.c_int(), C.c_int(), C.c_float(), C.c_int()
+            _check(lib().oq_tune_get(self.h, lat, prec, mode, nrhs, C.byref(bx), C.byref(by), C.byref(ms),
+                                     C.byref(fmt)), "oq_tune_get")
+            out[mode] = (bx.value, by.value, ms.value, "12-real" if fmt.value == LINK_12 else "18-real")
         return out
 
     # instrumentation ---------------------------------------------------

@@ -118,6 +118,25 @@ def test_u3_links_and_periodic_time():
             assert rel_err(from_dev(out, psi.shape), ref) < TOL[prec]
 
 
+def test_eighteen_real_copy_of_twelve_real_links():
+    """Handles uploaded with 12-real links keep an 18-real binary32 copy; a
+    tuned launch may use either.  Force both by tuning and check each pass."""
+    oq = _oq()
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.1365, 1.3)
+    h = make_handle(dims, u, 0.1365, 1.3, oq.LINK_12)
+    psi = dirac.even_part(synth.make_source(dims, 61))
+    ref = dirac.dw_hat(u, a, ainv, psi)
+    shapes = h.autotune(oq.F32, nrhs=1)
+    assert all(v[3] in ("12-real", "18-real") for v in shapes.values())
+    pin, pout = h.new_packed(oq.F32, oq.EVEN), h.new_packed(oq.F32, oq.EVEN)
+    h.pack(to_dev(psi), pin, oq.F32, oq.EVEN)
+    h.dw_hat(pin, pout, oq.F32)
+    out = to_dev(np.zeros_like(psi))
+    h.unpack(pout, out, oq.F32, oq.EVEN)
+    assert rel_err(from_dev(out, psi.shape), ref) < TOL[1]
+
+
 def test_multi_rhs_matches_single():
     oq = _oq()
     dims = (6, 4, 2, 6)
