@@ -456,7 +456,12 @@ def run_profile_case(args):
                           "launches": h.kernel_launches()}))
         h.close()
         return 0
-    h.autotune(prec, nrhs=nrhs)
+    if args.profile_pin:
+        bx, by, nr, cap, fmt = (int(v) for v in args.profile_pin.split(","))
+        for mode in (0, 1, 2):
+            h.tune_set(prec, mode, nrhs, bx, by, nr=nr, regcap=cap, link_fmt=fmt)
+    else:
+        h.autotune(prec, nrhs=nrhs)
     n_tune = h.kernel_launches()   # every launch so far is a stencil launch of the tuner
     if args.profile_kind == "cgne":
         # one batched mixed-precision CGNE solve; its first stencil launches
@@ -642,6 +647,8 @@ def main():
     ap.add_argument("--profile-prec", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
     ap.add_argument("--profile-nrhs", type=int, default=12)
     ap.add_argument("--profile-kind", default="dhat", choices=["dhat", "cgne", "tc", "cc", "sap"])
+    ap.add_argument("--profile-pin", default=None,
+                    help="bx,by,nr,regcap,link_fmt: pin the stencil launch instead of autotuning")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

@@ -105,7 +105,10 @@ typedef struct {
 } oq_status;
 
 /* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no
- * device: the current CUDA device at creation is used for every call. */
+ * device: the current CUDA device at creation is used for every call.
+ * Every extent must be even and >= 2, bc_t +1 or -1, and the volume at most
+ * 2^29 sites (half volume <= 2^28, so site offsets fit 32-bit arithmetic);
+ * otherwise OQ_ERR_ARG. */
 int oq_create(oq_handle* h, const oq_lattice* lats, int nlat);
 int oq_destroy(oq_handle h);
 const char* oq_error_string(int code);
@@ -173,20 +176,27 @@ int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* ou
 int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs,
                             int dagger, void* stream);
 
-/* Autotuner (no counterpart in the paper): time every admissible CTA shape
- * (bx sites x by right-hand sides per CTA, bx a multiple of 32, bx*by <= 256)
- * of the full Dw and of both Dhat passes for this (lattice, precision, nrhs)
- * on handle-owned scratch fields with CUDA events, and keep the fastest per
- * pass in the handle; every later stencil launch of that variant, including
- * those inside the solvers, uses it.  Synchronises `stream`.
- * For binary32-arithmetic kernels on 12-real links the tuner also tries the
- * 18-real copy the handle keeps (fewer instructions, more bytes) and keeps
- * the faster format.  oq_tune_get reports the chosen shape, its time per
- * launch and (link_fmt, nullable) the link format (mode 0 = Dw, 1 = Dhat
- * pass 1, 2 = Dhat pass 2); OQ_ERR_STATE if not tuned. */
+/* Autotuner (no counterpart in the paper): time every admissible launch of
+ * the full Dw and of both Dhat passes for this (lattice, precision, nrhs) on
+ * handle-owned scratch fields with CUDA events, and keep the fastest per pass
+ * in the handle; every later stencil launch of that variant, including those
+ * inside the solvers, uses it.  Synchronises `stream`.  A launch is: the CTA
+ * shape (bx sites x by rows, bx a multiple of 32), the right-hand sides per
+ * thread nr (1; or 2, 4 for F32/BF16/F16 storage with nrhs >= nr: the links,
+ * clover blocks and indices of a site are loaded once for nr right-hand sides
+ * and the arithmetic runs on packed pairs of them; bx*by <= 128), a register
+ * cap of the nr > 1 kernels (regcap 0/1), and for binary32-arithmetic kernels
+ * on 12-real links the 18-real copy the handle keeps (fewer instructions,
+ * more bytes).  oq_tune_get reports the chosen launch and its time
+ * (link_fmt, nr, regcap nullable; mode 0 = Dw, 1 = Dhat pass 1, 2 = Dhat
+ * pass 2); OQ_ERR_STATE if none is set.  oq_tune_set pins a launch without
+ * timing (link_fmt -1: the uploaded format; OQ_ERR_ARG for an inadmissible
+ * launch, OQ_ERR_STATE before oq_gauge_upload). */
 int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* stream);
 int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
-                int* link_fmt);
+                int* link_fmt, int* nr, int* regcap);
+int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int by, int nr, int regcap,
+                int link_fmt);
 
 /* Handle options (no counterpart in the paper).
  * OQ_OPT_DF64_RESETS: 1 = the intermediate CGNE reset steps of a

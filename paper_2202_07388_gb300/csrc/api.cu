@@ -16,6 +16,15 @@ using namespace oq;
 
 namespace oq {
 cudaError_t launch_hop(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  if (L.nr != 1) {
+    if (L.sys || (L.nr != 2 && L.nr != 4)) return cudaErrorInvalidValue;
+    switch (L.prec) {
+      case P_F32: return L.nr == 2 ? launch_hop_mr2_f32(L, a, s) : launch_hop_mr4_f32(L, a, s);
+      case P_BF16: return L.nr == 2 ? launch_hop_mr2_bf16(L, a, s) : launch_hop_mr4_bf16(L, a, s);
+      case P_F16: return L.nr == 2 ? launch_hop_mr2_f16(L, a, s) : launch_hop_mr4_f16(L, a, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (L.prec) {
     case P_F64: return launch_hop_f64(L, a, s);
     case P_F32: return launch_hop_f32(L, a, s);
@@ -48,6 +57,8 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
     for (int mu = 0; mu < 4; ++mu)
       if (lats[k].L[mu] < 2 || (lats[k].L[mu] & 1)) return OQ_ERR_ARG;
     if (lats[k].bc_t != 1 && lats[k].bc_t != -1) return OQ_ERR_ARG;
+    const double v = (double)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3];
+    if (v > (double)(1L << 29)) return OQ_ERR_ARG;  // Vh <= 2^28: 32-bit site offsets
   }
   oq_ctx* h = new (std::nothrow) oq_ctx();
   if (!h) return OQ_ERR_NOMEM;
@@ -62,6 +73,7 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
     L.g.Lh3 = lats[k].L[3] / 2;
     L.g.Vh = (long)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3] / 2;
     L.g.bc_t = (float)lats[k].bc_t;
+    geom_init_div(L.g);
   }
   *out = h;
   return OQ_OK;

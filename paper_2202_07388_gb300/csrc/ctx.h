@@ -48,6 +48,15 @@ struct TuneKey {
   }
 };
 
+// the launch shape chosen for one stencil variant (by the tuner or set)
+struct TuneVal {
+  int bx = 128, by = 1;  // CTA: bx sites x by groups of nr right-hand sides
+  int nr = 1;            // right-hand sides per thread
+  int regcap = 0;        // register-capped multi-rhs variant
+  int link_fmt = -1;     // binary32 link format (-1: the uploaded one)
+  float ms = 0.f;        // tuner's time per launch (0 if set by hand)
+};
+
 }  // namespace oq
 
 struct oq_ctx {
@@ -66,9 +75,7 @@ struct oq_ctx {
   oq::CgState* cg_host = nullptr;  // pinned mirror
   size_t cg_n = 0;
   // launch shapes
-  std::map<oq::TuneKey, std::pair<int, int>> tuned;
-  std::map<oq::TuneKey, float> tuned_ms;
-  std::map<oq::TuneKey, int> tuned_fmt;  // binary32 link format picked by the tuner
+  std::map<oq::TuneKey, oq::TuneVal> tuned;
   // kernels launched by this handle so far
   long long launches = 0;
   // CGNE: intermediate reset residuals in double-float arithmetic (off by
@@ -209,10 +216,11 @@ struct oq_ctx {
     l.epi = epi;
     auto it = tuned.find(oq::TuneKey{lat, prec, mode, nrhs});
     if (it != tuned.end()) {
-      l.bx = it->second.first;
-      l.by = it->second.second;
-      auto f = tuned_fmt.find(oq::TuneKey{lat, prec, mode, nrhs});
-      if (f != tuned_fmt.end()) l.link_fmt = f->second;
+      l.bx = it->second.bx;
+      l.by = it->second.by;
+      l.nr = it->second.nr;
+      l.regcap = it->second.regcap;
+      if (it->second.link_fmt >= 0) l.link_fmt = it->second.link_fmt;
     } else if (nrhs == 1) {
       l.bx = 128;
       l.by = 1;

@@ -1,0 +1,615 @@
+// Multi-right-hand-side form of the Wilson-clover stencil (binary32
+// arithmetic, F32 / BF16 / F16 spinor storage).
+//
+// One thread computes one output site for NR right-hand sides (NR even).
+// What depends only on the site is done once for all NR: coordinates and
+// neighbour indices (32-bit, by multiplication with precomputed
+// reciprocals), the eight link loads and their 12-real reconstruction, and
+// the clover block loads.  The spinor arithmetic runs on pairs of
+// right-hand sides with the two-lane binary32 FMA / ADD / MUL of sm_100-class
+// GPUs (one instruction for both right-hand sides, per-lane results equal
+// to the scalar fmaf / fadd / fmul).  The operator, its modes and epilogues
+// are those of hop_kernel (hop_impl.cuh):
+//
+//   HOP_DW : out = A in2 - 1/2 H in
+//   HOP_P1 : out = A^{-1} (-1/2 H in)
+//   HOP_P2 : out = A in2 + 1/2 H in
+//
+// with H the hopping term of Eq. (2.2) (projectors swapped for the adjoint),
+// the time-boundary factor on hops across x0 = T-1 <-> 0, and the norm / CG
+// update epilogues with deterministic binary64 grid reductions.
+#pragma once
+#include <type_traits>
+
+#include "reduce.cuh"
+
+namespace oq {
+namespace mr {
+
+typedef float2 F2;
+
+__device__ __forceinline__ F2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ F2 add(F2 a, F2 b) { return __fadd2_rn(a, b); }
+// a - b as a + (-1) b: one rounding, the same value as fsub
+__device__ __forceinline__ F2 sub(F2 a, F2 b) { return __ffma2_rn(b, bc(-1.f), a); }
+__device__ __forceinline__ F2 mul(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 ffma(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+
+// a complex number of two right-hand sides (lane x: first, lane y: second)
+struct C2 {
+  F2 re, im;
+};
+struct Sp2 {
+  C2 c[4][3];  // [spin][colour]
+};
+struct Hs2 {
+  C2 c[2][3];
+};
+
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {add(a.re, b.re), add(a.im, b.im)}; }
+__device__ __forceinline__ C2 csub(C2 a, C2 b) { return {sub(a.re, b.re), sub(a.im, b.im)}; }
+// a + i b, a - i b
+__device__ __forceinline__ C2 cadd_i(C2 a, C2 b) { return {sub(a.re, b.im), add(a.im, b.re)}; }
+__device__ __forceinline__ C2 csub_i(C2 a, C2 b) { return {add(a.re, b.im), sub(a.im, b.re)}; }
+
+// spinor of site j, 32-bit offsets (chunk c at c*Vh + j)
+template <int P>
+__device__ __forceinline__ void load_sp(const char* base, uint32_t Vh, uint32_t j, Spinor<float>& s) {
+  cx<float>* f = &s.c[0][0];
+  if constexpr (P == P_F32) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float4 v = __ldg(b + (c * Vh + j));
+      f[2 * c] = cx<float>{v.x, v.y};
+      f[2 * c + 1] = cx<float>{v.z, v.w};
+    }
+  } else {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint4 v = __ldg(b + (c * Vh + j));
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 z = (P == P_BF16) ? unpack_bf16x2(w[k]) : unpack_f16x2(w[k]);
+        f[4 * c + k] = cx<float>{z.x, z.y};
+      }
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void store_sp(char* base, uint32_t Vh, uint32_t i, const Spinor<float>& s) {
+  const cx<float>* f = &s.c[0][0];
+  if constexpr (P == P_F32) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      b[c * Vh + i] = make_float4(f[2 * c].re, f[2 * c].im, f[2 * c + 1].re, f[2 * c + 1].im);
+  } else {
+    uint4* b = reinterpret_cast<uint4*>(base);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        w[k] = (P == P_BF16) ? pack_bf16x2(f[4 * c + k].re, f[4 * c + k].im)
+                             : pack_f16x2(f[4 * c + k].re, f[4 * c + k].im);
+      b[c * Vh + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+__device__ __forceinline__ void join(const Spinor<float>& a, const Spinor<float>& b, Sp2& s) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      s.c[k][c].re = make_float2(a.c[k][c].re, b.c[k][c].re);
+      s.c[k][c].im = make_float2(a.c[k][c].im, b.c[k][c].im);
+    }
+}
+
+template <int LANE>
+__device__ __forceinline__ void lane(const Sp2& s, Spinor<float>& a) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      a.c[k][c] = LANE == 0 ? cx<float>{s.c[k][c].re.x, s.c[k][c].im.x} : cx<float>{s.c[k][c].re.y, s.c[k][c].im.y};
+}
+
+// link U_mu at eo site i of parity p (binary32, 18 or 12 reals), 32-bit offsets
+template <int FMT>
+__device__ __forceinline__ void load_u(const void* base, uint32_t Vh, int p, int mu, uint32_t i, Su3<float>& u) {
+  if constexpr (FMT == LINK_18) {
+    const float2* b = reinterpret_cast<const float2*>(base) + (size_t)((p * 4 + mu) * 9) * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float2 v = __ldg(b + (k * Vh + i));
+      u.m[k / 3][k % 3] = cx<float>{v.x, v.y};
+    }
+  } else {
+    const float4* b = reinterpret_cast<const float4*>(base) + (size_t)((p * 4 + mu) * 3) * Vh;
+    const float4 a0 = __ldg(b + i), a1 = __ldg(b + (Vh + i)), a2 = __ldg(b + (2 * Vh + i));
+    u.m[0][0] = {a0.x, a0.y};
+    u.m[0][1] = {a0.z, a0.w};
+    u.m[0][2] = {a1.x, a1.y};
+    u.m[1][0] = {a1.z, a1.w};
+    u.m[1][1] = {a2.x, a2.y};
+    u.m[1][2] = {a2.z, a2.w};
+    // row 2 = conj(row0 x row1)
+    u.m[2][0] = conj(u.m[0][1] * u.m[1][2] - u.m[0][2] * u.m[1][1]);
+    u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
+    u.m[2][2] = conj(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
+  }
+}
+
+// spin projection for the hop along mu: S = -1 (1 - g_mu), S = +1 (1 + g_mu)
+// (chiral basis; the same linear combinations as oq::project)
+template <int MU, int S>
+__device__ __forceinline__ void project(const Sp2& p, Hs2& h) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const C2 p0 = p.c[0][a], p1 = p.c[1][a], p2 = p.c[2][a], p3 = p.c[3][a];
+    if constexpr (MU == 0) {
+      if constexpr (S < 0) { h.c[0][a] = cadd(p0, p2); h.c[1][a] = cadd(p1, p3); }
+      else                 { h.c[0][a] = csub(p0, p2); h.c[1][a] = csub(p1, p3); }
+    } else if constexpr (MU == 1) {
+      if constexpr (S < 0) { h.c[0][a] = cadd_i(p0, p3); h.c[1][a] = cadd_i(p1, p2); }
+      else                 { h.c[0][a] = csub_i(p0, p3); h.c[1][a] = csub_i(p1, p2); }
+    } else if constexpr (MU == 2) {
+      if constexpr (S < 0) { h.c[0][a] = cadd(p0, p3); h.c[1][a] = csub(p1, p2); }
+      else                 { h.c[0][a] = csub(p0, p3); h.c[1][a] = cadd(p1, p2); }
+    } else {
+      if constexpr (S < 0) { h.c[0][a] = cadd_i(p0, p2); h.c[1][a] = csub_i(p1, p3); }
+      else                 { h.c[0][a] = csub_i(p0, p2); h.c[1][a] = cadd_i(p1, p3); }
+    }
+  }
+}
+
+// y = U h (UD = false) or U^dag h (UD = true) on both spin components; the
+// link elements are broadcast to both lanes
+template <bool UD>
+__device__ __forceinline__ void su3(const Su3<float>& u, const Hs2& h, Hs2& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      C2 acc;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float ur = UD ? u.m[b][a].re : u.m[a][b].re;
+        const float ui = UD ? -u.m[b][a].im : u.m[a][b].im;
+        const C2 x = h.c[s][b];
+        if (b == 0) {
+          acc.re = mul(bc(ur), x.re);
+          acc.im = mul(bc(ur), x.im);
+        } else {
+          acc.re = ffma(bc(ur), x.re, acc.re);
+          acc.im = ffma(bc(ur), x.im, acc.im);
+        }
+        acc.re = ffma(bc(-ui), x.im, acc.re);
+        acc.im = ffma(bc(ui), x.re, acc.im);
+      }
+      y.c[s][a] = acc;
+    }
+}
+
+// acc += sg * reconstruction of the transported half spinor t for the
+// projector (1 -/+ g_mu) (S = -1 / +1), sg = +-1 on both lanes
+template <int MU, int S>
+__device__ __forceinline__ void accum(Sp2& acc, const Hs2& t, F2 sg) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const C2 h0 = t.c[0][a], h1 = t.c[1][a];
+    if constexpr (MU == 0) {
+      // upper: +sg h; lower: l0 = h0, l1 = h1, negated for S = +1
+      const F2 nsg = mul(sg, bc(-1.f));
+      const F2 ls = S < 0 ? sg : nsg;
+      acc.c[0][a] = {ffma(sg, h0.re, acc.c[0][a].re), ffma(sg, h0.im, acc.c[0][a].im)};
+      acc.c[1][a] = {ffma(sg, h1.re, acc.c[1][a].re), ffma(sg, h1.im, acc.c[1][a].im)};
+      acc.c[2][a] = {ffma(ls, h0.re, acc.c[2][a].re), ffma(ls, h0.im, acc.c[2][a].im)};
+      acc.c[3][a] = {ffma(ls, h1.re, acc.c[3][a].re), ffma(ls, h1.im, acc.c[3][a].im)};
+    } else {
+      acc.c[0][a] = cadd(acc.c[0][a], h0);
+      acc.c[1][a] = cadd(acc.c[1][a], h1);
+      if constexpr (MU == 1) {  // l0 = -i h1, l1 = -i h0
+        if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h1); acc.c[3][a] = csub_i(acc.c[3][a], h0); }
+        else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h1); acc.c[3][a] = cadd_i(acc.c[3][a], h0); }
+      } else if constexpr (MU == 2) {  // l0 = -h1, l1 = h0
+        if constexpr (S < 0) { acc.c[2][a] = csub(acc.c[2][a], h1); acc.c[3][a] = cadd(acc.c[3][a], h0); }
+        else                 { acc.c[2][a] = cadd(acc.c[2][a], h1); acc.c[3][a] = csub(acc.c[3][a], h0); }
+      } else {  // l0 = -i h0, l1 = i h1
+        if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h0); acc.c[3][a] = cadd_i(acc.c[3][a], h1); }
+        else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h0); acc.c[3][a] = csub_i(acc.c[3][a], h1); }
+      }
+    }
+  }
+}
+
+// One Hermitian 6x6 clover block of a site (binary32 storage: 6 diagonal
+// reals, then 15 upper off-diagonal complex entries row by row).
+struct Blk {
+  float d[6];
+  cx<float> off[15];
+};
+
+__device__ __forceinline__ void load_blk(const void* base, uint32_t Vh, int p, int b, uint32_t i, Blk& k) {
+  const float4* q = reinterpret_cast<const float4*>(base) + (size_t)(p * 18) * Vh;
+  float r[36];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const float4 w = __ldg(q + ((9 * b + c) * Vh + i));
+    r[4 * c] = w.x;
+    r[4 * c + 1] = w.y;
+    r[4 * c + 2] = w.z;
+    r[4 * c + 3] = w.w;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) k.d[c] = r[c];
+#pragma unroll
+  for (int c = 0; c < 15; ++c) k.off[c] = cx<float>{r[6 + 2 * c], r[7 + 2 * c]};
+}
+
+// y = K x for one block (x, y: the 6 components 3*spin_local + colour)
+__device__ __forceinline__ void blk_apply(const Blk& k, const C2* x, C2* y) {
+#pragma unroll
+  for (int r = 0; r < 6; ++r) y[r] = {mul(bc(k.d[r]), x[r].re), mul(bc(k.d[r]), x[r].im)};
+  int n = 0;
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = r + 1; c < 6; ++c) {
+      const cx<float> o = k.off[n++];
+      // y[r] += o x[c]
+      y[r].re = ffma(bc(o.re), x[c].re, ffma(bc(-o.im), x[c].im, y[r].re));
+      y[r].im = ffma(bc(o.re), x[c].im, ffma(bc(o.im), x[c].re, y[r].im));
+      // y[c] += conj(o) x[r]
+      y[c].re = ffma(bc(o.re), x[r].re, ffma(bc(o.im), x[r].im, y[c].re));
+      y[c].im = ffma(bc(o.re), x[r].im, ffma(bc(-o.im), x[r].re, y[c].im));
+    }
+}
+
+// eo coordinates of site i (parity p), 32-bit
+__device__ __forceinline__ void coords(const Geom& g, int p, uint32_t i, int x[4]) {
+  uint32_t q = geom_div(i, g.dm[0], g.ds[0]);
+  const int k = (int)(i - q * (uint32_t)g.Lh3);
+  uint32_t t = q;
+  q = geom_div(t, g.dm[1], g.ds[1]);
+  x[2] = (int)(t - q * (uint32_t)g.L[2]);
+  t = q;
+  q = geom_div(t, g.dm[2], g.ds[2]);
+  x[1] = (int)(t - q * (uint32_t)g.L[1]);
+  x[0] = (int)q;
+  x[3] = 2 * k + ((p + x[0] + x[1] + x[2]) & 1);
+}
+
+// Per-thread work of hop_mr_kernel: the NR/2 lane pairs of one output site.
+template <int P, int FMT, int MODE, bool DAG, int EPI, int NR>
+__device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int p, const bool (&live)[NR],
+                                     double (&red)[NR]) {
+  constexpr int NP = NR / 2;
+  constexpr int SF = DAG ? +1 : -1;  // projector sign of the forward hop
+  const Geom& g = a.g;
+  const uint32_t Vh = (uint32_t)g.Vh;
+  int x[4];
+  coords(g, p, i, x);
+  // neighbour eo indices: a hop along mu = 0, 1, 2 moves the lexicographic
+  // index by an even stride (L[3] is even), i.e. the eo index by half of it;
+  // along mu = 3 the eo index is that of the row start plus x3' / 2
+  const uint32_t s2 = (uint32_t)g.Lh3, s1 = s2 * (uint32_t)g.L[2], s0 = s1 * (uint32_t)g.L[1];
+  const uint32_t st[3] = {s0, s1, s2};
+  uint32_t jf[4], jb[4];
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    const uint32_t wrap = (uint32_t)(g.L[mu] - 1) * st[mu];
+    jf[mu] = x[mu] == g.L[mu] - 1 ? i - wrap : i + st[mu];
+    jb[mu] = x[mu] == 0 ? i + wrap : i - st[mu];
+  }
+  {
+    const uint32_t row = i - (uint32_t)(x[3] >> 1);
+    const int xf = x[3] + 1 == g.L[3] ? 0 : x[3] + 1;
+    const int xb = x[3] == 0 ? g.L[3] - 1 : x[3] - 1;
+    jf[3] = row + (uint32_t)(xf >> 1);
+    jb[3] = row + (uint32_t)(xb >> 1);
+  }
+  const F2 sf = bc(x[0] == g.L[0] - 1 ? g.bc_t : 1.f);  // forward time hop crosses the boundary
+  const F2 sb = bc(x[0] == 0 ? g.bc_t : 1.f);
+
+  const long par_in = (MODE == HOP_DW) ? (long)(1 - p) * a.half_bytes : 0;
+  const long par_out = (MODE == HOP_DW) ? (long)p * a.half_bytes : 0;
+  const char* in[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const int r = rhs0 + k < a.nrhs ? rhs0 + k : a.nrhs - 1;  // clamp: lanes past nrhs are not stored
+    in[k] = (const char*)a.in + (long)r * a.in_stride + par_in;
+  }
+
+  Sp2 acc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[q].c[s][c] = {bc(0.f), bc(0.f)};
+
+  auto hop = [&](auto mu_c) {
+    constexpr int MU = decltype(mu_c)::value;
+    Su3<float> u;
+    // forward: U_mu(x) (1 -/+ g) psi(x + mu)
+    load_u<FMT>(a.links, Vh, p, MU, i, u);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      Spinor<float> n0, n1;
+      load_sp<P>(in[2 * q], Vh, jf[MU], n0);
+      load_sp<P>(in[2 * q + 1], Vh, jf[MU], n1);
+      Sp2 nb;
+      join(n0, n1, nb);
+      Hs2 h, t;
+      project<MU, SF>(nb, h);
+      su3<false>(u, h, t);
+      accum<MU, SF>(acc[q], t, MU == 0 ? sf : bc(1.f));
+    }
+    // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
+    load_u<FMT>(a.links, Vh, 1 - p, MU, jb[MU], u);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      Spinor<float> n0, n1;
+      load_sp<P>(in[2 * q], Vh, jb[MU], n0);
+      load_sp<P>(in[2 * q + 1], Vh, jb[MU], n1);
+      Sp2 nb;
+      join(n0, n1, nb);
+      Hs2 h, t;
+      project<MU, -SF>(nb, h);
+      su3<true>(u, h, t);
+      accum<MU, -SF>(acc[q], t, MU == 0 ? sb : bc(1.f));
+    }
+  };
+  hop(std::integral_constant<int, 0>{});
+  hop(std::integral_constant<int, 1>{});
+  hop(std::integral_constant<int, 2>{});
+  hop(std::integral_constant<int, 3>{});
+
+  const F2 w = bc(MODE == HOP_P2 ? 0.5f : -0.5f);
+  Sp2 res[NP];
+  if constexpr (MODE == HOP_P1) {
+    // res = A^{-1} (w H in)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      Blk k;
+      load_blk(a.cinv, Vh, p, b, i, k);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        C2 xv[6], yv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          const C2 v = acc[q].c[2 * b + r / 3][r % 3];
+          xv[r] = {mul(w, v.re), mul(w, v.im)};
+        }
+        blk_apply(k, xv, yv);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) res[q].c[2 * b + r / 3][r % 3] = yv[r];
+      }
+    }
+  } else {
+    // res = A in2 + w H in
+    Sp2 loc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      Spinor<float> l0, l1;
+      const int r0 = rhs0 + 2 * q < a.nrhs ? rhs0 + 2 * q : a.nrhs - 1;
+      const int r1 = rhs0 + 2 * q + 1 < a.nrhs ? rhs0 + 2 * q + 1 : a.nrhs - 1;
+      load_sp<P>((const char*)a.in2 + (long)r0 * a.in2_stride + par_out, Vh, i, l0);
+      load_sp<P>((const char*)a.in2 + (long)r1 * a.in2_stride + par_out, Vh, i, l1);
+      join(l0, l1, loc[q]);
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      Blk k;
+      load_blk(a.clov, Vh, p, b, i, k);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        C2 xv[6], yv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) xv[r] = loc[q].c[2 * b + r / 3][r % 3];
+        blk_apply(k, xv, yv);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          const C2 v = acc[q].c[2 * b + r / 3][r % 3];
+          res[q].c[2 * b + r / 3][r % 3] = {ffma(w, v.re, yv[r].re), ffma(w, v.im, yv[r].im)};
+        }
+      }
+    }
+  }
+
+  if constexpr (EPI == EPI_NONE || EPI == EPI_NORM) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      Spinor<float> o0, o1;
+      lane<0>(res[q], o0);
+      lane<1>(res[q], o1);
+      if (live[2 * q]) store_sp<P>((char*)a.out + (long)(rhs0 + 2 * q) * a.out_stride + par_out, Vh, i, o0);
+      if (live[2 * q + 1])
+        store_sp<P>((char*)a.out + (long)(rhs0 + 2 * q + 1) * a.out_stride + par_out, Vh, i, o1);
+      if constexpr (EPI == EPI_NORM) {
+        red[2 * q] = site_norm2(o0);
+        red[2 * q + 1] = site_norm2(o1);
+      }
+    }
+  } else if constexpr (EPI == EPI_CG) {
+    // q = res; x += alpha p (x binary32); r -= alpha q; norm of the stored r
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int r0 = rhs0 + 2 * q < a.nrhs ? rhs0 + 2 * q : a.nrhs - 1;
+      const int r1 = rhs0 + 2 * q + 1 < a.nrhs ? rhs0 + 2 * q + 1 : a.nrhs - 1;
+      const F2 al = make_float2((float)a.cg[r0].alpha, (float)a.cg[r1].alpha);
+      const F2 nal = mul(al, bc(-1.f));
+      Spinor<float> t0, t1;
+      Sp2 pv, rv, xv;
+      load_sp<P>((const char*)a.ep_p + (long)r0 * a.ep_p_stride, Vh, i, t0);
+      load_sp<P>((const char*)a.ep_p + (long)r1 * a.ep_p_stride, Vh, i, t1);
+      join(t0, t1, pv);
+      load_sp<P>((const char*)a.ep_r + (long)r0 * a.ep_r_stride, Vh, i, t0);
+      load_sp<P>((const char*)a.ep_r + (long)r1 * a.ep_r_stride, Vh, i, t1);
+      join(t0, t1, rv);
+      load_sp<P_F32>((const char*)a.ep_x + (long)r0 * a.ep_x_stride, Vh, i, t0);
+      load_sp<P_F32>((const char*)a.ep_x + (long)r1 * a.ep_x_stride, Vh, i, t1);
+      join(t0, t1, xv);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          xv.c[s][c].re = ffma(al, pv.c[s][c].re, xv.c[s][c].re);
+          xv.c[s][c].im = ffma(al, pv.c[s][c].im, xv.c[s][c].im);
+          rv.c[s][c].re = ffma(nal, res[q].c[s][c].re, rv.c[s][c].re);
+          rv.c[s][c].im = ffma(nal, res[q].c[s][c].im, rv.c[s][c].im);
+        }
+      Spinor<float> x0, x1, q0, q1;
+      lane<0>(xv, x0);
+      lane<1>(xv, x1);
+      lane<0>(rv, q0);
+      lane<1>(rv, q1);
+      round_trip<P>(q0);
+      round_trip<P>(q1);
+      if (live[2 * q]) {
+        store_sp<P_F32>((char*)a.ep_x + (long)r0 * a.ep_x_stride, Vh, i, x0);
+        store_sp<P>((char*)a.ep_r + (long)r0 * a.ep_r_stride, Vh, i, q0);
+        red[2 * q] = site_norm2(q0);
+      }
+      if (live[2 * q + 1]) {
+        store_sp<P_F32>((char*)a.ep_x + (long)r1 * a.ep_x_stride, Vh, i, x1);
+        store_sp<P>((char*)a.ep_r + (long)r1 * a.ep_r_stride, Vh, i, q1);
+        red[2 * q + 1] = site_norm2(q1);
+      }
+    }
+  }
+}
+
+// grid_reduce for NR values per thread (right-hand sides rhs0 .. rhs0+NR-1
+// of the thread's row): smem needs (blockDim.x / 32) * blockDim.y * NR doubles
+template <int NR>
+__device__ __forceinline__ void grid_reduce_nr(const double (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
+                                               double* smem, unsigned cta, unsigned ncta) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const double s = warp_sum(v[k]);
+    if ((tx & 31) == 0) smem[(ty * NR + k) * nw + (tx >> 5)] = s;
+  }
+  __syncthreads();
+  if (tx >= 32) return;
+  for (int k = 0; k < NR; ++k) {
+    const int rhs = rhs0 + k;
+    if (rhs >= nrhs) break;
+    bool last = false;
+    if (tx == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += smem[(ty * NR + k) * nw + w];
+      ra.partials[(long)rhs * ncta + cta] = s;
+      __threadfence();
+      const unsigned t = atomicAdd(ra.counters + rhs, 1u);
+      last = (t == ncta - 1);
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      double acc = 0.0;
+      const volatile double* part = ra.partials + (long)rhs * ncta;
+      for (unsigned b = tx; b < ncta; b += 32) acc += part[b];
+      acc = warp_sum(acc);
+      if (tx == 0) {
+        ra.counters[rhs] = 0u;
+        run_finisher(ra, rhs, acc);
+      }
+    }
+  }
+}
+
+}  // namespace mr
+
+// CTA = blockDim.x sites x blockDim.y groups of NR right-hand sides
+// (at most 128 threads); grid ordered as for hop_kernel (rhs tiles of one
+// site block adjacent).  CAP = 1 caps the registers (128 for NR = 2, 168 for
+// NR = 4: at least 16 / 12 warps per SM, with some spilling); CAP = 0 lets
+// the compiler keep all neighbour loads of a site in flight.
+template <int NR, int CAP>
+struct MrBounds {
+  static constexpr int min_blocks = CAP == 0 ? 1 : NR == 2 ? 4 : 3;
+};
+template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, int CAP>
+__global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_kernel(const HopArgs a) {
+  extern __shared__ double red_smem[];
+  const unsigned per_cta = blockDim.y * NR;
+  const unsigned ntile = (a.nrhs + per_cta - 1) / per_cta;
+  const unsigned tile = blockIdx.x % ntile;
+  const unsigned rest = blockIdx.x / ntile;
+  const unsigned blk = (MODE == HOP_DW) ? (rest >> 1) : rest;
+  const uint32_t i = blk * blockDim.x + threadIdx.x;
+  const int rhs0 = (int)(tile * blockDim.y + threadIdx.y) * NR;
+  const int p = (MODE == HOP_DW) ? (int)(rest & 1) : a.p;
+  bool live[NR];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    live[k] = (i < (uint32_t)a.g.Vh) && (rhs0 + k < a.nrhs);
+    if (live[k] && a.cg) live[k] = (a.cg[rhs0 + k].mode == a.gate);
+    any |= live[k];
+  }
+  double red[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) red[k] = 0.0;
+  if (any) mr::site<P, FMT, MODE, DAG, EPI, NR>(a, i, rhs0, p, live, red);
+  if constexpr (EPI != EPI_NONE) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+      if (!live[k]) red[k] = 0.0;
+    mr::grid_reduce_nr<NR>(red, a.red, rhs0, a.nrhs, red_smem, blk, gridDim.x / ntile);
+  }
+}
+
+template <int P, int FMT, int MODE, bool DAG, int EPI, int NR>
+static cudaError_t launch_mr_one(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  if (L.bx % 32 != 0 || L.bx * L.by > 128 || L.by < 1) return cudaErrorInvalidValue;
+  dim3 block(L.bx, L.by, 1);
+  const unsigned nb = (unsigned)((a.g.Vh + L.bx - 1) / L.bx);
+  const unsigned ntile = (unsigned)((a.nrhs + L.by * NR - 1) / (L.by * NR));
+  dim3 grid((MODE == HOP_DW ? 2u * nb : nb) * ntile, 1u, 1u);
+  const size_t smem = (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32) * L.by * NR;
+  if (L.regcap)
+    hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 1><<<grid, block, smem, s>>>(a);
+  else
+    hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 0><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int FMT, bool DAG, int NR>
+static cudaError_t mr_dispatch_mode_epi(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  switch (L.mode) {
+    case HOP_DW:
+      if (L.epi == EPI_NONE) return launch_mr_one<P, FMT, HOP_DW, DAG, EPI_NONE, NR>(L, a, s);
+      break;
+    case HOP_P1:
+      if (L.epi == EPI_NONE) return launch_mr_one<P, FMT, HOP_P1, DAG, EPI_NONE, NR>(L, a, s);
+      break;
+    case HOP_P2:
+      if (L.epi == EPI_NONE) return launch_mr_one<P, FMT, HOP_P2, DAG, EPI_NONE, NR>(L, a, s);
+      if (L.epi == EPI_NORM) return launch_mr_one<P, FMT, HOP_P2, DAG, EPI_NORM, NR>(L, a, s);
+      if (L.epi == EPI_CG) return launch_mr_one<P, FMT, HOP_P2, DAG, EPI_CG, NR>(L, a, s);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int NR>
+static cudaError_t mr_dispatch(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
+  if (L.link_fmt == LINK_12)
+    return L.dagger ? mr_dispatch_mode_epi<P, LINK_12, true, NR>(L, a, s)
+                    : mr_dispatch_mode_epi<P, LINK_12, false, NR>(L, a, s);
+  return L.dagger ? mr_dispatch_mode_epi<P, LINK_18, true, NR>(L, a, s)
+                  : mr_dispatch_mode_epi<P, LINK_18, false, NR>(L, a, s);
+}
+
+}  // namespace oq

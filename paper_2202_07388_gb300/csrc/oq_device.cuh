@@ -149,7 +149,29 @@ struct Geom {
   int Lh3;    // L[3] / 2
   long Vh;    // V / 2
   float bc_t; // fermion factor for hops across the time boundary (-1 antiperiodic)
+  // 32-bit division by Lh3, L[2], L[1] (in that order) as n / d =
+  // (n * dm) >> ds, exact for n < 2^31 (geom_init_div)
+  uint32_t dm[3];
+  int ds[3];
 };
+
+// Multipliers for geom's 32-bit divisions: for d >= 1 let l be the smallest
+// integer with 2^l >= d, m = ceil(2^(31+l) / d) (< 2^32) and s = 31 + l.
+// With m d = 2^s + e, 0 <= e < d <= 2^l, n m / 2^s = n/d + n e / (d 2^s) and
+// the second term is below 1/d for n < 2^31, so the floor is floor(n / d).
+__host__ __device__ inline void geom_div_magic(uint32_t d, uint32_t* m, int* s) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  *m = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+  *s = 31 + l;
+}
+__host__ __device__ inline void geom_init_div(Geom& g) {
+  const uint32_t d[3] = {(uint32_t)g.Lh3, (uint32_t)g.L[2], (uint32_t)g.L[1]};
+  for (int k = 0; k < 3; ++k) geom_div_magic(d[k], &g.dm[k], &g.ds[k]);
+}
+__device__ __forceinline__ uint32_t geom_div(uint32_t n, uint32_t m, int s) {
+  return (uint32_t)(((unsigned long long)n * m) >> s);
+}
 
 // coordinates of eo site i of parity p
 __device__ __forceinline__ void eo_coords(const Geom& g, int p, long i, int x[4]) {

@@ -75,7 +75,9 @@ struct HopLaunch {
   int mode;      // HopMode
   int dagger;
   int epi;       // HopEpi
-  int bx, by;    // CTA shape: bx sites x by right-hand sides
+  int bx, by;    // CTA shape: bx sites x by groups of nr right-hand sides
+  int nr = 1;    // right-hand sides per thread (1: hop_kernel; 2, 4: hop_mr_kernel)
+  int regcap = 0;  // hop_mr_kernel: 1 = register-capped variant
   // batched launch over several systems (hop_batch_kernel) when sys != null:
   // per-system arguments and the (system, site block) tile list in device memory
   const HopArgs* sys = nullptr;
@@ -90,6 +92,13 @@ cudaError_t launch_hop_f32(const HopLaunch& L, const HopArgs& a, cudaStream_t s)
 cudaError_t launch_hop_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_df64(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+// several right-hand sides per thread (binary32 arithmetic types, nr = 2 or 4)
+cudaError_t launch_hop_mr2_f32(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_mr4_f32(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_mr2_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_mr4_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_mr2_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+cudaError_t launch_hop_mr4_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 
 __host__ __device__ inline int prec_bytes(int prec) {
   return (prec == P_F64 || prec == P_DF64) ? 8 : prec == P_F32 ? 4 : 2;

@@ -1,9 +1,11 @@
 // Autotuner for the stencil launch shape: for one (lattice, precision,
-// number of right-hand sides) it times every admissible CTA shape
-// (bx sites x by right-hand sides, bx a multiple of 32, bx*by <= 256) of the
-// full Dw and of both Dhat passes with CUDA events on scratch fields, and
-// keeps the fastest shape per mode in the handle.  Later launches of that
-// variant (any epilogue) use the chosen shape.
+// number of right-hand sides) it times every admissible launch of the full
+// Dw and of both Dhat passes with CUDA events on scratch fields: CTA shapes
+// (bx sites x by rows, bx a multiple of 32), one or several (2, 4)
+// right-hand sides per thread with or without a register cap, and both
+// binary32 link formats when the handle holds both.  The fastest launch per
+// mode is kept in the handle and used by every later launch of that variant
+// (any epilogue).  oq_tune_set pins a launch by hand.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -15,17 +17,57 @@ using namespace oq;
 
 namespace {
 
-std::vector<std::pair<int, int>> candidates(int nrhs) {
-  std::vector<std::pair<int, int>> c;
+std::vector<TuneVal> candidates(int prec, int nrhs) {
+  std::vector<TuneVal> c;
   const int bxs[] = {32, 64, 128, 256};
   for (int bx : bxs)
     for (int by = 1; by <= 8 && by <= nrhs; ++by) {
       if (bx * by > 256) continue;
       if (nrhs > 1 && by > 1 && nrhs % by != 0 && by != nrhs) continue;
       if (nrhs > 1 && by == 1 && bx < 64) continue;
-      c.push_back({bx, by});
+      TuneVal v;
+      v.bx = bx;
+      v.by = by;
+      c.push_back(v);
     }
+  // several right-hand sides per thread (binary32 arithmetic types)
+  if (prec == P_F32 || prec == P_BF16 || prec == P_F16) {
+    const int nrs[] = {2, 4};
+    for (int nr : nrs) {
+      if (nr > nrhs) continue;
+      for (int cap = 0; cap < 2; ++cap)
+        for (int bx : bxs)
+          for (int by = 1; by <= 2; ++by) {
+            if (bx * by > 128 || by * nr > nrhs) continue;
+            TuneVal v;
+            v.bx = bx;
+            v.by = by;
+            v.nr = nr;
+            v.regcap = cap;
+            c.push_back(v);
+          }
+    }
+  }
   return c;
+}
+
+bool valid_shape(const LatCtx& L, int prec, int nrhs, const TuneVal& v) {
+  if (v.bx < 32 || v.bx % 32 != 0 || v.by < 1 || v.by > nrhs) return false;
+  if (v.nr == 1) {
+    if (v.bx * v.by > 256 || v.regcap != 0) return false;
+  } else if (v.nr == 2 || v.nr == 4) {
+    if (prec != P_F32 && prec != P_BF16 && prec != P_F16) return false;
+    if (v.bx * v.by > 128 || (v.regcap != 0 && v.regcap != 1)) return false;
+  } else {
+    return false;
+  }
+  if (v.link_fmt != -1) {
+    if (prec == P_F64 || prec == P_DF64) return false;
+    if (v.link_fmt == LINK_12 && L.link_fmt != LINK_12) return false;
+    if (v.link_fmt == LINK_18 && L.link_fmt == LINK_12 && !L.u32_18.p) return false;
+    if (v.link_fmt != LINK_12 && v.link_fmt != LINK_18) return false;
+  }
+  return true;
 }
 
 }  // namespace
@@ -65,16 +107,17 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
       a.in_stride = a.in2_stride = a.out_stride = (long)half;
       a.half_bytes = (long)half;
     }
-    float best = 1e30f;
-    std::pair<int, int> best_shape{128, 1};
-    int best_fmt = L.link_fmt;
+    TuneVal best;
+    best.ms = 1e30f;
     // binary32 kernels may also read the 18-real copy of 12-real links
     const bool two_fmts = prec != P_F64 && prec != P_DF64 && L.link_fmt == LINK_12 && L.u32_18.p;
     for (int fmt = L.link_fmt; fmt >= 0; fmt = (two_fmts && fmt == LINK_12) ? LINK_18 : -1) {
-      for (auto c : candidates(nrhs)) {
+      for (TuneVal c : candidates(prec, nrhs)) {
         HopLaunch l = h->hop_launch(lat, prec, mode, 0, EPI_NONE, nrhs);
-        l.bx = c.first;
-        l.by = c.second;
+        l.bx = c.bx;
+        l.by = c.by;
+        l.nr = c.nr;
+        l.regcap = c.regcap;
         l.link_fmt = fmt;
         const HopArgs b = h->with_links(l, a);
         for (int w = 0; w < 2; ++w)
@@ -90,18 +133,16 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= reps;
-        if (ms < best) {
-          best = ms;
-          best_shape = c;
-          best_fmt = fmt;
+        if (ms < best.ms) {
+          best = c;
+          best.link_fmt = fmt;
+          best.ms = ms;
         }
       }
       if (ret) break;
     }
     if (ret) break;
-    h->tuned[TuneKey{lat, prec, mode, nrhs}] = best_shape;
-    h->tuned_ms[TuneKey{lat, prec, mode, nrhs}] = best;
-    h->tuned_fmt[TuneKey{lat, prec, mode, nrhs}] = best_fmt;
+    h->tuned[TuneKey{lat, prec, mode, nrhs}] = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -109,13 +150,35 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
 }
 
 extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
-                           int* link_fmt) {
+                           int* link_fmt, int* nr, int* regcap) {
   if (!h || !bx || !by || !ms || lat < 0 || lat >= (int)h->lats.size()) return OQ_ERR_ARG;
   auto it = h->tuned.find(TuneKey{lat, prec, mode, nrhs});
   if (it == h->tuned.end()) return OQ_ERR_STATE;
-  *bx = it->second.first;
-  *by = it->second.second;
-  *ms = h->tuned_ms[TuneKey{lat, prec, mode, nrhs}];
-  if (link_fmt) *link_fmt = h->tuned_fmt[TuneKey{lat, prec, mode, nrhs}];
+  const TuneVal& v = it->second;
+  *bx = v.bx;
+  *by = v.by;
+  *ms = v.ms;
+  if (link_fmt) *link_fmt = v.link_fmt >= 0 ? v.link_fmt : h->lats[lat].link_fmt;
+  if (nr) *nr = v.nr;
+  if (regcap) *regcap = v.regcap;
+  return OQ_OK;
+}
+
+extern "C" int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int by, int nr, int regcap,
+                           int link_fmt) {
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 4 || mode < 0 || mode > 2 || nrhs < 1 ||
+      nrhs > 64)
+    return OQ_ERR_ARG;
+  const LatCtx& L = h->lats[lat];
+  if (!L.has_gauge) return OQ_ERR_STATE;
+  TuneVal v;
+  v.bx = bx;
+  v.by = by;
+  v.nr = nr;
+  v.regcap = regcap;
+  v.link_fmt = link_fmt;
+  v.ms = 0.f;
+  if (!valid_shape(L, prec, nrhs, v)) return OQ_ERR_ARG;
+  h->tuned[TuneKey{lat, prec, mode, nrhs}] = v;
   return OQ_OK;
 }

@@ -86,7 +86,10 @@ _SIGS = {
     "oq_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
     "oq_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
     "oq_tune_get": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                              C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+                              C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                              C.POINTER(C.c_int)]),
+    "oq_tune_set": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                              C.c_int]),
     "oq_profile_start": (C.c_int, [_P]),
     "oq_kernel_launches": (C.c_longlong, [_P]),
     "oq_profile_stop": (C.c_int, [_P, C.POINTER(OqKernelTime), C.c_int, C.POINTER(C.c_int)]),
@@ -307,14 +310,22 @@ class Handle:
 
     # tuning ------------------------------------------------------------
     def autotune(self, prec, nrhs=1, lat=0, stream=None):
+        """Tune the stencil launches of (lat, prec, nrhs); returns per mode (0 Dw, 1 Dhat pass 1,
+        2 Dhat pass 2) the chosen (bx, by, ms, link format, rhs per thread, register cap)."""
         _check(lib().oq_autotune(self.h, lat, prec, nrhs, _stream(stream)), "oq_autotune")
-        out = {}
-        for mode in (0, 1, 2):
-            bx, by, ms, fmt = C.c_int(), C.c_int(), C.c_float(), C.c_int()
-            _check(lib().oq_tune_get(self.h, lat, prec, mode, nrhs, C.byref(bx), C.byref(by), C.byref(ms),
-                                     C.byref(fmt)), "oq_tune_get")
-            out[mode] = (bx.value, by.value, ms.value, "12-real" if fmt.value == LINK_12 else "18-real")
-        return out
+        return {mode: self.tune_get(prec, mode, nrhs, lat) for mode in (0, 1, 2)}
+
+    def tune_get(self, prec, mode, nrhs=1, lat=0):
+        bx, by, ms, fmt, nr, cap = C.c_int(), C.c_int(), C.c_float(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().oq_tune_get(self.h, lat, prec, mode, nrhs, C.byref(bx), C.byref(by), C.byref(ms),
+                                 C.byref(fmt), C.byref(nr), C.byref(cap)), "oq_tune_get")
+        return (bx.value, by.value, ms.value, "12-real" if fmt.value == LINK_12 else "18-real", nr.value, cap.value)
+
+    def tune_set(self, prec, mode, nrhs, bx, by, nr=1, regcap=0, link_fmt=-1, lat=0, check=True):
+        rc = lib().oq_tune_set(self.h, lat, prec, mode, nrhs, bx, by, nr, regcap, link_fmt)
+        if check:
+            _check(rc, "oq_tune_set")
+        return rc
 
     # instrumentation ---------------------------------------------------
     def profile_start(self):

@@ -1,0 +1,110 @@
+"""GPU parity of the multi-right-hand-side stencil (2 or 4 right-hand sides
+per thread, packed two-lane binary32 arithmetic, with and without the
+register cap) against the FP64 oracle, pinned with oq_tune_set: full Dw,
+Dhat and their adjoints for every binary32-arithmetic storage type and both
+link formats, on ragged site counts and right-hand-side counts that are not
+multiples of the per-thread count; the fused CG epilogue through a batched
+CGNE solve to a binary64 residual of 1e-10."""
+import numpy as np
+import pytest
+
+from oracle import dirac
+from paper_2202_07388_gb300 import synth
+from tests.gpu_cases import TOL, oracle_case, make_handle, to_dev, from_dev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((6, 4, 2, 6), 0.5, 2, 0.135, 1.0),       # Vh = 144: ragged tail for every bx
+         ((8, 6, 4, 10), 0.5, 3, 0.1365, 1.3)]     # Vh = 960
+
+
+def _oq():
+    from paper_2202_07388_gb300 import oq
+    return oq
+
+
+def _pin(h, prec, nrhs, bx, by, nr, cap, fmt):
+    for mode in (0, 1, 2):
+        h.tune_set(prec, mode, nrhs, bx, by, nr=nr, regcap=cap, link_fmt=fmt)
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", [1, 2, 3])
+@pytest.mark.parametrize("nr,nrhs,bx,by", [(2, 5, 64, 2), (4, 5, 32, 1), (4, 8, 128, 1), (2, 2, 32, 1)])
+@pytest.mark.parametrize("cap", [0, 1])
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_multi_rhs_dw_and_dw_hat(case, prec, nr, nrhs, bx, by, cap, fmt):
+    oq = _oq()
+    dims, eps, seed, kappa, csw = case
+    u, a, ainv = oracle_case(dims, eps, seed, kappa, csw)
+    h = make_handle(dims, u, kappa, csw, oq.LINK_12)
+    _pin(h, prec, nrhs, bx, by, nr, cap, fmt)
+    psi = synth.make_source(dims, seed + 400, nrhs=nrhs)
+    for dagger in (False, True):
+        pin, pout = h.new_packed(prec, nrhs=nrhs), h.new_packed(prec, nrhs=nrhs)
+        h.pack(to_dev(psi), pin, prec, nrhs=nrhs)
+        h.dw(pin, pout, prec, nrhs=nrhs, dagger=dagger)
+        out = to_dev(np.zeros_like(psi))
+        h.unpack(pout, out, prec, nrhs=nrhs)
+        got = from_dev(out, psi.shape)
+        for k in range(nrhs):
+            ref = dirac.dw_dagger(u, a, psi[k]) if dagger else dirac.dw(u, a, psi[k])
+            assert rel_err(got[k], ref) < TOL[prec], (k, dagger)
+        ev = np.stack([dirac.even_part(p) for p in psi])
+        pin, pout = h.new_packed(prec, oq.EVEN, nrhs=nrhs), h.new_packed(prec, oq.EVEN, nrhs=nrhs)
+        h.pack(to_dev(ev), pin, prec, oq.EVEN, nrhs=nrhs)
+        h.dw_hat(pin, pout, prec, nrhs=nrhs, dagger=dagger)
+        out = to_dev(np.zeros_like(ev))
+        h.unpack(pout, out, prec, oq.EVEN, nrhs=nrhs)
+        got = from_dev(out, ev.shape)
+        for k in range(nrhs):
+            ref = dirac.dw_hat_dagger(u, a, ainv, ev[k]) if dagger else dirac.dw_hat(u, a, ainv, ev[k])
+            assert rel_err(got[k], ref) < TOL[prec], (k, dagger)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("nr,cap", [(2, 0), (4, 1)])
+def test_multi_rhs_cgne_epilogues(prec, nr, cap):
+    """The norm and CG-update epilogues of the multi-rhs kernel inside the
+    batched CGNE: 5 right-hand sides (a ragged group), every one to a binary64
+    normal-equation residual of 1e-10, the same step counts as the one-rhs
+    kernel up to rounding."""
+    oq = _oq()
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.135, 1.0)
+    n = 5
+    eta = np.stack([dirac.even_part(e) for e in synth.make_source(dims, 91, nrhs=n)])
+    steps = {}
+    for variant in ("one", "multi"):
+        h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+        if variant == "multi":
+            _pin(h, prec, n, 32, 1, nr, cap, -1)
+        else:
+            _pin(h, prec, n, 64, 1, 1, 0, -1)
+        psi = to_dev(np.zeros_like(eta))
+        rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5000, sdtype=prec), nrhs=n)
+        assert rc == oq.OK
+        x = from_dev(psi, eta.shape)
+        for k in range(n):
+            ax = dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, x[k]))
+            r = np.linalg.norm((eta[k] - ax).reshape(-1)) / np.linalg.norm(eta[k].reshape(-1))
+            assert r <= 1.2e-10 and st[k]["converged"], (variant, k, r)
+        steps[variant] = [s["steps"] for s in st]
+    for a_, b_ in zip(steps["one"], steps["multi"]):
+        assert abs(a_ - b_) <= 3
+
+
+def test_tune_set_rejects_inadmissible_launches():
+    oq = _oq()
+    dims = (4, 4, 4, 4)
+    u, a, ainv = oracle_case(dims, 0.3, 1, 0.13, 1.0)
+    h = make_handle(dims, u, 0.13, 1.0, oq.LINK_12)
+    assert h.tune_set(oq.F16, 1, 4, 48, 1, check=False) == oq.ERR_ARG            # bx not a multiple of 32
+    assert h.tune_set(oq.F16, 1, 4, 128, 2, nr=2, check=False) == oq.ERR_ARG     # 256 threads with nr > 1
+    assert h.tune_set(oq.F64, 1, 4, 64, 1, nr=2, check=False) == oq.ERR_ARG      # binary64: one rhs per thread
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=3, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=1, regcap=1, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=4, regcap=1) == oq.OK
+    assert h.tune_get(oq.F16, 1, 4)[4:] == (4, 1)
+    h2 = make_handle(dims, u, 0.13, 1.0, oq.LINK_18)
+    assert h2.tune_set(oq.F32, 1, 1, 64, 1, link_fmt=oq.LINK_12, check=False) == oq.ERR_ARG
