@@ -392,6 +392,29 @@ def run_ours(args):
         tts["speedup_fp16_vs_fp64"] = tts["fp64"]["s"] / tts["fp16"]["s"]
         tts["batched_12rhs_f16_s_per_rhs"] = (t_ms * 1e-3 / args.steps) / NRHS
         tts["speedup_batched_f16_vs_fp64_per_rhs"] = tts["fp64"]["s"] / tts["batched_12rhs_f16_s_per_rhs"]
+        # the same solves with double-float intermediate resets (binary64 confirmation at the end)
+        h.set_option(oq.OPT_DF64_RESETS, 1)
+        for name, sd in (("fp16_df64_resets", oq.F16), ("bf16_df64_resets", oq.BF16)):
+            p1 = oq.SolverParams(res=RES, nmx=50000, sdtype=sd)
+            h.cgne(eta1, psi1, p1, nrhs=1)
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            rc, st1 = h.cgne(eta1, psi1, p1, nrhs=1)
+            torch.cuda.synchronize()
+            tts[name] = {"s": time.perf_counter() - s0, "steps": st1[0]["steps"], "resets": st1[0]["resets"],
+                         "true_rel_res": st1[0]["true_rel_res"], "converged": st1[0]["converged"]}
+        torch.cuda.synchronize()
+        h.profile_start()
+        s0 = time.perf_counter()
+        rc, stb = h.cgne(eta, psi, prm, nrhs=NRHS)
+        torch.cuda.synchronize()
+        tts["batched_12rhs_f16_df64_resets_s_per_rhs"] = (time.perf_counter() - s0) / NRHS
+        tts["batched_12rhs_f16_df64_resets_max_res"] = max(x["true_rel_res"] for x in stb)
+        tts["batched_12rhs_f16_df64_resets_resets"] = [x["resets"] for x in stb]
+        tts["batched_12rhs_f16_df64_resets_kernels"] = [
+            {"kernel": f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}",
+             "launches": p["launches"], "ms": p["total_ms"]} for p in h.profile_stop()]
+        h.set_option(oq.OPT_DF64_RESETS, 0)
 
     st_last = statuses[-1]
     if rank == 0:

@@ -51,10 +51,15 @@ extern "C" {
 typedef struct oq_ctx* oq_handle;
 
 /* storage precision of spinor fields (arithmetic is binary32 for F32/BF16/F16).
- * OQ_DF64: binary64 storage (the OQ_F64 layout) with double-float arithmetic
- * (hi + lo pairs of binary32, ~48 significant bits) on the binary32 pipes,
- * accepted by oq_dw_apply, oq_dw_hat_apply, oq_autotune and the packing
- * calls; the CGNE uses it for intermediate reset steps. */
+ * OQ_DF64: double-float storage and arithmetic: every real is an unevaluated
+ * sum hi + lo of two binary32 numbers (~48 significant bits), stored as the
+ * pair (hi, lo) in 8 bytes (the OQ_F64 sizes; one complex per 16-byte chunk:
+ * re.hi, re.lo, im.hi, im.lo), with arithmetic on the binary32 pipes.
+ * Accepted by oq_dw_apply, oq_dw_hat_apply, oq_autotune and the packing
+ * calls (packing splits binary64 values, unpacking returns hi + lo); the
+ * kernels read double-float splits of the links and clover blocks that the
+ * handle makes from the binary64 ones on first use; the CGNE uses it for
+ * intermediate reset steps (OQ_OPT_DF64_RESETS). */
 enum { OQ_F64 = 0, OQ_F32 = 1, OQ_BF16 = 2, OQ_F16 = 3, OQ_DF64 = 4 };
 /* storage of the binary32 link copy: 18 reals, or 12 reals with the third
  * row rebuilt as conj(row0 x row1) (SU(3) links only) */

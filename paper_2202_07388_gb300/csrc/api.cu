@@ -116,6 +116,7 @@ extern "C" int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int li
     return OQ_ERR_CUDA;
   L.has_gauge = true;
   L.has_clover = false;
+  L.df_ready = false;
   return OQ_OK;
 }
 
@@ -142,6 +143,7 @@ extern "C" int oq_clover_build(oq_handle h, int lat, double kappa, double csw, v
   L.kappa = kappa;
   L.csw = csw;
   L.has_clover = true;
+  L.df_ready = false;
   return OQ_OK;
 }
 
@@ -149,8 +151,7 @@ static bool valid_lat(oq_handle h, int lat) { return h && lat >= 0 && lat < (int
 
 extern "C" int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const double* canon_dev, void* packed_dev,
                               double scale, int nrhs, void* stream) {
-  if (prec == P_DF64) prec = P_F64;  // same binary64 storage
-  if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 3 || subset < 0 || subset > 2 ||
+  if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 4 || subset < 0 || subset > 2 ||
       nrhs < 1 || !(scale != 0.0) || !isfinite(scale))
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
@@ -164,8 +165,7 @@ extern "C" int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const 
 
 extern "C" int oq_spinor_unpack(oq_handle h, int lat, int prec, int subset, const void* packed_dev, double* canon_dev,
                                 double scale, int nrhs, void* stream) {
-  if (prec == P_DF64) prec = P_F64;  // same binary64 storage
-  if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 3 || subset < 0 || subset > 2 ||
+  if (!valid_lat(h, lat) || !canon_dev || !packed_dev || prec < 0 || prec > 4 || subset < 0 || subset > 2 ||
       nrhs < 1 || !(scale != 0.0) || !isfinite(scale))
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
@@ -190,6 +190,10 @@ extern "C" int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, v
   if (!L.has_clover) return OQ_ERR_STATE;
   const size_t full = oq_spinor_bytes(h, lat, prec, OQ_FULL);
   if (overlap(in_dev, out_dev, full * nrhs)) return OQ_ERR_ARG;
+  if (prec == P_DF64) {
+    const int rc = h->ensure_df(lat, (cudaStream_t)stream);
+    if (rc) return rc;
+  }
   HopArgs a = h->hop_args(lat, prec);
   a.in = in_dev;
   a.in2 = in_dev;
@@ -212,6 +216,10 @@ extern "C" int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_de
   int rc = h->workspace(lat, "dwhat_t", half * nrhs, &t);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == P_DF64) {
+    rc = h->ensure_df(lat, s);
+    if (rc) return rc;
+  }
   HopArgs a = h->hop_args(lat, prec);
   a.nrhs = nrhs;
   a.in_stride = a.in2_stride = a.out_stride = (long)half;

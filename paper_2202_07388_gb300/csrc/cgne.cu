@@ -150,8 +150,24 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   // the reset step for all rhs in MODE_RESET.  rp: arithmetic of the residual
   // recomputation (binary64 storage either way); accumulate: add s x_s to x_d
   // first (false re-checks the same x_d)
+  // double-float resets read the splits of x_d and eta (DF64 storage, the
+  // size of binary64) and write r_d in binary64
+  void *xdf = nullptr, *etadf = nullptr;
   auto reset_step = [&](int rp, bool accumulate) -> int {
     if (accumulate) KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
+    const void* xin = xd;
+    const void* eta_in = eta64;
+    if (rp == P_DF64) {
+      RK(h->ensure_df(lat, s));
+      if (!xdf) {
+        RK(h->workspace(lat, "cg_xdf", h64 * nrhs, &xdf));
+        RK(h->workspace(lat, "cg_etadf", h64 * nrhs, &etadf));
+        KL(split_f64((const double*)eta64, etadf, h64 * nrhs / sizeof(double), s));
+      }
+      KL(split_f64((const double*)xd, xdf, h64 * nrhs / sizeof(double), s));
+      xin = xdf;
+      eta_in = etadf;
+    }
     HopArgs a = h->hop_args(lat, rp);
     a.nrhs = nrhs;
     a.cg = h->cg_dev;
@@ -159,15 +175,15 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     a.in_stride = a.in2_stride = a.out_stride = (long)h64;
     a.half_bytes = (long)h64;
     // t = A_oo^-1 D_oe x_d ; u = Dhat x_d
-    a.in = xd; a.out = t64; a.p = 1;
+    a.in = xin; a.out = t64; a.p = 1;
     RK(h->run_hop(h->hop_launch(lat, rp, HOP_P1, 0, EPI_NONE, nrhs), a, s));
-    a.in = t64; a.in2 = xd; a.out = u64v; a.p = 0;
+    a.in = t64; a.in2 = xin; a.out = u64v; a.p = 0;
     RK(h->run_hop(h->hop_launch(lat, rp, HOP_P2, 0, EPI_NONE, nrhs), a, s));
     // t = ..., r_d = eta - Dhat^dag u, ||r_d||^2
     a.in = u64v; a.out = t64; a.p = 1;
     RK(h->run_hop(h->hop_launch(lat, rp, HOP_P1, 1, EPI_NONE, nrhs), a, s));
     a.in = t64; a.in2 = u64v; a.out = rd; a.p = 0;
-    a.ep_eta = eta64; a.ep_eta_stride = (long)h64;
+    a.ep_eta = eta_in; a.ep_eta_stride = (long)h64;
     a.red = h->red_args(FIN_RD2, MODE_RESET);
     RK(h->run_hop(h->hop_launch(lat, rp, HOP_P2, 1, EPI_RESID64, nrhs), a, s));
     return OQ_OK;

@@ -12,6 +12,7 @@
 
 #include "../../include/oq.h"
 #include "oq_internal.h"
+#include "oq_kernels.h"
 
 namespace oq {
 
@@ -27,6 +28,10 @@ struct LatCtx {
   double kappa = 0.0, csw = 0.0;
   DevBuf u64, u32, a64, a32, i64, i32;
   DevBuf u32_18;  // 18-real binary32 copy kept next to 12-real links
+  // double-float (hi, lo) splits of the binary64 links, clover and inverse
+  // clover, made on the first DF64 use after an upload / clover build
+  DevBuf udf, adf, idf;
+  bool df_ready = false;
   std::map<std::string, DevBuf> ws;
 };
 
@@ -37,14 +42,16 @@ struct ProfRec {
   double bytes;
 };
 
-// tuned CTA shape of one stencil variant
+// tuned CTA shape of one stencil variant; epi = EPI_NONE is the entry for
+// every epilogue the tuner did not time separately
 struct TuneKey {
-  int lat, prec, mode, nrhs;
+  int lat, prec, mode, nrhs, epi;
   bool operator<(const TuneKey& o) const {
     if (lat != o.lat) return lat < o.lat;
     if (prec != o.prec) return prec < o.prec;
     if (mode != o.mode) return mode < o.mode;
-    return nrhs < o.nrhs;
+    if (nrhs != o.nrhs) return nrhs < o.nrhs;
+    return epi < o.epi;
   }
 };
 
@@ -198,13 +205,37 @@ struct oq_ctx {
     oq::HopArgs a;
     memset(&a, 0, sizeof(a));
     a.g = L.g;
-    const bool f64 = prec == oq::P_F64 || prec == oq::P_DF64;
-    a.links = f64 ? L.u64.p : L.u32.p;
-    a.clov = f64 ? L.a64.p : L.a32.p;
-    a.cinv = f64 ? L.i64.p : L.i32.p;
+    if (prec == oq::P_DF64) {  // ensure_df(lat) has made the splits
+      a.links = L.udf.p;
+      a.clov = L.adf.p;
+      a.cinv = L.idf.p;
+    } else {
+      const bool f64 = prec == oq::P_F64;
+      a.links = f64 ? L.u64.p : L.u32.p;
+      a.clov = f64 ? L.a64.p : L.a32.p;
+      a.cinv = f64 ? L.i64.p : L.i32.p;
+    }
     a.nrhs = 1;
     a.lat = lat;
     return a;
+  }
+
+  // the double-float splits of links and clover that DF64 kernels read
+  int ensure_df(int lat, cudaStream_t s) {
+    oq::LatCtx& L = lats[lat];
+    if (L.df_ready) return OQ_OK;
+    if (!L.has_clover) return OQ_ERR_STATE;
+    const size_t nu = (size_t)2 * 4 * 18 * L.g.Vh, na = (size_t)2 * 72 * L.g.Vh;
+    int rc = alloc(&L.udf, nu * sizeof(float2));
+    if (!rc) rc = alloc(&L.adf, na * sizeof(float2));
+    if (!rc) rc = alloc(&L.idf, na * sizeof(float2));
+    if (rc) return rc;
+    if (oq::split_f64((const double*)L.u64.p, L.udf.p, nu, s) != cudaSuccess ||
+        oq::split_f64((const double*)L.a64.p, L.adf.p, na, s) != cudaSuccess ||
+        oq::split_f64((const double*)L.i64.p, L.idf.p, na, s) != cudaSuccess)
+      return OQ_ERR_CUDA;
+    L.df_ready = true;
+    return OQ_OK;
   }
 
   oq::HopLaunch hop_launch(int lat, int prec, int mode, int dagger, int epi, int nrhs) {
@@ -214,7 +245,8 @@ struct oq_ctx {
     l.mode = mode;
     l.dagger = dagger;
     l.epi = epi;
-    auto it = tuned.find(oq::TuneKey{lat, prec, mode, nrhs});
+    auto it = tuned.find(oq::TuneKey{lat, prec, mode, nrhs, epi});
+    if (it == tuned.end()) it = tuned.find(oq::TuneKey{lat, prec, mode, nrhs, oq::EPI_NONE});
     if (it != tuned.end()) {
       l.bx = it->second.bx;
       l.by = it->second.by;
@@ -301,7 +333,7 @@ struct oq_ctx {
 
   void release() {
     for (auto& L : lats) {
-      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18};
+      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18, &L.udf, &L.adf, &L.idf};
       for (auto* b : bs) cudaFree(b->p);
       for (auto& kv : L.ws) cudaFree(kv.second.p);
     }

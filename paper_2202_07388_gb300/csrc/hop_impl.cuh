@@ -126,7 +126,17 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
       for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) res.c[s][c] = e.c[s][c] - res.c[s][c];
-      store_spinor<P>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, res);
+      if constexpr (P == P_DF64) {
+        // the reset residual is kept in binary64 (hi + lo is exact in binary64)
+        Spinor<double> r64;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) r64.c[s][c] = cx<double>{(double)res.c[s][c].re, (double)res.c[s][c].im};
+        store_spinor<P_F64>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, r64);
+      } else {
+        store_spinor<P>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, res);
+      }
       double acc2 = 0.0;
 #pragma unroll
       for (int s = 0; s < 4; ++s)

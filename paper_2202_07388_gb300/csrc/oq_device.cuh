@@ -6,36 +6,47 @@
 //   spinor  : 24 reals/site, stored as chunks of 16 bytes, chunk-major:
 //             chunk c of site i at base[c*Vh + i].  Real index r of the site
 //             vector = 2*(3*spin + colour) + (0 re | 1 im).
-//             F64: 12 chunks (double2), F32: 6 chunks (float4),
-//             BF16/F16: 3 chunks (8 halves each).
+//             F64: 12 chunks (double2), DF64: 12 chunks (float4 = re.hi,
+//             re.lo, im.hi, im.lo), F32: 6 chunks (float4), BF16/F16: 3
+//             chunks (8 halves each).
 //   links   : U_mu(x) at [parity(x)][mu][chunk][Vh];
-//             18-real: 9 chunks (F64 double2 / F32 float2), element a*3+b;
+//             18-real: 9 chunks (F64 double2 / DF64 float4 / F32 float2),
+//             element a*3+b;
 //             12-real (F32, SU(3) only): 3 float4 chunks holding rows 0 and 1,
 //             row 2 = conj(row0 x row1).
 //   clover  : per site two Hermitian 6x6 blocks (chirality +, -), each as
 //             6 real diagonal entries then the 15 upper off-diagonal complex
 //             entries in row-major order (36 reals/block, 72 reals/site);
-//             F64: 36 double2 chunks, F32: 18 float4 chunks, [parity][chunk][Vh].
+//             F64: 36 double2 chunks, DF64: 36 float4 chunks (two reals
+//             as hi, lo, hi, lo), F32: 18 float4 chunks, [parity][chunk][Vh].
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace oq {
 
-// P_DF64 (internal): binary64 storage, "double-float" arithmetic (a value is
-// an unevaluated sum hi + lo of two binary32 numbers, ~48 significant bits)
-// on the binary32 pipes, for the reset-step residuals on a GPU whose binary64
-// rate is far below its binary32 rate.
+// P_DF64: "double-float" values (an unevaluated sum hi + lo of two binary32
+// numbers with |lo| <= ulp(hi)/2, ~48 significant bits) stored as (hi, lo)
+// pairs in the 8 bytes of a binary64 value, with arithmetic on the binary32
+// pipes, for the reset-step residuals on a GPU whose binary64 rate is far
+// below its binary32 rate.  Operands are split from binary64 once (links,
+// clover, the solution vector), never inside the stencil.
 enum Prec : int { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3, P_DF64 = 4 };
 
 // ---------------------------------------------------------------------------
-// double-float arithmetic: error-free transformations (Knuth's two-sum,
-// Dekker's fast two-sum, the FMA two-product) combined into the accurate
-// double-word addition and multiplication of Joldes, Muller and Popescu
-// (ACM TOMS 44, 2017).  Explicit _rn intrinsics keep the compiler from
-// contracting or reassociating the compensated steps.
+// double-float arithmetic from error-free transformations: Knuth's two-sum,
+// Dekker's fast two-sum and the FMA two-product.  Sums use the "sloppy"
+// double-word addition (two-sum of the high parts, the low parts added,
+// renormalised), whose absolute error is a few u^2 (|x| + |y|), u = 2^-24:
+// the operands' own magnitudes bound every error of a stencil sum, which is
+// the accuracy a residual recomputation needs.  A product is added to an
+// accumulator with one renormalisation in all (Joldes, Muller, Popescu, ACM
+// TOMS 44, 2017, for the building blocks).  Explicit _rn intrinsics keep the
+// compiler from contracting or reassociating the compensated steps.
 // ---------------------------------------------------------------------------
 struct dfloat {
   float hi, lo;
@@ -61,10 +72,8 @@ __device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
   return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 __device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
-  dfloat s = df_two_sum(x.hi, y.hi);
-  const dfloat t = df_two_sum(x.lo, y.lo);
-  s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+  const dfloat s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 __device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
@@ -79,7 +88,16 @@ __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) {
   x = x + y;
   return x;
 }
-__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+// a * b + c: the two-product of the high parts with the cross terms, added
+// to c by a two-sum of the high parts, one renormalisation at the end
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const dfloat s = df_two_sum(c.hi, p);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(c.lo, e)));
+}
 using ::fma;  // keep the float / double overloads visible next to the dfloat one
 enum LinkFmt : int { LINK_18 = 0, LINK_12 = 1 };
 
@@ -211,7 +229,7 @@ template <> struct PrecTraits<P_F64> { typedef double R; typedef double2 Chunk; 
 template <> struct PrecTraits<P_F32> { typedef float R;  typedef float4 Chunk;  static const int nchunk = 6;  static const int bytes = 4; };
 template <> struct PrecTraits<P_BF16> { typedef float R; typedef uint4 Chunk;   static const int nchunk = 3;  static const int bytes = 2; };
 template <> struct PrecTraits<P_F16> { typedef float R;  typedef uint4 Chunk;   static const int nchunk = 3;  static const int bytes = 2; };
-template <> struct PrecTraits<P_DF64> { typedef dfloat R; typedef double2 Chunk; static const int nchunk = 12; static const int bytes = 8; };
+template <> struct PrecTraits<P_DF64> { typedef dfloat R; typedef float4 Chunk;  static const int nchunk = 12; static const int bytes = 8; };
 
 template <typename T>
 __device__ __forceinline__ T ldg_nc(const T* p) { return __ldg(p); }
@@ -239,12 +257,20 @@ __device__ __forceinline__ void load_spinor(const void* base, long Vh, long i,
                                             Spinor<typename PrecTraits<P>::R>& s) {
   typedef typename PrecTraits<P>::R R;
   cx<R>* f = &s.c[0][0];
-  if constexpr (P == P_F64 || P == P_DF64) {
+  if constexpr (P == P_F64) {
     const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       double2 v = ldg_nc(b + c * Vh + i);
       f[c] = cx<R>{R(v.x), R(v.y)};
+    }
+  } else if constexpr (P == P_DF64) {
+    // one complex per chunk: (re.hi, re.lo, im.hi, im.lo)
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      float4 v = ldg_nc(b + c * Vh + i);
+      f[c] = cx<R>{dfloat(v.x, v.y), dfloat(v.z, v.w)};
     }
   } else if constexpr (P == P_F32) {
     const float4* b = reinterpret_cast<const float4*>(base);
@@ -274,10 +300,14 @@ __device__ __forceinline__ void store_spinor(void* base, long Vh, long i,
                                              const Spinor<typename PrecTraits<P>::R>& s) {
   typedef typename PrecTraits<P>::R R;
   const cx<R>* f = &s.c[0][0];
-  if constexpr (P == P_F64 || P == P_DF64) {
+  if constexpr (P == P_F64) {
     double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; ++c) b[c * Vh + i] = make_double2((double)f[c].re, (double)f[c].im);
+  } else if constexpr (P == P_DF64) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) b[c * Vh + i] = make_float4(f[c].re.hi, f[c].re.lo, f[c].im.hi, f[c].im.lo);
   } else if constexpr (P == P_F32) {
     float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll
@@ -336,7 +366,15 @@ __device__ __forceinline__ void round_trip(Spinor<R>& s) {
 // double for F64 storage.
 template <typename R, int FMT>
 __device__ __forceinline__ void load_link(const void* base, long Vh, int p, int mu, long i, Su3<R>& u) {
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (std::is_same<R, dfloat>::value) {
+    // split binary64 links: one complex element per (re.hi, re.lo, im.hi, im.lo) chunk
+    const float4* b = reinterpret_cast<const float4*>(base) + ((long)(p * 4 + mu) * 9) * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float4 v = ldg_nc(b + k * Vh + i);
+      u.m[k / 3][k % 3] = cx<R>{dfloat(v.x, v.y), dfloat(v.z, v.w)};
+    }
+  } else if constexpr (sizeof(R) == 8) {
     const double2* b = reinterpret_cast<const double2*>(base) + ((long)(p * 4 + mu) * 9) * Vh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -408,7 +446,21 @@ __device__ __forceinline__ void clover_apply(const void* base, long Vh, int p, l
   for (int b = 0; b < 2; ++b) {
     R d[6];
     cx<R> off[15];
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (std::is_same<R, dfloat>::value) {
+      // split binary64 clover: chunk k holds reals 2k, 2k+1 as (hi, lo, hi, lo)
+      const float4* q = reinterpret_cast<const float4*>(base) + (long)p * 36 * Vh;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float4 w = ldg_nc(q + (18 * b + k) * Vh + i);
+        d[2 * k] = dfloat(w.x, w.y);
+        d[2 * k + 1] = dfloat(w.z, w.w);
+      }
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        float4 w = ldg_nc(q + (18 * b + 3 + k) * Vh + i);
+        off[k] = cx<R>{dfloat(w.x, w.y), dfloat(w.z, w.w)};
+      }
+    } else if constexpr (sizeof(R) == 8) {
       const double2* q = reinterpret_cast<const double2*>(base) + (long)p * 36 * Vh;
       // block b occupies chunks 18b .. 18b+17: 3 chunks of diagonal, 15 off
 #pragma unroll

@@ -12,6 +12,8 @@ cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon
                         int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s);
 cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
                           int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s);
+// binary64 array of n values -> n double-float (hi, lo) pairs
+cudaError_t split_f64(const double* in, void* out, size_t n, cudaStream_t s);
 cudaError_t build_clover(const Geom& g, const double* u64, double kappa, double csw, double* a64, float* a32,
                          double* i64, float* i32, int* status_dev, cudaStream_t s);
 

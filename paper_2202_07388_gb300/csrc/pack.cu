@@ -128,6 +128,7 @@ cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon
     case P_F32: pack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
     case P_BF16: pack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
     case P_F16: pack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+    case P_DF64: pack_spinor_kernel<P_DF64><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -144,8 +145,27 @@ cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, d
     case P_F32: unpack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
     case P_BF16: unpack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
     case P_F16: unpack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
+    case P_DF64: unpack_spinor_kernel<P_DF64><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// binary64 array -> double-float pairs (hi = rn(x), lo = rn(x - hi)), element
+// by element: a binary64-layout field or table becomes its DF64 layout
+__global__ void split_f64_kernel(const double* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const double x = in[k];
+    const float hi = __double2float_rn(x);
+    out[k] = make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+}
+
+cudaError_t split_f64(const double* in, void* out, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  split_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, reinterpret_cast<float2*>(out), n);
   return cudaGetLastError();
 }
 

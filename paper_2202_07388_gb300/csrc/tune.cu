@@ -4,8 +4,10 @@
 // (bx sites x by rows, bx a multiple of 32), one or several (2, 4)
 // right-hand sides per thread with or without a register cap, and both
 // binary32 link formats when the handle holds both.  The fastest launch per
-// mode is kept in the handle and used by every later launch of that variant
-// (any epilogue).  oq_tune_set pins a launch by hand.
+// mode is kept in the handle and used by every later launch of that mode;
+// pass 2 is also timed with its norm and CG-update epilogues (on scratch
+// operands: alpha = 0, reductions only stored), which keep their own choice.
+// oq_tune_set pins a launch by hand for every epilogue of a mode.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -78,6 +80,10 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == P_DF64) {
+    const int rc = h->ensure_df(lat, s);
+    if (rc) return rc;
+  }
   const size_t full = 2 * (size_t)spinor_half_bytes(L.g.Vh, prec) * nrhs;
   void *in = nullptr, *out = nullptr;
   int rc = h->workspace(lat, "tune_in", full, &in);
@@ -91,9 +97,38 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
     return OQ_ERR_CUDA;
   }
   const size_t half = full / 2 / nrhs;
-  const int modes[] = {HOP_DW, HOP_P1, HOP_P2};
   int ret = OQ_OK;
-  for (int mode : modes) {
+  // scratch for the epilogue variants of pass 2: the CG update reads a state
+  // with alpha = 0 (x and r do not change) and every reduction only stores
+  const int XP = prec == P_F64 ? P_F64 : P_F32;
+  void *xs = nullptr, *rs = nullptr, *cgs = nullptr;
+  const bool epis = prec != P_DF64;
+  if (epis) {
+    rc = h->workspace(lat, "tune_x", (size_t)spinor_half_bytes(L.g.Vh, XP) * nrhs, &xs);
+    if (!rc) rc = h->workspace(lat, "tune_r", half * nrhs, &rs);
+    if (!rc) rc = h->workspace(lat, "tune_cg", sizeof(CgState) * nrhs, &cgs);
+    if (!rc) rc = h->ensure_reduce(2 * nrhs, (L.g.Vh + 31) / 32);
+    if (rc) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+    if (cudaMemsetAsync(xs, 0, (size_t)spinor_half_bytes(L.g.Vh, XP) * nrhs, s) != cudaSuccess ||
+        cudaMemsetAsync(rs, 0, half * nrhs, s) != cudaSuccess ||
+        cudaMemsetAsync(cgs, 0, sizeof(CgState) * nrhs, s) != cudaSuccess)  // mode RUN, alpha 0
+      ret = OQ_ERR_CUDA;
+  }
+  struct Variant {
+    int mode, epi;
+  };
+  std::vector<Variant> variants = {{HOP_DW, EPI_NONE}, {HOP_P1, EPI_NONE}, {HOP_P2, EPI_NONE}};
+  if (epis) {
+    variants.push_back({HOP_P2, EPI_NORM});
+    variants.push_back({HOP_P2, EPI_CG});
+  }
+  for (const Variant var : variants) {
+    if (ret) break;
+    const int mode = var.mode;
     HopArgs a = h->hop_args(lat, prec);
     a.nrhs = nrhs;
     a.in = in;
@@ -107,13 +142,27 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
       a.in_stride = a.in2_stride = a.out_stride = (long)half;
       a.half_bytes = (long)half;
     }
+    if (var.epi != EPI_NONE) {
+      a.red = h->red_args(FIN_STORE, MODE_RUN);
+      if (var.epi == EPI_CG) {
+        a.out = nullptr;
+        a.cg = (CgState*)cgs;
+        a.gate = MODE_RUN;
+        a.ep_x = xs;
+        a.ep_x_stride = (long)spinor_half_bytes(L.g.Vh, XP);
+        a.ep_p = in;
+        a.ep_p_stride = (long)half;
+        a.ep_r = rs;
+        a.ep_r_stride = (long)half;
+      }
+    }
     TuneVal best;
     best.ms = 1e30f;
     // binary32 kernels may also read the 18-real copy of 12-real links
     const bool two_fmts = prec != P_F64 && prec != P_DF64 && L.link_fmt == LINK_12 && L.u32_18.p;
     for (int fmt = L.link_fmt; fmt >= 0; fmt = (two_fmts && fmt == LINK_12) ? LINK_18 : -1) {
       for (TuneVal c : candidates(prec, nrhs)) {
-        HopLaunch l = h->hop_launch(lat, prec, mode, 0, EPI_NONE, nrhs);
+        HopLaunch l = h->hop_launch(lat, prec, mode, 0, var.epi, nrhs);
         l.bx = c.bx;
         l.by = c.by;
         l.nr = c.nr;
@@ -142,7 +191,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
       if (ret) break;
     }
     if (ret) break;
-    h->tuned[TuneKey{lat, prec, mode, nrhs}] = best;
+    h->tuned[TuneKey{lat, prec, mode, nrhs, var.epi}] = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -152,7 +201,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
 extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
                            int* link_fmt, int* nr, int* regcap) {
   if (!h || !bx || !by || !ms || lat < 0 || lat >= (int)h->lats.size()) return OQ_ERR_ARG;
-  auto it = h->tuned.find(TuneKey{lat, prec, mode, nrhs});
+  auto it = h->tuned.find(TuneKey{lat, prec, mode, nrhs, EPI_NONE});
   if (it == h->tuned.end()) return OQ_ERR_STATE;
   const TuneVal& v = it->second;
   *bx = v.bx;
@@ -179,6 +228,9 @@ extern "C" int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, i
   v.link_fmt = link_fmt;
   v.ms = 0.f;
   if (!valid_shape(L, prec, nrhs, v)) return OQ_ERR_ARG;
-  h->tuned[TuneKey{lat, prec, mode, nrhs}] = v;
+  // the pinned launch serves every epilogue of the mode
+  const int epis[] = {EPI_NORM, EPI_CG, EPI_RESID64};
+  for (int e : epis) h->tuned.erase(TuneKey{lat, prec, mode, nrhs, e});
+  h->tuned[TuneKey{lat, prec, mode, nrhs, EPI_NONE}] = v;
   return OQ_OK;
 }
