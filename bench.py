@@ -43,6 +43,8 @@ EPS, SEED, KAPPA, CSW = 0.6, 3, 0.135, 1.0
 NRHS = 12
 RES = 1e-10
 FP64_PEAK_TFLOPS = 1.25          # GB300 nominal binary64 rate (no measured figure available)
+# GB300 binary32 FMA rate from unit counts and clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SLAB = (4, 32, 32, 32)           # oracle sample: same spatial extent, 4 time slices
 MODE_NAMES = {0: "dw_full", 1: "dw_hat_pass1_odd", 2: "dw_hat_pass2_even"}
 EPI_NAMES = {0: "store", 1: "store+norm", 2: "cg_update", 3: "fp64_residual"}
@@ -140,6 +142,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def kernel_key(p):
+    """Name of a profiled stencil variant: pass / epilogue / storage / rhs per thread / link format."""
+    fmt = {-1: "u64", 0: "u18", 1: "u12"}[p.get("link_fmt", -1)]
+    return f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}/nr{p.get('nr', 1)}/{fmt}"
+
+
 def traffic_for(kernel_key):
     """ncu DRAM bytes per launch recorded for this kernel, if the kernel source is unchanged since."""
     import hashlib
@@ -148,7 +156,7 @@ def traffic_for(kernel_key):
         return None
     d = json.load(open(p))
     h = hashlib.sha256()
-    for f in ("hop_impl.cuh", "oq_device.cuh", "reduce.cuh"):
+    for f in ("hop_impl.cuh", "hop_mr.cuh", "oq_device.cuh", "reduce.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2202_07388_gb300", "csrc", f), "rb").read())
     if d.get("source_sha256") != h.hexdigest():
         return None
@@ -303,6 +311,9 @@ def run_ours(args):
     setup_s = time.perf_counter() - t_setup
 
     statuses = []
+    # the solves (warm-up and timed) are the range an `ncu --profile-from-start off`
+    # launch list covers; set-up and tuning stay outside it
+    torch.cuda.profiler.start()
     for _ in range(args.warmup):
         rc, st = h.cgne(eta, psi, prm, nrhs=NRHS)
         assert rc == oq.OK, rc
@@ -321,6 +332,7 @@ def run_ours(args):
             statuses.append(st)
         ev1.record()
         torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     prof = h.profile_stop()
     launches = h.kernel_launches() - n0
     t_ms = ev0.elapsed_time(ev1)
@@ -334,7 +346,7 @@ def run_ours(args):
     vh = int(np.prod(DIMS)) // 2
 
     def roofline_of(p):
-        key = f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}"
+        key = kernel_key(p)
         avg = p["total_ms"] / p["launches"]
         if p["prec"] in (0, 4):
             # binary64 passes: bound by the FP64 pipe of GB300.  Flops per output
@@ -348,9 +360,15 @@ def run_ours(args):
         achieved = (p["bytes"] / p["launches"]) / (avg * 1e-3) / 1e9
         tr = traffic_for(key)
         traffic = tr["dram_bytes_per_site"] * vh if tr else None
+        # binary32 arithmetic of the same launch (stencil flops only): with many
+        # right-hand sides the pass sits near the binary32 ridge
+        flops = (1824.0 if p["mode"] == 1 else 1848.0) * vh * (2 if p["mode"] == 0 else 1) * NRHS
+        alu = flops / (avg * 1e-3) / 1e12
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": key, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                "avg_launch_ms": avg, "launches": p["launches"]}
+                "avg_launch_ms": avg, "launches": p["launches"],
+                "alu": {"achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu / FP32_PEAK_TFLOPS,
+                        "peak_kind": "binary32 FMA rate from unit counts and the 2.07 GHz clock"}}
 
     dom = max(prof, key=lambda p: p["total_ms"])
     roof = roofline_of(dom)
@@ -412,7 +430,7 @@ def run_ours(args):
         tts["batched_12rhs_f16_df64_resets_max_res"] = max(x["true_rel_res"] for x in stb)
         tts["batched_12rhs_f16_df64_resets_resets"] = [x["resets"] for x in stb]
         tts["batched_12rhs_f16_df64_resets_kernels"] = [
-            {"kernel": f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}",
+            {"kernel": kernel_key(p),
              "launches": p["launches"], "ms": p["total_ms"]} for p in h.profile_stop()]
         h.set_option(oq.OPT_DF64_RESETS, 0)
 
@@ -433,7 +451,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "solve": {"steps": [s["steps"] for s in st_last], "resets": [s["resets"] for s in st_last],
                       "max_true_rel_res": max(s["true_rel_res"] for s in st_last)},
-            "kernels": [{"kernel": f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}",
+            "kernels": [{"kernel": kernel_key(p),
                          "launches": p["launches"], "ms": p["total_ms"],
                          "gbs": p["bytes"] / (p["total_ms"] * 1e-3) / 1e9} for p in prof],
             "tts": tts, "setup_s": setup_s, "tuned_shapes": tuned,
@@ -667,7 +685,7 @@ def main():
     ap.add_argument("--nn-steps", type=int, default=100)
     ap.add_argument("--nn-lr", type=float, default=0.01)
     ap.add_argument("--profile-case", action="store_true")
-    ap.add_argument("--profile-prec", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
+    ap.add_argument("--profile-prec", default="fp16", choices=["fp64", "fp32", "bf16", "fp16", "df64"])
     ap.add_argument("--profile-nrhs", type=int, default=12)
     ap.add_argument("--profile-kind", default="dhat", choices=["dhat", "cgne", "tc", "cc", "sap"])
     ap.add_argument("--profile-pin", default=None,

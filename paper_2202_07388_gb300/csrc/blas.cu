@@ -165,8 +165,11 @@ cudaError_t cg_accumulate_x(int xprec, double* xd, const void* xs, long Vh, long
   return cudaGetLastError();
 }
 
-// r_s = r_d / scale (rounded to P), p = r_s, x_s = 0, ||r_s||^2 -> FIN_RESTART
-template <int P, int XP>
+// r_s = p = r_d / scale in the small type, x_s = 0, ||r_s||^2 -> FIN_RESTART.
+// RD: storage of r_d (P_F64 after a binary64 reset, P_DF64 after a
+// double-float one).  For the binary32-arithmetic types the site's squares
+// are summed in binary32 (as in the stencil epilogues), converted once.
+template <int P, int XP, int RD>
 __global__ void __launch_bounds__(256) cg_restart_kernel(const char* rd, char* rs, char* p, char* xs, long Vh,
                                                          long sd, long ss, long sx, int nrhs, RedArgs ra) {
   typedef typename PrecTraits<P>::R R;
@@ -177,41 +180,63 @@ __global__ void __launch_bounds__(256) cg_restart_kernel(const char* rd, char* r
   double acc = 0.0;
   if (i < Vh && ra.cg[rhs].mode == MODE_RESET) {
     const double inv = 1.0 / ra.cg[rhs].scale;
-    Spinor<double> d;
-    load_spinor<P_F64>(rd + rhs * sd, Vh, i, d);
     Spinor<R> v;
     Spinor<RX> z;
+    if constexpr (RD == P_DF64) {
+      Spinor<dfloat> d;
+      load_spinor<P_DF64>(rd + rhs * sd, Vh, i, d);
+      const float invf = (float)inv;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          v.c[s][c] = cx<R>{(R)(__fadd_rn(d.c[s][c].re.hi, d.c[s][c].re.lo) * invf),
+                            (R)(__fadd_rn(d.c[s][c].im.hi, d.c[s][c].im.lo) * invf)};
+    } else {
+      Spinor<double> d;
+      load_spinor<P_F64>(rd + rhs * sd, Vh, i, d);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v.c[s][c] = cx<R>{(R)(d.c[s][c].re * inv), (R)(d.c[s][c].im * inv)};
+    }
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        v.c[s][c] = cx<R>{(R)(d.c[s][c].re * inv), (R)(d.c[s][c].im * inv)};
-        z.c[s][c] = cx<RX>{0, 0};
-      }
+      for (int c = 0; c < 3; ++c) z.c[s][c] = cx<RX>{0, 0};
     round_trip<P>(v);  // the norm below is that of the stored (rounded) values
     store_spinor<P>(rs + rhs * ss, Vh, i, v);
     store_spinor<P>(p + rhs * ss, Vh, i, v);
     store_spinor<XP>(xs + rhs * sx, Vh, i, z);
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc += (double)v.c[s][c].re * v.c[s][c].re + (double)v.c[s][c].im * v.c[s][c].im;
+    acc = site_norm2(v);
   }
   grid_reduce(acc, ra, rhs, nrhs, smem, blockIdx.x, gridDim.x);
 }
 
-cudaError_t cg_restart(int prec, const double* rd, void* rs, void* p, void* xs, int xprec, long Vh, long stride_d,
-                       long stride_s, long stride_xs, int nrhs, const RedArgs& ra, cudaStream_t s) {
+cudaError_t cg_restart(int prec, const void* rd, int rd_prec, void* rs, void* p, void* xs, int xprec, long Vh,
+                       long stride_d, long stride_s, long stride_xs, int nrhs, const RedArgs& ra, cudaStream_t s) {
   dim3 grid((unsigned)((Vh + 255) / 256), nrhs), block(256);
   const char* d = (const char*)rd;
   char *r = (char*)rs, *pp = (char*)p, *x = (char*)xs;
-  switch (prec) {
-    case P_F64: cg_restart_kernel<P_F64, P_F64><<<grid, block, 0, s>>>(d, r, pp, x, Vh, stride_d, stride_s, stride_xs, nrhs, ra); break;
-    case P_F32: cg_restart_kernel<P_F32, P_F32><<<grid, block, 0, s>>>(d, r, pp, x, Vh, stride_d, stride_s, stride_xs, nrhs, ra); break;
-    case P_BF16: cg_restart_kernel<P_BF16, P_F32><<<grid, block, 0, s>>>(d, r, pp, x, Vh, stride_d, stride_s, stride_xs, nrhs, ra); break;
-    case P_F16: cg_restart_kernel<P_F16, P_F32><<<grid, block, 0, s>>>(d, r, pp, x, Vh, stride_d, stride_s, stride_xs, nrhs, ra); break;
-    default: return cudaErrorInvalidValue;
+#define OQ_RESTART(PP, XX, RR) \
+  cg_restart_kernel<PP, XX, RR><<<grid, block, 0, s>>>(d, r, pp, x, Vh, stride_d, stride_s, stride_xs, nrhs, ra)
+  if (rd_prec == P_DF64) {
+    switch (prec) {
+      case P_F32: OQ_RESTART(P_F32, P_F32, P_DF64); break;
+      case P_BF16: OQ_RESTART(P_BF16, P_F32, P_DF64); break;
+      case P_F16: OQ_RESTART(P_F16, P_F32, P_DF64); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (prec) {
+      case P_F64: OQ_RESTART(P_F64, P_F64, P_F64); break;
+      case P_F32: OQ_RESTART(P_F32, P_F32, P_F64); break;
+      case P_BF16: OQ_RESTART(P_BF16, P_F32, P_F64); break;
+      case P_F16: OQ_RESTART(P_F16, P_F32, P_F64); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
+#undef OQ_RESTART
   (void)xprec;
   return cudaGetLastError();
 }

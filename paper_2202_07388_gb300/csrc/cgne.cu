@@ -141,17 +141,20 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     CK(cudaStreamSynchronize(s));
     return OQ_OK;
   };
+  // storage of r_d: binary64, or double-float after a double-float reset
+  // (every rhs that restarts was reset by the latest reset step)
+  int rd_prec = P_F64;
   auto restart = [&]() -> int {
     RedArgs ra = h->red_args(FIN_RESTART, MODE_RESET);
-    KL(cg_restart(P, (const double*)rd, rv, pv, xs, XP, Vh, (long)h64, (long)hP, (long)hX, nrhs, ra, s));
+    KL(cg_restart(P, rd, rd_prec, rv, pv, xs, XP, Vh, (long)h64, (long)hP, (long)hX, nrhs, ra, s));
     return OQ_OK;
   };
 
   // the reset step for all rhs in MODE_RESET.  rp: arithmetic of the residual
   // recomputation (binary64 storage either way); accumulate: add s x_s to x_d
   // first (false re-checks the same x_d)
-  // double-float resets read the splits of x_d and eta (DF64 storage, the
-  // size of binary64) and write r_d in binary64
+  // double-float resets read the splits of x_d and eta and write r_d as
+  // double-float (DF64 storage has the size of binary64)
   void *xdf = nullptr, *etadf = nullptr;
   auto reset_step = [&](int rp, bool accumulate) -> int {
     if (accumulate) KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
@@ -186,6 +189,7 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     a.ep_eta = eta_in; a.ep_eta_stride = (long)h64;
     a.red = h->red_args(FIN_RD2, MODE_RESET);
     RK(h->run_hop(h->hop_launch(lat, rp, HOP_P2, 1, EPI_RESID64, nrhs), a, s));
+    rd_prec = rp;
     return OQ_OK;
   };
 

@@ -21,6 +21,25 @@
 
 namespace oq {
 
+// Accumulate one transported hop: with weight w (times the time-boundary
+// factor when the hop crosses it) for binary64 / binary32, where the weight
+// folds into FMAs; double-float sums the hops unweighted (a sign flip for
+// the boundary) and hop_site scales once by w = +-1/2 (exact).
+template <int MU, int S, typename R>
+__device__ __forceinline__ void hop_accum(Spinor<R>& acc, HalfSpinor<R>& t, R w, bool cr, float bc_t) {
+  if constexpr (std::is_same<R, dfloat>::value) {
+    if (cr && bc_t < 0.f) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t.c[s][c] = -t.c[s][c];
+    }
+    accum_reconstruct<MU, S, R, false>(acc, t, w);
+  } else {
+    accum_reconstruct<MU, S>(acc, t, cr ? w * (R)bc_t : w);
+  }
+}
+
 template <int P, int FMT, int MU, bool DAG>
 __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p, long i, const int x[4],
                                         Spinor<typename PrecTraits<P>::R>& acc,
@@ -38,7 +57,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p,
     Su3<R> u;
     load_link<R, FMT>(a.links, a.g.Vh, p, MU, i, u);
     su3_mul(u, h, t);
-    accum_reconstruct<MU, SF>(acc, t, cr ? w * (R)a.g.bc_t : w);
+    hop_accum<MU, SF>(acc, t, w, cr, a.g.bc_t);
   }
   // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
   {
@@ -50,7 +69,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p,
     Su3<R> u;
     load_link<R, FMT>(a.links, a.g.Vh, 1 - p, MU, j, u);
     su3_dag_mul(u, h, t);
-    accum_reconstruct<MU, -SF>(acc, t, cr ? w * (R)a.g.bc_t : w);
+    hop_accum<MU, -SF>(acc, t, w, cr, a.g.bc_t);
   }
 }
 
@@ -76,6 +95,13 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
     hop_dir<P, FMT, 1, DAG>(a, in, p, i, x, acc, w);
     hop_dir<P, FMT, 2, DAG>(a, in, p, i, x, acc, w);
     hop_dir<P, FMT, 3, DAG>(a, in, p, i, x, acc, w);
+    if constexpr (std::is_same<R, dfloat>::value) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          acc.c[s][c] = cx<R>{df_scale(acc.c[s][c].re, w.hi), df_scale(acc.c[s][c].im, w.hi)};
+    }
 
     Spinor<R> res;
     if constexpr (MODE == HOP_P1) {
@@ -126,27 +152,26 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
       for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) res.c[s][c] = e.c[s][c] - res.c[s][c];
+      store_spinor<P>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, res);
       if constexpr (P == P_DF64) {
-        // the reset residual is kept in binary64 (hi + lo is exact in binary64)
-        Spinor<double> r64;
+        // the site's 24 squares summed in double-float, one conversion
+        dfloat acc2(0.f);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) r64.c[s][c] = cx<double>{(double)res.c[s][c].re, (double)res.c[s][c].im};
-        store_spinor<P_F64>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, r64);
+          for (int c = 0; c < 3; ++c) acc2 = fma(res.c[s][c].re, res.c[s][c].re, fma(res.c[s][c].im, res.c[s][c].im, acc2));
+        red = (double)acc2;
       } else {
-        store_spinor<P>((char*)a.out + rhs * a.out_stride, a.g.Vh, i, res);
+        double acc2 = 0.0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double re = (double)res.c[s][c].re, im = (double)res.c[s][c].im;
+            acc2 += re * re + im * im;
+          }
+        red = acc2;
       }
-      double acc2 = 0.0;
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-        {
-          const double re = (double)res.c[s][c].re, im = (double)res.c[s][c].im;
-          acc2 += re * re + im * im;
-        }
-      red = acc2;
     }
   return red;
 }

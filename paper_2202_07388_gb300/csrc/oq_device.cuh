@@ -98,6 +98,32 @@ __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
   const dfloat s = df_two_sum(c.hi, p);
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(c.lo, e)));
 }
+// A dot product of double-float numbers accumulated lazily: s is the running
+// sum of the high products (each added by a two-sum), e collects the
+// two-sum errors and the low parts of every product in binary32; one
+// renormalisation at the end.  12 binary32 operations per term instead of
+// the 15 of a renormalised fma.
+struct DfAcc {
+  float s, e;
+};
+__device__ __forceinline__ void dfa_first(DfAcc& a, dfloat x, dfloat y) {  // a = x y
+  a.s = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -a.s);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  a.e = __fmaf_rn(x.lo, y.hi, e);
+}
+__device__ __forceinline__ void dfa_add(DfAcc& a, dfloat x, dfloat y) {  // a += x y
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const dfloat t = df_two_sum(a.s, p);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, e));
+}
+__device__ __forceinline__ dfloat dfa_get(const DfAcc& a) { return df_fast_two_sum(a.s, a.e); }
+// x * 2^k for a power of two s = 2^k: exact, both parts scaled
+__device__ __forceinline__ dfloat df_scale(dfloat x, float s) { return dfloat(x.hi * s, x.lo * s); }
 using ::fma;  // keep the float / double overloads visible next to the dfloat one
 enum LinkFmt : int { LINK_18 = 0, LINK_12 = 1 };
 
@@ -432,6 +458,49 @@ __device__ __forceinline__ void su3_dag_mul(const Su3<R>& u, const HalfSpinor<R>
     }
 }
 
+// double-float forms: each output real is one 6-term dot product
+__device__ __forceinline__ void su3_mul(const Su3<dfloat>& u, const HalfSpinor<dfloat>& h, HalfSpinor<dfloat>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      DfAcc re, im;
+      dfa_first(re, u.m[a][0].re, h.c[s][0].re);
+      dfa_add(re, -u.m[a][0].im, h.c[s][0].im);
+      dfa_first(im, u.m[a][0].re, h.c[s][0].im);
+      dfa_add(im, u.m[a][0].im, h.c[s][0].re);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        dfa_add(re, u.m[a][b].re, h.c[s][b].re);
+        dfa_add(re, -u.m[a][b].im, h.c[s][b].im);
+        dfa_add(im, u.m[a][b].re, h.c[s][b].im);
+        dfa_add(im, u.m[a][b].im, h.c[s][b].re);
+      }
+      y.c[s][a] = cx<dfloat>{dfa_get(re), dfa_get(im)};
+    }
+}
+__device__ __forceinline__ void su3_dag_mul(const Su3<dfloat>& u, const HalfSpinor<dfloat>& h,
+                                            HalfSpinor<dfloat>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      DfAcc re, im;  // sum_b conj(U_ba) h_b
+      dfa_first(re, u.m[0][a].re, h.c[s][0].re);
+      dfa_add(re, u.m[0][a].im, h.c[s][0].im);
+      dfa_first(im, u.m[0][a].re, h.c[s][0].im);
+      dfa_add(im, -u.m[0][a].im, h.c[s][0].re);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        dfa_add(re, u.m[b][a].re, h.c[s][b].re);
+        dfa_add(re, u.m[b][a].im, h.c[s][b].im);
+        dfa_add(im, u.m[b][a].re, h.c[s][b].im);
+        dfa_add(im, -u.m[b][a].im, h.c[s][b].re);
+      }
+      y.c[s][a] = cx<dfloat>{dfa_get(re), dfa_get(im)};
+    }
+}
+
 // ---------------------------------------------------------------------------
 // clover blocks
 // ---------------------------------------------------------------------------
@@ -492,17 +561,41 @@ __device__ __forceinline__ void clover_apply(const void* base, long Vh, int p, l
     }
     const cx<R>* x = v + 6 * b;
     cx<R>* y = o + 6 * b;
+    if constexpr (std::is_same<R, dfloat>::value) {
+      // row r: d_r x_r + sum_{c > r} K_rc x_c + sum_{c < r} conj(K_cr) x_c,
+      // off-diagonal K_rc (r < c) at index k(r, c) of the row-major upper triangle
 #pragma unroll
-    for (int r0 = 0; r0 < 6; ++r0) y[r0] = d[r0] * x[r0];
-    int k = 0;
+      for (int r0 = 0; r0 < 6; ++r0) {
+        DfAcc re, im;
+        dfa_first(re, d[r0], x[r0].re);
+        dfa_first(im, d[r0], x[r0].im);
 #pragma unroll
-    for (int r0 = 0; r0 < 6; ++r0)
-#pragma unroll
-      for (int c0 = r0 + 1; c0 < 6; ++c0) {
-        cfma(y[r0], off[k], x[c0]);
-        cfmac(y[c0], off[k], x[r0]);
-        ++k;
+        for (int c0 = 0; c0 < 6; ++c0) {
+          if (c0 == r0) continue;
+          const int a0 = r0 < c0 ? r0 : c0, b0 = r0 < c0 ? c0 : r0;
+          const int k = a0 * 5 - a0 * (a0 - 1) / 2 + (b0 - a0 - 1);
+          const cx<R> o2 = off[k];
+          const R oi = r0 < c0 ? o2.im : -o2.im;  // conj for the lower triangle
+          dfa_add(re, o2.re, x[c0].re);
+          dfa_add(re, -oi, x[c0].im);
+          dfa_add(im, o2.re, x[c0].im);
+          dfa_add(im, oi, x[c0].re);
+        }
+        y[r0] = cx<R>{dfa_get(re), dfa_get(im)};
       }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < 6; ++r0) y[r0] = d[r0] * x[r0];
+      int k = 0;
+#pragma unroll
+      for (int r0 = 0; r0 < 6; ++r0)
+#pragma unroll
+        for (int c0 = r0 + 1; c0 < 6; ++c0) {
+          cfma(y[r0], off[k], x[c0]);
+          cfmac(y[c0], off[k], x[r0]);
+          ++k;
+        }
+    }
   }
 }
 
@@ -534,11 +627,16 @@ __device__ __forceinline__ void project(const Spinor<R>& p, HalfSpinor<R>& h) {
 }
 
 // acc += w * (1 -/+ g_mu)-reconstruction of the transported half spinor h
-template <int MU, int S, typename R>
+// (SCALE = false: w = 1, no multiplication)
+template <int MU, int S, typename R, bool SCALE = true>
 __device__ __forceinline__ void accum_reconstruct(Spinor<R>& acc, const HalfSpinor<R>& h, R w) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    cx<R> h0 = w * h.c[0][a], h1 = w * h.c[1][a];
+    cx<R> h0 = h.c[0][a], h1 = h.c[1][a];
+    if constexpr (SCALE) {
+      h0 = w * h0;
+      h1 = w * h1;
+    }
     acc.c[0][a] = acc.c[0][a] + h0;
     acc.c[1][a] = acc.c[1][a] + h1;
     cx<R> l0, l1;

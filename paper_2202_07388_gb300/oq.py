@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "liboq.so")
 F64, F32, BF16, F16, DF64 = 0, 1, 2, 3, 4
 LINK_18, LINK_12 = 0, 1
 EVEN, ODD, FULL = 0, 1, 2
-PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16}
+PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16, "df64": DF64}
 OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA, OPT_NN_TENSOR_CORES, OPT_SAP_TWO_CTAS = 1, 2, 3, 4
 
 OK = 0
@@ -48,7 +48,7 @@ class OqStatus(C.Structure):
 
 class OqKernelTime(C.Structure):
     _fields_ = [("mode", C.c_int), ("epi", C.c_int), ("prec", C.c_int), ("launches", C.c_int),
-                ("total_ms", C.c_double), ("bytes", C.c_double)]
+                ("total_ms", C.c_double), ("bytes", C.c_double), ("nr", C.c_int), ("link_fmt", C.c_int)]
 
 
 _lib = None
@@ -339,4 +339,4 @@ class Handle:
         n = C.c_int()
         _check(lib().oq_profile_stop(self.h, buf, 64, C.byref(n)), "oq_profile_stop")
         return [{"mode": b.mode, "epi": b.epi, "prec": b.prec, "launches": b.launches, "total_ms": b.total_ms,
-                 "bytes": b.bytes} for b in buf[: n.value]]
+                 "bytes": b.bytes, "nr": b.nr, "link_fmt": b.link_fmt} for b in buf[: n.value]]

@@ -94,6 +94,29 @@ def test_pack_roundtrip_and_reductions():
         assert np.array_equal(from_dev(back, x.shape), x)
 
 
+def test_df64_pack_splits_binary64():
+    """Double-float storage: packing splits every binary64 value x into
+    hi = rn32(x), lo = rn32(x - hi); unpacking returns hi + lo, within
+    2^-48 |x| of x (the rounding of lo)."""
+    oq = _oq()
+    dims = (6, 4, 2, 6)
+    u, a, ainv = oracle_case(dims, 0.5, 2, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_18)
+    x = synth.make_source(dims, 8, nrhs=2)
+    px = h.new_packed(oq.DF64, nrhs=2)
+    h.pack(to_dev(x), px, oq.DF64, nrhs=2)
+    back = to_dev(np.zeros_like(x))
+    h.unpack(px, back, oq.DF64, nrhs=2)
+    xr = from_dev(back, x.shape)
+    xv, bv = x.view(np.float64), xr.view(np.float64)
+    assert np.all(np.abs(bv - xv) <= 2.0 ** -48 * np.abs(xv))
+    # the stored pairs are (rn32(x), rn32(x - rn32(x)))
+    raw = px.cpu().numpy().view(np.float32).reshape(2, 2, -1, 4)   # rhs, parity, chunk*site, (re.hi, re.lo, im.hi, im.lo)
+    hi = raw[..., 0].astype(np.float64)
+    lo = raw[..., 1].astype(np.float64)
+    assert np.all(np.abs(lo) <= np.spacing(np.abs(hi).astype(np.float32)).astype(np.float64) / 2 + 0.0)
+
+
 def test_u3_links_and_periodic_time():
     """QCD+QED links U(3) = SU(3) x exp(i q A) (18-real storage), both time
     boundary conditions."""
