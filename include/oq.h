@@ -204,12 +204,14 @@ int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int 
                 int link_fmt);
 
 /* Handle options (no counterpart in the paper).
- * OQ_OPT_DF64_RESETS: 1 = the intermediate CGNE reset steps of a
+ * OQ_OPT_DF64_RESETS: 1 (default) = the intermediate CGNE reset steps of a
  *   low-precision solve recompute the residual with OQ_DF64 arithmetic; a
- *   residual that meets the target is confirmed in binary64 before the solve
- *   stops, and a double-float value found too optimistic switches the solve
- *   back to binary64 resets.  Default 0 (binary64 resets): on GB300 the
- *   double-float stencil measured slower than the native binary64 one.
+ *   residual that meets the target is confirmed by a binary64 reset before
+ *   the solve stops (so the reported true residual, and the stop decision,
+ *   are binary64), and a double-float value found too optimistic switches the
+ *   solve to binary64 resets.  0 = every reset in binary64 (the paper's
+ *   scheme).  On GB300, whose binary64 rate is 1/64 of its binary32 rate, a
+ *   double-float reset pass is ~3x faster than a binary64 one.
  * OQ_OPT_TEST_TC_SKIP_MMA: testing aid for failure detection; 1 = the
  *   tensor-core PTC layer issues no MMA, so its bounded (1 s) wait for the
  *   tensor core runs out and oq_nnprec_apply_tc returns OQ_ERR_TIMEOUT with

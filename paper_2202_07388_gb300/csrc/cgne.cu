@@ -5,10 +5,14 @@
 // binary32 arithmetic), every reduction is binary64.  The small-type CG
 // solves A x_s = r_d / s for the current binary64 residual r_d, scaled by
 // s = ||r_d|| / sqrt(12 Ve) so that stored components are O(1).  A reset step
-// adds s x_s to the binary64 solution x_d and recomputes r_d = eta - A x_d in
-// binary64 once the recursive residual has dropped below delta times its
-// value at the previous reset (delta ~ 10 eps of the small type), reached the
-// target, or nmx steps are used.  The regular steps never wait for the host:
+// adds s x_s to the binary64 solution x_d and recomputes r_d = eta - A x_d
+// once the recursive residual has dropped below delta times its value at the
+// previous reset (delta ~ 10 eps of the small type), reached the target, or
+// nmx steps are used.  The paper recomputes r_d in binary64; here the
+// intermediate recomputations use double-float arithmetic (~48 bits, on the
+// binary32 pipes, 3x faster than binary64 on GB300) unless
+// OQ_OPT_DF64_RESETS is 0, and a residual that meets the target is always
+// confirmed by a binary64 recomputation.  The regular steps never wait for the host:
 // alpha, beta and the reset decision are computed on the device by the last
 // CTA of each fused grid reduction; the host looks at the per-rhs state once
 // every CHUNK iterations.
@@ -220,9 +224,9 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     return OQ_OK;
   };
 
-  // Reset residuals use binary64 arithmetic; optionally (OQ_OPT_DF64_RESETS)
-  // the intermediate resets of a low-precision solve use double-float
-  // arithmetic, and every convergence decision is still taken in binary64.
+  // The intermediate resets of a low-precision solve use double-float
+  // arithmetic (OQ_OPT_DF64_RESETS, default; else binary64 as in the
+  // paper); every convergence decision is still taken in binary64.
   int reset_prec = (P != P_F64 && h->df64_resets) ? P_DF64 : P_F64;
   int pending = decide(false);
   RK(upload());

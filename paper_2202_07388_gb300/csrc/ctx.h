@@ -87,7 +87,7 @@ struct oq_ctx {
   long long launches = 0;
   // CGNE: intermediate reset residuals in double-float arithmetic (off by
   // default: measured slower than native binary64 on GB300)
-  bool df64_resets = false;
+  bool df64_resets = true;   // OQ_OPT_DF64_RESETS
   // test hook: the tensor-core PTC layer issues no MMA, so its bounded wait runs out
   bool hook_tc_skip_commit = false;
   // SAP block kernel with registers capped for two CTAs per SM (measured ~5 %

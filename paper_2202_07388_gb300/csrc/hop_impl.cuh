@@ -73,6 +73,94 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p,
   }
 }
 
+// eo_neighbour for a runtime direction, without indexing a local array
+__device__ __forceinline__ long eo_neighbour_rt(const Geom& g, const int x[4], int mu, int d, bool* crossed) {
+  const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+  const int xm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
+  int v = xm + d;
+  bool c = false;
+  if (v == L) { v = 0; c = true; }
+  if (v < 0) { v = L - 1; c = true; }
+  *crossed = c && (mu == 0);
+  const int y0 = mu == 0 ? v : x[0], y1 = mu == 1 ? v : x[1], y2 = mu == 2 ? v : x[2], y3 = mu == 3 ? v : x[3];
+  const long lex = (((long)y0 * g.L[1] + y1) * g.L[2] + y2) * g.L[3] + y3;
+  return lex >> 1;
+}
+
+// z * i^c for c in 0..3 (double-float): a swap of the parts for odd c and
+// sign flips, all by selects
+__device__ __forceinline__ cx<dfloat> rot_ic(const cx<dfloat>& z, int c) {
+  const bool sw = c & 1;
+  dfloat re = sw ? z.im : z.re, im = sw ? z.re : z.im;
+  if (c == 1 || c == 2) re = -re;
+  if (c >= 2) im = -im;
+  return cx<dfloat>{re, im};
+}
+
+// The hopping sum in double-float as one runtime loop over the 8 hops: the
+// fully unrolled double-float stencil is ~14k instructions, far beyond the
+// instruction cache, while one loop body (~1k) stays resident.  The spin
+// projection for hop (mu, projector sign S) is h0 = p0 + i^c0 p[q0],
+// h1 = p1 + i^c1 p[q1], the reconstruction acc2 += i^d0 t[r0],
+// acc3 += i^d1 t[r1] (the same linear maps as project / accum_reconstruct,
+// as tables; S = +1 adds 2 to every power); a backward hop applies
+// U(x - mu)^dag by conjugate-transposing the link in registers.
+template <int P, int FMT, bool DAG>
+__device__ __forceinline__ void hop_loop_df(const HopArgs& a, const char* in, int p, long i, const int x[4],
+                                            Spinor<dfloat>& acc) {
+  constexpr int SF = DAG ? +1 : -1;  // projector sign of the forward hop
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int mu = k >> 1;
+    const bool fwd = (k & 1) == 0;
+    const int sh = ((fwd ? SF : -SF) > 0) ? 2 : 0;
+    bool cr;
+    const long j = eo_neighbour_rt(a.g, x, mu, fwd ? +1 : -1, &cr);
+    Spinor<dfloat> nb;
+    load_spinor<P>(in, a.g.Vh, j, nb);
+    Su3<dfloat> u;
+    load_link<dfloat, FMT>(a.links, a.g.Vh, fwd ? p : 1 - p, mu, fwd ? i : j, u);
+    if (!fwd) {
+      Su3<dfloat> v = u;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u.m[r][c] = conj(v.m[c][r]);
+    }
+    // projection tables (mu = 0..3): partners q0, q1 and powers of i
+    const bool swq = (mu == 1 || mu == 2);       // q0 = 3, q1 = 2
+    const int c0 = ((mu == 1 || mu == 3) ? 1 : 0) + sh;
+    const int c1 = (mu == 0 ? 0 : mu == 1 ? 1 : mu == 2 ? 2 : 3) + sh;
+    HalfSpinor<dfloat> h, t;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cx<dfloat> pa = swq ? nb.c[3][c] : nb.c[2][c];
+      const cx<dfloat> pb = swq ? nb.c[2][c] : nb.c[3][c];
+      h.c[0][c] = nb.c[0][c] + rot_ic(pa, c0 & 3);
+      h.c[1][c] = nb.c[1][c] + rot_ic(pb, c1 & 3);
+    }
+    su3_mul(u, h, t);
+    if (cr && a.g.bc_t < 0.f) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t.c[s][c] = -t.c[s][c];
+    }
+    // reconstruction tables: r0 = 1, r1 = 0 for mu = 1, 2
+    const int d0 = (mu == 0 ? 0 : mu == 1 ? 3 : mu == 2 ? 2 : 3) + sh;
+    const int d1 = (mu == 0 ? 0 : mu == 1 ? 3 : mu == 2 ? 0 : 1) + sh;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc.c[0][c] = acc.c[0][c] + t.c[0][c];
+      acc.c[1][c] = acc.c[1][c] + t.c[1][c];
+      const cx<dfloat> ta = swq ? t.c[1][c] : t.c[0][c];
+      const cx<dfloat> tb = swq ? t.c[0][c] : t.c[1][c];
+      acc.c[2][c] = acc.c[2][c] + rot_ic(ta, d0 & 3);
+      acc.c[3][c] = acc.c[3][c] + rot_ic(tb, d1 & 3);
+    }
+  }
+}
+
 // One output site i (parity p) of right-hand side rhs: the stencil, the
 // clover term and the epilogue.  Returns the site's contribution to the
 // epilogue's reduction (0 if none).
@@ -91,10 +179,14 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc.c[s][c] = cx<R>{0, 0};
     const R w = (MODE == HOP_P2) ? (R)0.5 : (R)-0.5;
-    hop_dir<P, FMT, 0, DAG>(a, in, p, i, x, acc, w);
-    hop_dir<P, FMT, 1, DAG>(a, in, p, i, x, acc, w);
-    hop_dir<P, FMT, 2, DAG>(a, in, p, i, x, acc, w);
-    hop_dir<P, FMT, 3, DAG>(a, in, p, i, x, acc, w);
+    if constexpr (std::is_same<R, dfloat>::value) {
+      hop_loop_df<P, FMT, DAG>(a, in, p, i, x, acc);
+    } else {
+      hop_dir<P, FMT, 0, DAG>(a, in, p, i, x, acc, w);
+      hop_dir<P, FMT, 1, DAG>(a, in, p, i, x, acc, w);
+      hop_dir<P, FMT, 2, DAG>(a, in, p, i, x, acc, w);
+      hop_dir<P, FMT, 3, DAG>(a, in, p, i, x, acc, w);
+    }
     if constexpr (std::is_same<R, dfloat>::value) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
