@@ -392,6 +392,10 @@ def run_ours(args):
     psi_host = torch.empty_like(eta_host).pin_memory()
     eta_dev2 = torch.empty_like(eta)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one untimed pass first: the first copies into freshly pinned buffers pay one-off costs
+    eta_dev2.copy_(eta_host, non_blocking=True)
+    rc, _ = h.cgne(eta_dev2, psi, prm, nrhs=NRHS)
+    psi_host.copy_(psi, non_blocking=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(args.e2e_steps):

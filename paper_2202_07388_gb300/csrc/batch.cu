@@ -9,7 +9,9 @@
 //  * per-system arguments, solver state and reduction scratch live in
 //    device memory, so a chunk of CHUNK regular iterations has no host
 //    dependency: it is captured once into a CUDA graph and replayed;
-//  * binary64 reset steps run (uncaptured) when any system asks for one.
+//  * reset steps run (uncaptured) when any system asks for one: double-float
+//    intermediate resets with a binary64 confirmation, as in oq_cgne_solve
+//    (binary64 only when OQ_OPT_DF64_RESETS is 0).
 #include <math.h>
 #include <string.h>
 
@@ -30,12 +32,12 @@ struct VecSys {
   char* r;      // small-type residual
   char* xs;     // small-type solution (binary32, or binary64 for F64 solves)
   char* xd;     // binary64 solution
-  char* rd;     // binary64 residual
+  char* rd;     // residual r_d: binary64, or double-float after a double-float reset
   CgState* cg;
   RedArgs red;
 };
 
-enum VecOp { VOP_P = 0, VOP_ACCX = 1, VOP_RESTART = 2 };
+enum VecOp { VOP_P = 0, VOP_ACCX = 1, VOP_RESTART = 2, VOP_RESTART_DF = 3 };
 
 static const int VT = 256;  // sites per vector tile
 
@@ -82,17 +84,30 @@ __global__ void __launch_bounds__(VT) vec_batch_kernel(const VecSys* __restrict_
         store_spinor<P_F64>(v.xd, v.Vh, i, d);
       } else {
         const double inv = 1.0 / v.cg->scale;
-        Spinor<double> d;
-        load_spinor<P_F64>(v.rd, v.Vh, i, d);
         Spinor<R> q;
         Spinor<RX> z;
+        if constexpr (OP == VOP_RESTART_DF) {
+          Spinor<dfloat> d;
+          load_spinor<P_DF64>(v.rd, v.Vh, i, d);
+          const float invf = (float)inv;
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              q.c[s][c] = cx<R>{(R)(__fadd_rn(d.c[s][c].re.hi, d.c[s][c].re.lo) * invf),
+                                (R)(__fadd_rn(d.c[s][c].im.hi, d.c[s][c].im.lo) * invf)};
+        } else {
+          Spinor<double> d;
+          load_spinor<P_F64>(v.rd, v.Vh, i, d);
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) q.c[s][c] = cx<R>{(R)(d.c[s][c].re * inv), (R)(d.c[s][c].im * inv)};
+        }
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            q.c[s][c] = cx<R>{(R)(d.c[s][c].re * inv), (R)(d.c[s][c].im * inv)};
-            z.c[s][c] = cx<RX>{0, 0};
-          }
+          for (int c = 0; c < 3; ++c) z.c[s][c] = cx<RX>{0, 0};
         round_trip<P>(q);
         store_spinor<P>(v.r, v.Vh, i, q);
         store_spinor<P>(v.p, v.Vh, i, q);
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(VT) vec_batch_kernel(const VecSys* __restrict_
         acc = site_norm2(q);
       }
     }
-    if constexpr (OP == VOP_RESTART) {
+    if constexpr (OP == VOP_RESTART || OP == VOP_RESTART_DF) {
       const unsigned nblk = (unsigned)((v.Vh + VT - 1) / VT);
       grid_reduce(acc, v.red, 0, 1, smem, (unsigned)tl.y, nblk);
     }
@@ -112,7 +127,11 @@ static cudaError_t vec_batch(int op, const VecSys* sys, const int2* tiles, int n
   switch (op) {
     case VOP_P: vec_batch_kernel<P, XP, VOP_P><<<grid, VT, 0, s>>>(sys, tiles, ntiles); break;
     case VOP_ACCX: vec_batch_kernel<P, XP, VOP_ACCX><<<grid, VT, 0, s>>>(sys, tiles, ntiles); break;
-    default: vec_batch_kernel<P, XP, VOP_RESTART><<<grid, VT, 0, s>>>(sys, tiles, ntiles); break;
+    case VOP_RESTART: vec_batch_kernel<P, XP, VOP_RESTART><<<grid, VT, 0, s>>>(sys, tiles, ntiles); break;
+    default:
+      if constexpr (P == P_F64) return cudaErrorInvalidValue;  // binary64 solves reset in binary64
+      else vec_batch_kernel<P, XP, VOP_RESTART_DF><<<grid, VT, 0, s>>>(sys, tiles, ntiles);
+      break;
   }
   return cudaGetLastError();
 }
@@ -166,7 +185,14 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
   // per-system buffers
   std::vector<long> Vh(nsys);
   std::vector<void*> eta64(nsys), xd(nsys), rd(nsys), t64(nsys), u64v(nsys), pv(nsys), rv(nsys), uv(nsys),
-      tv(nsys), xs(nsys);
+      tv(nsys), xs(nsys), xdf(nsys), etadf(nsys);
+  // double-float intermediate resets (binary64 confirmation), as oq_cgne_solve
+  int reset_prec = (P != P_F64 && h->df64_resets) ? P_DF64 : P_F64;
+  if (reset_prec == P_DF64)
+    for (int s2 = 0; s2 < nsys; ++s2) {
+      rc = h->ensure_df(lats[s2], s);
+      if (rc) return rc;
+    }
   long maxblk = 1;
   for (int s2 = 0; s2 < nsys; ++s2) {
     const int lat = lats[s2];
@@ -184,13 +210,17 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     rc |= h->workspace(lat, (k + "u").c_str(), hP, &uv[s2]);
     rc |= h->workspace(lat, (k + "t").c_str(), hP, &tv[s2]);
     rc |= h->workspace(lat, (k + "xs").c_str(), hX, &xs[s2]);
+    if (reset_prec == P_DF64) {
+      rc |= h->workspace(lat, (k + "xdf").c_str(), h64, &xdf[s2]);
+      rc |= h->workspace(lat, (k + "etadf").c_str(), h64, &etadf[s2]);
+    }
     const long nb = (Vh[s2] + 31) / 32;
     if (nb > maxblk) maxblk = nb;
   }
   if (rc) return OQ_ERR_NOMEM;
   // batch scratch (on lattice 0's workspace): partials, counters, results, states, args, tiles
   void *bpart, *bcnt, *bres, *bcg, *bargs, *bvsys, *btiles;
-  const int NARG = 8;
+  const int NARG = 12;
   std::vector<int2> tiles_lo, tiles_64, tiles_v;
   for (int s2 = 0; s2 < nsys; ++s2) {
     for (long b = 0; b < (Vh[s2] + bx_lo - 1) / bx_lo; ++b) tiles_lo.push_back(make_int2(s2, (int)b));
@@ -202,7 +232,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
   rc |= h->workspace(lats[0], "b_res", sizeof(double) * nsys, &bres);
   rc |= h->workspace(lats[0], "b_cg", sizeof(CgState) * nsys, &bcg);
   rc |= h->workspace(lats[0], "b_args", sizeof(HopArgs) * NARG * nsys, &bargs);
-  rc |= h->workspace(lats[0], "b_vsys", sizeof(VecSys) * 3 * nsys, &bvsys);
+  rc |= h->workspace(lats[0], "b_vsys", sizeof(VecSys) * 4 * nsys, &bvsys);
   rc |= h->workspace(lats[0], "b_tiles", sizeof(int2) * (tiles_lo.size() + tiles_64.size() + tiles_v.size()),
                      &btiles);
   if (rc) return OQ_ERR_NOMEM;
@@ -236,7 +266,8 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     r.gate = gate;
     return r;
   };
-  // argument sets: 0 P1, 1 P2+norm, 2 P1^dag, 3 P2^dag+CG (small type); 4..7 the binary64 reset passes
+  // argument sets: 0 P1, 1 P2+norm, 2 P1^dag, 3 P2^dag+CG (small type); 4..7 the binary64 reset
+  // passes; 8..11 the double-float reset passes (split x_d and eta in, r_d out as double-float)
   std::vector<HopArgs> args((size_t)NARG * nsys);
   for (int s2 = 0; s2 < nsys; ++s2) {
     const int lat = lats[s2];
@@ -279,10 +310,30 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     a.ep_eta = eta64[s2];
     a.red = red_for(s2, FIN_RD2, MODE_RESET);
     args[7 * nsys + s2] = a;
+    if (reset_prec == P_DF64) {
+      HopArgs bdf = h->hop_args(lat, P_DF64);
+      bdf.cg = cg + s2;
+      bdf.gate = MODE_RESET;
+      bdf.half_bytes = h64;
+      a = bdf;
+      a.in = xdf[s2]; a.out = t64[s2]; a.p = 1;
+      args[8 * nsys + s2] = a;
+      a = bdf;
+      a.in = t64[s2]; a.in2 = xdf[s2]; a.out = u64v[s2]; a.p = 0;
+      args[9 * nsys + s2] = a;
+      a = bdf;
+      a.in = u64v[s2]; a.out = t64[s2]; a.p = 1;
+      args[10 * nsys + s2] = a;
+      a = bdf;
+      a.in = t64[s2]; a.in2 = u64v[s2]; a.out = rd[s2]; a.p = 0;
+      a.ep_eta = etadf[s2];
+      a.red = red_for(s2, FIN_RD2, MODE_RESET);
+      args[11 * nsys + s2] = a;
+    }
     (void)hX;
   }
   CK(cudaMemcpyAsync(bargs, args.data(), sizeof(HopArgs) * args.size(), cudaMemcpyHostToDevice, s));
-  std::vector<VecSys> vs((size_t)3 * nsys);
+  std::vector<VecSys> vs((size_t)4 * nsys);
   for (int s2 = 0; s2 < nsys; ++s2) {
     VecSys v;
     v.Vh = Vh[s2];
@@ -297,6 +348,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     vs[1 * nsys + s2] = v;  // VOP_ACCX
     v.red = red_for(s2, FIN_RESTART, MODE_RESET);
     vs[2 * nsys + s2] = v;  // VOP_RESTART
+    vs[3 * nsys + s2] = v;  // VOP_RESTART_DF
   }
   CK(cudaMemcpyAsync(bvsys, vs.data(), sizeof(VecSys) * vs.size(), cudaMemcpyHostToDevice, s));
   const HopArgs* dargs = (const HopArgs*)bargs;
@@ -314,7 +366,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     l.mode = mode;
     l.dagger = dag;
     l.epi = epi;
-    const bool f64 = prec == P_F64;
+    const bool f64 = prec == P_F64 || prec == P_DF64;
     l.bx = f64 ? bx_64 : bx_lo;
     l.by = 1;
     l.sys = dargs + (long)argset * nsys;
@@ -340,6 +392,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
       CK(cudaMemsetAsync(xd[s2], 0, h64, s));
       CK(cudaMemsetAsync(xs[s2], 0, spinor_half_bytes(Vh[s2], XP), s));
       CK(cudaMemcpyAsync(rd[s2], eta64[s2], h64, cudaMemcpyDeviceToDevice, s));
+      if (reset_prec == P_DF64) KL(split_f64((const double*)eta64[s2], etadf[s2], h64 / sizeof(double), s));
       ra = h->red_args(FIN_STORE, 0);
       KL(reduce_norm2(P_F64, eta64[s2], Vh[s2], h64, 1, ra, s));
       double v = 0.0;
@@ -389,16 +442,33 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     CK(cudaStreamSynchronize(s));
     return OQ_OK;
   };
+  // storage of r_d (every system that restarts was reset by the latest reset step)
+  int rd_prec = P_F64;
   auto restart = [&]() -> int {
-    KL(vec_batch_any(P, VOP_RESTART, dvs + 2 * nsys, t_v, (int)tiles_v.size(), grid_v, s));
+    if (rd_prec == P_DF64)
+      KL(vec_batch_any(P, VOP_RESTART_DF, dvs + 3 * nsys, t_v, (int)tiles_v.size(), grid_v, s));
+    else
+      KL(vec_batch_any(P, VOP_RESTART, dvs + 2 * nsys, t_v, (int)tiles_v.size(), grid_v, s));
     return OQ_OK;
   };
-  auto reset_step = [&]() -> int {
-    KL(vec_batch_any(P, VOP_ACCX, dvs + 1 * nsys, t_v, (int)tiles_v.size(), grid_v, s));
-    CK(hop(4, P_F64, HOP_P1, 0, EPI_NONE));
-    CK(hop(5, P_F64, HOP_P2, 0, EPI_NONE));
-    CK(hop(6, P_F64, HOP_P1, 1, EPI_NONE));
-    CK(hop(7, P_F64, HOP_P2, 1, EPI_RESID64));
+  // rp: arithmetic of the residual recomputation; accumulate: add s x_s to
+  // x_d first (false re-checks the same x_d in binary64)
+  auto reset_step = [&](int rp, bool accumulate) -> int {
+    if (accumulate) KL(vec_batch_any(P, VOP_ACCX, dvs + 1 * nsys, t_v, (int)tiles_v.size(), grid_v, s));
+    if (rp == P_DF64) {
+      for (int s2 = 0; s2 < nsys; ++s2)
+        KL(split_f64((const double*)xd[s2], xdf[s2], spinor_half_bytes(Vh[s2], P_F64) / sizeof(double), s));
+      CK(hop(8, P_DF64, HOP_P1, 0, EPI_NONE));
+      CK(hop(9, P_DF64, HOP_P2, 0, EPI_NONE));
+      CK(hop(10, P_DF64, HOP_P1, 1, EPI_NONE));
+      CK(hop(11, P_DF64, HOP_P2, 1, EPI_RESID64));
+    } else {
+      CK(hop(4, P_F64, HOP_P1, 0, EPI_NONE));
+      CK(hop(5, P_F64, HOP_P2, 0, EPI_NONE));
+      CK(hop(6, P_F64, HOP_P1, 1, EPI_NONE));
+      CK(hop(7, P_F64, HOP_P2, 1, EPI_RESID64));
+    }
+    rd_prec = rp;
     return OQ_OK;
   };
   auto iteration = [&]() -> cudaError_t {
@@ -449,10 +519,28 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
         rst += cs[k].mode == MODE_RESET;
       }
       if (rst) {
-        r2 = reset_step();
+        r2 = reset_step(reset_prec, true);
         if (r2) return r2;
         r2 = download();
         if (r2) return r2;
+        if (reset_prec == P_DF64) {
+          // a double-float residual may only propose convergence: confirm in binary64
+          bool claims = false;
+          for (int k = 0; k < nsys; ++k)
+            if (cs[k].mode == MODE_RESET && sqrt(cs[k].rd2) <= prm->res * eta_n[k]) claims = true;
+          if (claims) {
+            std::vector<double> df(nsys);
+            for (int k = 0; k < nsys; ++k) df[k] = cs[k].rd2;
+            r2 = reset_step(P_F64, false);
+            if (r2) return r2;
+            r2 = download();
+            if (r2) return r2;
+            for (int k = 0; k < nsys; ++k)
+              if (cs[k].mode == MODE_RESET && sqrt(df[k]) <= prm->res * eta_n[k] &&
+                  sqrt(cs[k].rd2) > prm->res * eta_n[k])
+                reset_prec = P_F64;
+          }
+        }
         pending = decide(true);
         r2 = upload();
         if (r2) return r2;

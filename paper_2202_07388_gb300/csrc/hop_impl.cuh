@@ -73,20 +73,6 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p,
   }
 }
 
-// eo_neighbour for a runtime direction, without indexing a local array
-__device__ __forceinline__ long eo_neighbour_rt(const Geom& g, const int x[4], int mu, int d, bool* crossed) {
-  const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
-  const int xm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
-  int v = xm + d;
-  bool c = false;
-  if (v == L) { v = 0; c = true; }
-  if (v < 0) { v = L - 1; c = true; }
-  *crossed = c && (mu == 0);
-  const int y0 = mu == 0 ? v : x[0], y1 = mu == 1 ? v : x[1], y2 = mu == 2 ? v : x[2], y3 = mu == 3 ? v : x[3];
-  const long lex = (((long)y0 * g.L[1] + y1) * g.L[2] + y2) * g.L[3] + y3;
-  return lex >> 1;
-}
-
 // z * i^c for c in 0..3 (double-float): a swap of the parts for odd c and
 // sign flips, all by selects
 __device__ __forceinline__ cx<dfloat> rot_ic(const cx<dfloat>& z, int c) {
@@ -136,8 +122,9 @@ __device__ __forceinline__ void hop_loop_df(const HopArgs& a, const char* in, in
     for (int c = 0; c < 3; ++c) {
       const cx<dfloat> pa = swq ? nb.c[3][c] : nb.c[2][c];
       const cx<dfloat> pb = swq ? nb.c[2][c] : nb.c[3][c];
-      h.c[0][c] = nb.c[0][c] + rot_ic(pa, c0 & 3);
-      h.c[1][c] = nb.c[1][c] + rot_ic(pb, c1 & 3);
+      const cx<dfloat> ra = rot_ic(pa, c0 & 3), rb = rot_ic(pb, c1 & 3);
+      h.c[0][c] = cx<dfloat>{df_add_lazy(nb.c[0][c].re, ra.re), df_add_lazy(nb.c[0][c].im, ra.im)};
+      h.c[1][c] = cx<dfloat>{df_add_lazy(nb.c[1][c].re, rb.re), df_add_lazy(nb.c[1][c].im, rb.im)};
     }
     su3_mul(u, h, t);
     if (cr && a.g.bc_t < 0.f) {
@@ -151,14 +138,19 @@ __device__ __forceinline__ void hop_loop_df(const HopArgs& a, const char* in, in
     const int d1 = (mu == 0 ? 0 : mu == 1 ? 3 : mu == 2 ? 0 : 1) + sh;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      acc.c[0][c] = acc.c[0][c] + t.c[0][c];
-      acc.c[1][c] = acc.c[1][c] + t.c[1][c];
-      const cx<dfloat> ta = swq ? t.c[1][c] : t.c[0][c];
-      const cx<dfloat> tb = swq ? t.c[0][c] : t.c[1][c];
-      acc.c[2][c] = acc.c[2][c] + rot_ic(ta, d0 & 3);
-      acc.c[3][c] = acc.c[3][c] + rot_ic(tb, d1 & 3);
+      const cx<dfloat> ta = rot_ic(swq ? t.c[1][c] : t.c[0][c], d0 & 3);
+      const cx<dfloat> tb = rot_ic(swq ? t.c[0][c] : t.c[1][c], d1 & 3);
+      const cx<dfloat> up[4] = {t.c[0][c], t.c[1][c], ta, tb};
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2)
+        acc.c[s2][c] = cx<dfloat>{df_add_lazy(acc.c[s2][c].re, up[s2].re), df_add_lazy(acc.c[s2][c].im, up[s2].im)};
     }
   }
+  // the hops were summed without renormalising
+#pragma unroll
+  for (int s2 = 0; s2 < 4; ++s2)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc.c[s2][c] = cx<dfloat>{df_norm(acc.c[s2][c].re), df_norm(acc.c[s2][c].im)};
 }
 
 // One output site i (parity p) of right-hand side rhs: the stencil, the

@@ -101,6 +101,31 @@ __device__ __forceinline__ void store_sp(char* base, uint32_t Vh, uint32_t i, co
   }
 }
 
+// A site's spinor as loaded (16-byte chunks, not yet converted): 6 float4
+// (F32) or 3 uint4 (BF16/F16); component k (= 3 spin + colour) on demand.
+template <int P>
+struct RawSp {
+  static constexpr int NC = P == P_F32 ? 6 : 3;
+  uint4 ch[NC];
+  __device__ __forceinline__ void load(const char* base, uint32_t Vh, uint32_t j) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ch[c] = __ldg(b + (c * Vh + j));
+  }
+  __device__ __forceinline__ cx<float> get(int k) const {
+    if constexpr (P == P_F32) {
+      const uint4 v = ch[k / 2];
+      return (k & 1) ? cx<float>{__uint_as_float(v.z), __uint_as_float(v.w)}
+                     : cx<float>{__uint_as_float(v.x), __uint_as_float(v.y)};
+    } else {
+      const uint4 v = ch[k / 4];
+      const uint32_t w = (k % 4 == 0) ? v.x : (k % 4 == 1) ? v.y : (k % 4 == 2) ? v.z : v.w;
+      const float2 z = (P == P_BF16) ? unpack_bf16x2(w) : unpack_f16x2(w);
+      return cx<float>{z.x, z.y};
+    }
+  }
+};
+
 __device__ __forceinline__ void join(const Spinor<float>& a, const Spinor<float>& b, Sp2& s) {
 #pragma unroll
   for (int k = 0; k < 4; ++k)
@@ -146,86 +171,89 @@ __device__ __forceinline__ void load_u(const void* base, uint32_t Vh, int p, int
   }
 }
 
-// spin projection for the hop along mu: S = -1 (1 - g_mu), S = +1 (1 + g_mu)
-// (chiral basis; the same linear combinations as oq::project)
+// acc[.][a] += sg * reconstruction (projector 1 -/+ g_mu, S = -1 / +1) of
+// the transported colour-a components h0, h1 (spins 0, 1); sg = +-1 on both
+// lanes (the time-boundary factor)
 template <int MU, int S>
-__device__ __forceinline__ void project(const Sp2& p, Hs2& h) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const C2 p0 = p.c[0][a], p1 = p.c[1][a], p2 = p.c[2][a], p3 = p.c[3][a];
-    if constexpr (MU == 0) {
-      if constexpr (S < 0) { h.c[0][a] = cadd(p0, p2); h.c[1][a] = cadd(p1, p3); }
-      else                 { h.c[0][a] = csub(p0, p2); h.c[1][a] = csub(p1, p3); }
-    } else if constexpr (MU == 1) {
-      if constexpr (S < 0) { h.c[0][a] = cadd_i(p0, p3); h.c[1][a] = cadd_i(p1, p2); }
-      else                 { h.c[0][a] = csub_i(p0, p3); h.c[1][a] = csub_i(p1, p2); }
-    } else if constexpr (MU == 2) {
-      if constexpr (S < 0) { h.c[0][a] = cadd(p0, p3); h.c[1][a] = csub(p1, p2); }
-      else                 { h.c[0][a] = csub(p0, p3); h.c[1][a] = cadd(p1, p2); }
-    } else {
-      if constexpr (S < 0) { h.c[0][a] = cadd_i(p0, p2); h.c[1][a] = csub_i(p1, p3); }
-      else                 { h.c[0][a] = csub_i(p0, p2); h.c[1][a] = cadd_i(p1, p3); }
+__device__ __forceinline__ void accum_col(Sp2& acc, int a, const C2& h0, const C2& h1, F2 sg) {
+  if constexpr (MU == 0) {
+    // upper: +sg h; lower: l0 = h0, l1 = h1, negated for S = +1
+    const F2 ls = S < 0 ? sg : mul(sg, bc(-1.f));
+    acc.c[0][a] = {ffma(sg, h0.re, acc.c[0][a].re), ffma(sg, h0.im, acc.c[0][a].im)};
+    acc.c[1][a] = {ffma(sg, h1.re, acc.c[1][a].re), ffma(sg, h1.im, acc.c[1][a].im)};
+    acc.c[2][a] = {ffma(ls, h0.re, acc.c[2][a].re), ffma(ls, h0.im, acc.c[2][a].im)};
+    acc.c[3][a] = {ffma(ls, h1.re, acc.c[3][a].re), ffma(ls, h1.im, acc.c[3][a].im)};
+  } else {
+    acc.c[0][a] = cadd(acc.c[0][a], h0);
+    acc.c[1][a] = cadd(acc.c[1][a], h1);
+    if constexpr (MU == 1) {  // l0 = -i h1, l1 = -i h0
+      if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h1); acc.c[3][a] = csub_i(acc.c[3][a], h0); }
+      else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h1); acc.c[3][a] = cadd_i(acc.c[3][a], h0); }
+    } else if constexpr (MU == 2) {  // l0 = -h1, l1 = h0
+      if constexpr (S < 0) { acc.c[2][a] = csub(acc.c[2][a], h1); acc.c[3][a] = cadd(acc.c[3][a], h0); }
+      else                 { acc.c[2][a] = cadd(acc.c[2][a], h1); acc.c[3][a] = csub(acc.c[3][a], h0); }
+    } else {  // l0 = -i h0, l1 = i h1
+      if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h0); acc.c[3][a] = cadd_i(acc.c[3][a], h1); }
+      else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h0); acc.c[3][a] = csub_i(acc.c[3][a], h1); }
     }
   }
 }
 
-// y = U h (UD = false) or U^dag h (UD = true) on both spin components; the
-// link elements are broadcast to both lanes
-template <bool UD>
-__device__ __forceinline__ void su3(const Su3<float>& u, const Hs2& h, Hs2& y) {
+// One hop for a pair of right-hand sides, with little live state: the
+// projection reads the loaded chunks (n0, n1) directly, and each colour row
+// of U h (or U^dag h) is accumulated into acc as soon as it is formed, so
+// neither the converted neighbour spinor nor the transported half spinor is
+// held whole.  Same linear maps as project, su3 and accum_col.
+template <int P, int MU, int S, bool UD>
+__device__ __forceinline__ void hop_pair(const Su3<float>& u, const RawSp<P>& n0, const RawSp<P>& n1, Sp2& acc,
+                                         F2 sg) {
+  Hs2 h;
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int a = 0; a < 3; ++a) {
+    C2 pc[4];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      C2 acc;
+    for (int s = 0; s < 4; ++s) {
+      const cx<float> z0 = n0.get(3 * s + a), z1 = n1.get(3 * s + a);
+      pc[s] = {make_float2(z0.re, z1.re), make_float2(z0.im, z1.im)};
+    }
+    if constexpr (MU == 0) {
+      if constexpr (S < 0) { h.c[0][a] = cadd(pc[0], pc[2]); h.c[1][a] = cadd(pc[1], pc[3]); }
+      else                 { h.c[0][a] = csub(pc[0], pc[2]); h.c[1][a] = csub(pc[1], pc[3]); }
+    } else if constexpr (MU == 1) {
+      if constexpr (S < 0) { h.c[0][a] = cadd_i(pc[0], pc[3]); h.c[1][a] = cadd_i(pc[1], pc[2]); }
+      else                 { h.c[0][a] = csub_i(pc[0], pc[3]); h.c[1][a] = csub_i(pc[1], pc[2]); }
+    } else if constexpr (MU == 2) {
+      if constexpr (S < 0) { h.c[0][a] = cadd(pc[0], pc[3]); h.c[1][a] = csub(pc[1], pc[2]); }
+      else                 { h.c[0][a] = csub(pc[0], pc[3]); h.c[1][a] = cadd(pc[1], pc[2]); }
+    } else {
+      if constexpr (S < 0) { h.c[0][a] = cadd_i(pc[0], pc[2]); h.c[1][a] = csub_i(pc[1], pc[3]); }
+      else                 { h.c[0][a] = csub_i(pc[0], pc[2]); h.c[1][a] = cadd_i(pc[1], pc[3]); }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    C2 t[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      C2 y;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const float ur = UD ? u.m[b][a].re : u.m[a][b].re;
         const float ui = UD ? -u.m[b][a].im : u.m[a][b].im;
         const C2 x = h.c[s][b];
         if (b == 0) {
-          acc.re = mul(bc(ur), x.re);
-          acc.im = mul(bc(ur), x.im);
+          y.re = mul(bc(ur), x.re);
+          y.im = mul(bc(ur), x.im);
         } else {
-          acc.re = ffma(bc(ur), x.re, acc.re);
-          acc.im = ffma(bc(ur), x.im, acc.im);
+          y.re = ffma(bc(ur), x.re, y.re);
+          y.im = ffma(bc(ur), x.im, y.im);
         }
-        acc.re = ffma(bc(-ui), x.im, acc.re);
-        acc.im = ffma(bc(ui), x.re, acc.im);
+        y.re = ffma(bc(-ui), x.im, y.re);
+        y.im = ffma(bc(ui), x.re, y.im);
       }
-      y.c[s][a] = acc;
+      t[s] = y;
     }
-}
-
-// acc += sg * reconstruction of the transported half spinor t for the
-// projector (1 -/+ g_mu) (S = -1 / +1), sg = +-1 on both lanes
-template <int MU, int S>
-__device__ __forceinline__ void accum(Sp2& acc, const Hs2& t, F2 sg) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const C2 h0 = t.c[0][a], h1 = t.c[1][a];
-    if constexpr (MU == 0) {
-      // upper: +sg h; lower: l0 = h0, l1 = h1, negated for S = +1
-      const F2 nsg = mul(sg, bc(-1.f));
-      const F2 ls = S < 0 ? sg : nsg;
-      acc.c[0][a] = {ffma(sg, h0.re, acc.c[0][a].re), ffma(sg, h0.im, acc.c[0][a].im)};
-      acc.c[1][a] = {ffma(sg, h1.re, acc.c[1][a].re), ffma(sg, h1.im, acc.c[1][a].im)};
-      acc.c[2][a] = {ffma(ls, h0.re, acc.c[2][a].re), ffma(ls, h0.im, acc.c[2][a].im)};
-      acc.c[3][a] = {ffma(ls, h1.re, acc.c[3][a].re), ffma(ls, h1.im, acc.c[3][a].im)};
-    } else {
-      acc.c[0][a] = cadd(acc.c[0][a], h0);
-      acc.c[1][a] = cadd(acc.c[1][a], h1);
-      if constexpr (MU == 1) {  // l0 = -i h1, l1 = -i h0
-        if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h1); acc.c[3][a] = csub_i(acc.c[3][a], h0); }
-        else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h1); acc.c[3][a] = cadd_i(acc.c[3][a], h0); }
-      } else if constexpr (MU == 2) {  // l0 = -h1, l1 = h0
-        if constexpr (S < 0) { acc.c[2][a] = csub(acc.c[2][a], h1); acc.c[3][a] = cadd(acc.c[3][a], h0); }
-        else                 { acc.c[2][a] = cadd(acc.c[2][a], h1); acc.c[3][a] = csub(acc.c[3][a], h0); }
-      } else {  // l0 = -i h0, l1 = i h1
-        if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h0); acc.c[3][a] = cadd_i(acc.c[3][a], h1); }
-        else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h0); acc.c[3][a] = csub_i(acc.c[3][a], h1); }
-      }
-    }
+    accum_col<MU, S>(acc, a, t[0], t[1], sg);
   }
 }
 
@@ -342,29 +370,19 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
     load_u<FMT>(a.links, Vh, p, MU, i, u);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      Spinor<float> n0, n1;
-      load_sp<P>(in[2 * q], Vh, jf[MU], n0);
-      load_sp<P>(in[2 * q + 1], Vh, jf[MU], n1);
-      Sp2 nb;
-      join(n0, n1, nb);
-      Hs2 h, t;
-      project<MU, SF>(nb, h);
-      su3<false>(u, h, t);
-      accum<MU, SF>(acc[q], t, MU == 0 ? sf : bc(1.f));
+      RawSp<P> n0, n1;
+      n0.load(in[2 * q], Vh, jf[MU]);
+      n1.load(in[2 * q + 1], Vh, jf[MU]);
+      hop_pair<P, MU, SF, false>(u, n0, n1, acc[q], MU == 0 ? sf : bc(1.f));
     }
     // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
     load_u<FMT>(a.links, Vh, 1 - p, MU, jb[MU], u);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      Spinor<float> n0, n1;
-      load_sp<P>(in[2 * q], Vh, jb[MU], n0);
-      load_sp<P>(in[2 * q + 1], Vh, jb[MU], n1);
-      Sp2 nb;
-      join(n0, n1, nb);
-      Hs2 h, t;
-      project<MU, -SF>(nb, h);
-      su3<true>(u, h, t);
-      accum<MU, -SF>(acc[q], t, MU == 0 ? sb : bc(1.f));
+      RawSp<P> n0, n1;
+      n0.load(in[2 * q], Vh, jb[MU]);
+      n1.load(in[2 * q + 1], Vh, jb[MU]);
+      hop_pair<P, MU, -SF, true>(u, n0, n1, acc[q], MU == 0 ? sb : bc(1.f));
     }
   };
   hop(std::integral_constant<int, 0>{});
@@ -372,8 +390,9 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
   hop(std::integral_constant<int, 2>{});
   hop(std::integral_constant<int, 3>{});
 
+  // the result overwrites the hopping sum in place, one clover block at a time
   const F2 w = bc(MODE == HOP_P2 ? 0.5f : -0.5f);
-  Sp2 res[NP];
+  Sp2 (&res)[NP] = acc;
   if constexpr (MODE == HOP_P1) {
     // res = A^{-1} (w H in)
 #pragma unroll
@@ -394,16 +413,13 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       }
     }
   } else {
-    // res = A in2 + w H in
-    Sp2 loc[NP];
+    // res = A in2 + w H in; the site-local spinors stay in their loaded
+    // (unconverted) chunks until their block is multiplied
+    RawSp<P> loc[NR];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      Spinor<float> l0, l1;
-      const int r0 = rhs0 + 2 * q < a.nrhs ? rhs0 + 2 * q : a.nrhs - 1;
-      const int r1 = rhs0 + 2 * q + 1 < a.nrhs ? rhs0 + 2 * q + 1 : a.nrhs - 1;
-      load_sp<P>((const char*)a.in2 + (long)r0 * a.in2_stride + par_out, Vh, i, l0);
-      load_sp<P>((const char*)a.in2 + (long)r1 * a.in2_stride + par_out, Vh, i, l1);
-      join(l0, l1, loc[q]);
+    for (int k = 0; k < NR; ++k) {
+      const int r = rhs0 + k < a.nrhs ? rhs0 + k : a.nrhs - 1;
+      loc[k].load((const char*)a.in2 + (long)r * a.in2_stride + par_out, Vh, i);
     }
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -413,7 +429,10 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       for (int q = 0; q < NP; ++q) {
         C2 xv[6], yv[6];
 #pragma unroll
-        for (int r = 0; r < 6; ++r) xv[r] = loc[q].c[2 * b + r / 3][r % 3];
+        for (int r = 0; r < 6; ++r) {
+          const cx<float> z0 = loc[2 * q].get(6 * b + r), z1 = loc[2 * q + 1].get(6 * b + r);
+          xv[r] = {make_float2(z0.re, z1.re), make_float2(z0.im, z1.im)};
+        }
         blk_apply(k, xv, yv);
 #pragma unroll
         for (int r = 0; r < 6; ++r) {

@@ -122,6 +122,15 @@ __device__ __forceinline__ void dfa_add(DfAcc& a, dfloat x, dfloat y) {  // a +=
   a.e = __fadd_rn(a.e, __fadd_rn(t.lo, e));
 }
 __device__ __forceinline__ dfloat dfa_get(const DfAcc& a) { return df_fast_two_sum(a.s, a.e); }
+// x + y without the final renormalisation: the two-sum of the high parts
+// and the low parts added to its error (8 operations instead of 11).  The
+// low part may exceed ulp(hi)/2 by a few ulp; a product or another lazy sum
+// takes such a value as it is, and df_norm restores the normal form.
+__device__ __forceinline__ dfloat df_add_lazy(dfloat x, dfloat y) {
+  const dfloat s = df_two_sum(x.hi, y.hi);
+  return dfloat(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfloat df_norm(dfloat x) { return df_fast_two_sum(x.hi, x.lo); }
 // x * 2^k for a power of two s = 2^k: exact, both parts scaled
 __device__ __forceinline__ dfloat df_scale(dfloat x, float s) { return dfloat(x.hi * s, x.lo * s); }
 using ::fma;  // keep the float / double overloads visible next to the dfloat one
@@ -245,6 +254,20 @@ __device__ __forceinline__ long eo_neighbour(const Geom& g, const int x[4], int 
   y[mu] = v;
   *crossed = c && (mu == 0);
   return eo_index(g, y);
+}
+
+// eo_neighbour for a runtime direction, without indexing a local array
+__device__ __forceinline__ long eo_neighbour_rt(const Geom& g, const int x[4], int mu, int d, bool* crossed) {
+  const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+  const int xm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
+  int v = xm + d;
+  bool c = false;
+  if (v == L) { v = 0; c = true; }
+  if (v < 0) { v = L - 1; c = true; }
+  *crossed = c && (mu == 0);
+  const int y0 = mu == 0 ? v : x[0], y1 = mu == 1 ? v : x[1], y2 = mu == 2 ? v : x[2], y3 = mu == 3 ? v : x[3];
+  const long lex = (((long)y0 * g.L[1] + y1) * g.L[2] + y2) * g.L[3] + y3;
+  return lex >> 1;
 }
 
 // ---------------------------------------------------------------------------

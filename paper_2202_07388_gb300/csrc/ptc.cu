@@ -50,7 +50,7 @@ __device__ __forceinline__ void transport(const PtcArgs& a, const char* f, int q
   const int mu = (q - 1) >> 1;
   const bool fwd = ((q - 1) & 1) == 0;
   bool cr;
-  const long j = eo_neighbour(a.g, x, mu, fwd ? +1 : -1, &cr);
+  const long j = eo_neighbour_rt(a.g, x, mu, fwd ? +1 : -1, &cr);
   Spinor<float> s;
   load_spinor<P_F32>(f + (long)(1 - p) * a.hbytes, a.g.Vh, j, s);
   Su3<float> u;

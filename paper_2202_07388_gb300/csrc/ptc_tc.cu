@@ -79,7 +79,7 @@ __device__ __forceinline__ void tc_transport(const PtcTcArgs& a, const char* f, 
   const int mu = (q - 1) >> 1;
   const bool fwd = ((q - 1) & 1) == 0;
   bool cr;
-  const long j = eo_neighbour(a.g, x, mu, fwd ? +1 : -1, &cr);
+  const long j = eo_neighbour_rt(a.g, x, mu, fwd ? +1 : -1, &cr);
   Spinor<float> s;
   load_spinor<P_F32>(f + (long)(1 - p) * a.hbytes, a.g.Vh, j, s);
   Su3<float> u;
