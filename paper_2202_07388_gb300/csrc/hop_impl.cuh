@@ -261,8 +261,7 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
 }
 
 template <int P, int FMT, int MODE, bool DAG, int EPI>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
-  extern __shared__ double red_smem[];
+__device__ __forceinline__ void hop_kernel_body(const HopArgs& a, double* red_smem) {
   // CTA = blockDim.x sites x blockDim.y right-hand sides (one rhs per row:
   // the rows read the same links and clover blocks, served by L1).  The
   // grid index runs fastest over the rhs tiles of one site block, then (for
@@ -282,6 +281,20 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
   if constexpr (EPI != EPI_NONE) {
     grid_reduce(red, a.red, rhs, a.nrhs, red_smem, (unsigned)blk, gridDim.x / ntile);
   }
+}
+
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+  extern __shared__ double red_smem[];
+  hop_kernel_body<P, FMT, MODE, DAG, EPI>(a, red_smem);
+}
+
+// double-float only: at most 128 threads and 128 registers per thread, so
+// that 16 warps fit on an SM (the tuner weighs it against hop_kernel)
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+__global__ void __launch_bounds__(128, 4) hop_kernel_capped(const HopArgs a) {
+  extern __shared__ double red_smem[];
+  hop_kernel_body<P, FMT, MODE, DAG, EPI>(a, red_smem);
 }
 
 // Batched form over several systems (lattices / operators of any size, one
@@ -322,6 +335,13 @@ static cudaError_t launch_one(const HopLaunch& L, const HopArgs& a, cudaStream_t
     hop_batch_kernel<P, FMT, MODE, DAG, EPI><<<L.grid, bblock, (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32),
                                                 s>>>(L.sys, L.tiles, L.ntiles);
     return cudaGetLastError();
+  }
+  if constexpr (P == P_DF64) {
+    if (L.regcap) {
+      if (L.bx * L.by > 128) return cudaErrorInvalidValue;
+      hop_kernel_capped<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
+      return cudaGetLastError();
+    }
   }
   hop_kernel<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();

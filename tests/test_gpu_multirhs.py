@@ -103,8 +103,46 @@ def test_tune_set_rejects_inadmissible_launches():
     assert h.tune_set(oq.F16, 1, 4, 128, 2, nr=2, check=False) == oq.ERR_ARG     # 256 threads with nr > 1
     assert h.tune_set(oq.F64, 1, 4, 64, 1, nr=2, check=False) == oq.ERR_ARG      # binary64: one rhs per thread
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=3, check=False) == oq.ERR_ARG
-    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=1, regcap=1, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=1, regcap=1, check=False) == oq.ERR_ARG   # cap: nr > 1 or DF64
+    assert h.tune_set(oq.DF64, 1, 4, 128, 2, nr=1, regcap=1, check=False) == oq.ERR_ARG  # capped: <= 128 threads
+    assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=1) == oq.OK
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=4, regcap=1) == oq.OK
     assert h.tune_get(oq.F16, 1, 4)[4:] == (4, 1)
     h2 = make_handle(dims, u, 0.13, 1.0, oq.LINK_18)
     assert h2.tune_set(oq.F32, 1, 1, 64, 1, link_fmt=oq.LINK_12, check=False) == oq.ERR_ARG
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("cap", [0, 1])
+def test_double_float_kernels_pinned(case, cap):
+    """Double-float storage and arithmetic (one rhs per thread), with and
+    without the register cap, pinned with oq_tune_set: Dw, Dhat and their
+    adjoints within 1e-12 of the FP64 oracle for 3 right-hand sides."""
+    oq = _oq()
+    dims, eps, seed, kappa, csw = case
+    u, a, ainv = oracle_case(dims, eps, seed, kappa, csw)
+    h = make_handle(dims, u, kappa, csw, oq.LINK_12)
+    n = 3
+    for mode in (0, 1, 2):
+        h.tune_set(oq.DF64, mode, n, 32, 2, nr=1, regcap=cap)
+    psi = synth.make_source(dims, seed + 500, nrhs=n)
+    ev = np.stack([dirac.even_part(p) for p in psi])
+    for dagger in (False, True):
+        pin, pout = h.new_packed(oq.DF64, nrhs=n), h.new_packed(oq.DF64, nrhs=n)
+        h.pack(to_dev(psi), pin, oq.DF64, nrhs=n)
+        h.dw(pin, pout, oq.DF64, nrhs=n, dagger=dagger)
+        out = to_dev(np.zeros_like(psi))
+        h.unpack(pout, out, oq.DF64, nrhs=n)
+        got = from_dev(out, psi.shape)
+        for k in range(n):
+            ref = dirac.dw_dagger(u, a, psi[k]) if dagger else dirac.dw(u, a, psi[k])
+            assert rel_err(got[k], ref) < TOL[4]
+        pin, pout = h.new_packed(oq.DF64, oq.EVEN, nrhs=n), h.new_packed(oq.DF64, oq.EVEN, nrhs=n)
+        h.pack(to_dev(ev), pin, oq.DF64, oq.EVEN, nrhs=n)
+        h.dw_hat(pin, pout, oq.DF64, nrhs=n, dagger=dagger)
+        out = to_dev(np.zeros_like(ev))
+        h.unpack(pout, out, oq.DF64, oq.EVEN, nrhs=n)
+        got = from_dev(out, ev.shape)
+        for k in range(n):
+            ref = dirac.dw_hat_dagger(u, a, ainv, ev[k]) if dagger else dirac.dw_hat(u, a, ainv, ev[k])
+            assert rel_err(got[k], ref) < TOL[4]
