@@ -171,7 +171,22 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc.c[s][c] = cx<R>{0, 0};
     const R w = (MODE == HOP_P2) ? (R)0.5 : (R)-0.5;
-    if constexpr (std::is_same<R, dfloat>::value) {
+    constexpr bool DF = std::is_same<R, dfloat>::value;
+    if constexpr (DF && MODE != HOP_P1) {
+      // double-float: A in2 / w first (w = +-1/2, so the scaling is exact)
+      // while few registers are live; the unweighted hops add onto it and
+      // one final scaling by w gives A in2 + w H in
+      Spinor<R> loc;
+      load_spinor<P>((const char*)a.in2 + rhs * a.in2_stride + par_out, a.g.Vh, i, loc);
+      clover_apply<R>(a.clov, a.g.Vh, p, i, loc, acc);
+      const float iw = 1.f / w.hi;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          acc.c[s][c] = cx<R>{df_scale(acc.c[s][c].re, iw), df_scale(acc.c[s][c].im, iw)};
+    }
+    if constexpr (DF) {
       hop_loop_df<P, FMT, DAG>(a, in, p, i, x, acc);
     } else {
       hop_dir<P, FMT, 0, DAG>(a, in, p, i, x, acc, w);
@@ -179,7 +194,7 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
       hop_dir<P, FMT, 2, DAG>(a, in, p, i, x, acc, w);
       hop_dir<P, FMT, 3, DAG>(a, in, p, i, x, acc, w);
     }
-    if constexpr (std::is_same<R, dfloat>::value) {
+    if constexpr (DF) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -190,6 +205,8 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
     Spinor<R> res;
     if constexpr (MODE == HOP_P1) {
       clover_apply<R>(a.cinv, a.g.Vh, p, i, acc, res);
+    } else if constexpr (DF) {
+      res = acc;
     } else {
       const char* in2 = (const char*)a.in2 + rhs * a.in2_stride + par_out;
       Spinor<R> loc, al;

@@ -171,31 +171,32 @@ __device__ __forceinline__ void load_u(const void* base, uint32_t Vh, int p, int
   }
 }
 
-// acc[.][a] += sg * reconstruction (projector 1 -/+ g_mu, S = -1 / +1) of
-// the transported colour-a components h0, h1 (spins 0, 1); sg = +-1 on both
-// lanes (the time-boundary factor)
+// acc[.][a] += wt * reconstruction (projector 1 -/+ g_mu, S = -1 / +1) of
+// the transported colour-a components h0, h1 (spins 0, 1): every update is
+// one FMA with +-wt (wt = the hop weight +-1/2, times the time-boundary
+// factor for mu = 0).  The lower components are l0, l1 of the projector's
+// reconstruction: mu = 0: (h0, h1); 1: (-i h1, -i h0); 2: (-h1, h0);
+// 3: (-i h0, i h1); all negated for S = +1.
 template <int MU, int S>
-__device__ __forceinline__ void accum_col(Sp2& acc, int a, const C2& h0, const C2& h1, F2 sg) {
+__device__ __forceinline__ void accum_col(Sp2& acc, int a, const C2& h0, const C2& h1, F2 wt) {
+  const F2 nw = mul(wt, bc(-1.f));
+  const F2 pos = S < 0 ? wt : nw, neg = S < 0 ? nw : wt;
+  acc.c[0][a] = {ffma(wt, h0.re, acc.c[0][a].re), ffma(wt, h0.im, acc.c[0][a].im)};
+  acc.c[1][a] = {ffma(wt, h1.re, acc.c[1][a].re), ffma(wt, h1.im, acc.c[1][a].im)};
+  C2& l0 = acc.c[2][a];
+  C2& l1 = acc.c[3][a];
   if constexpr (MU == 0) {
-    // upper: +sg h; lower: l0 = h0, l1 = h1, negated for S = +1
-    const F2 ls = S < 0 ? sg : mul(sg, bc(-1.f));
-    acc.c[0][a] = {ffma(sg, h0.re, acc.c[0][a].re), ffma(sg, h0.im, acc.c[0][a].im)};
-    acc.c[1][a] = {ffma(sg, h1.re, acc.c[1][a].re), ffma(sg, h1.im, acc.c[1][a].im)};
-    acc.c[2][a] = {ffma(ls, h0.re, acc.c[2][a].re), ffma(ls, h0.im, acc.c[2][a].im)};
-    acc.c[3][a] = {ffma(ls, h1.re, acc.c[3][a].re), ffma(ls, h1.im, acc.c[3][a].im)};
+    l0 = {ffma(pos, h0.re, l0.re), ffma(pos, h0.im, l0.im)};
+    l1 = {ffma(pos, h1.re, l1.re), ffma(pos, h1.im, l1.im)};
+  } else if constexpr (MU == 1) {
+    l0 = {ffma(pos, h1.im, l0.re), ffma(neg, h1.re, l0.im)};
+    l1 = {ffma(pos, h0.im, l1.re), ffma(neg, h0.re, l1.im)};
+  } else if constexpr (MU == 2) {
+    l0 = {ffma(neg, h1.re, l0.re), ffma(neg, h1.im, l0.im)};
+    l1 = {ffma(pos, h0.re, l1.re), ffma(pos, h0.im, l1.im)};
   } else {
-    acc.c[0][a] = cadd(acc.c[0][a], h0);
-    acc.c[1][a] = cadd(acc.c[1][a], h1);
-    if constexpr (MU == 1) {  // l0 = -i h1, l1 = -i h0
-      if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h1); acc.c[3][a] = csub_i(acc.c[3][a], h0); }
-      else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h1); acc.c[3][a] = cadd_i(acc.c[3][a], h0); }
-    } else if constexpr (MU == 2) {  // l0 = -h1, l1 = h0
-      if constexpr (S < 0) { acc.c[2][a] = csub(acc.c[2][a], h1); acc.c[3][a] = cadd(acc.c[3][a], h0); }
-      else                 { acc.c[2][a] = cadd(acc.c[2][a], h1); acc.c[3][a] = csub(acc.c[3][a], h0); }
-    } else {  // l0 = -i h0, l1 = i h1
-      if constexpr (S < 0) { acc.c[2][a] = csub_i(acc.c[2][a], h0); acc.c[3][a] = cadd_i(acc.c[3][a], h1); }
-      else                 { acc.c[2][a] = cadd_i(acc.c[2][a], h0); acc.c[3][a] = csub_i(acc.c[3][a], h1); }
-    }
+    l0 = {ffma(pos, h0.im, l0.re), ffma(neg, h0.re, l0.im)};
+    l1 = {ffma(neg, h1.im, l1.re), ffma(pos, h1.re, l1.im)};
   }
 }
 
@@ -206,7 +207,7 @@ __device__ __forceinline__ void accum_col(Sp2& acc, int a, const C2& h0, const C
 // held whole.  Same linear maps as project, su3 and accum_col.
 template <int P, int MU, int S, bool UD>
 __device__ __forceinline__ void hop_pair(const Su3<float>& u, const RawSp<P>& n0, const RawSp<P>& n1, Sp2& acc,
-                                         F2 sg) {
+                                         F2 wt) {
   Hs2 h;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -253,7 +254,7 @@ __device__ __forceinline__ void hop_pair(const Su3<float>& u, const RawSp<P>& n0
       }
       t[s] = y;
     }
-    accum_col<MU, S>(acc, a, t[0], t[1], sg);
+    accum_col<MU, S>(acc, a, t[0], t[1], wt);
   }
 }
 
@@ -355,66 +356,20 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
     in[k] = (const char*)a.in + (long)r * a.in_stride + par_in;
   }
 
-  Sp2 acc[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q)
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[q].c[s][c] = {bc(0.f), bc(0.f)};
-
-  auto hop = [&](auto mu_c) {
-    constexpr int MU = decltype(mu_c)::value;
-    Su3<float> u;
-    // forward: U_mu(x) (1 -/+ g) psi(x + mu)
-    load_u<FMT>(a.links, Vh, p, MU, i, u);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      RawSp<P> n0, n1;
-      n0.load(in[2 * q], Vh, jf[MU]);
-      n1.load(in[2 * q + 1], Vh, jf[MU]);
-      hop_pair<P, MU, SF, false>(u, n0, n1, acc[q], MU == 0 ? sf : bc(1.f));
-    }
-    // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
-    load_u<FMT>(a.links, Vh, 1 - p, MU, jb[MU], u);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      RawSp<P> n0, n1;
-      n0.load(in[2 * q], Vh, jb[MU]);
-      n1.load(in[2 * q + 1], Vh, jb[MU]);
-      hop_pair<P, MU, -SF, true>(u, n0, n1, acc[q], MU == 0 ? sb : bc(1.f));
-    }
-  };
-  hop(std::integral_constant<int, 0>{});
-  hop(std::integral_constant<int, 1>{});
-  hop(std::integral_constant<int, 2>{});
-  hop(std::integral_constant<int, 3>{});
-
-  // the result overwrites the hopping sum in place, one clover block at a time
+  // The weighted hops accumulate onto acc: for pass 2 and Dw onto A in2,
+  // formed first while few registers are live (the site-local spinors stay
+  // in their loaded chunks until their clover block is multiplied), for
+  // pass 1 onto zero, then multiplied by A^{-1}.
   const F2 w = bc(MODE == HOP_P2 ? 0.5f : -0.5f);
-  Sp2 (&res)[NP] = acc;
+  Sp2 acc[NP];
   if constexpr (MODE == HOP_P1) {
-    // res = A^{-1} (w H in)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      Blk k;
-      load_blk(a.cinv, Vh, p, b, i, k);
+    for (int q = 0; q < NP; ++q)
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        C2 xv[6], yv[6];
+      for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
-          const C2 v = acc[q].c[2 * b + r / 3][r % 3];
-          xv[r] = {mul(w, v.re), mul(w, v.im)};
-        }
-        blk_apply(k, xv, yv);
-#pragma unroll
-        for (int r = 0; r < 6; ++r) res[q].c[2 * b + r / 3][r % 3] = yv[r];
-      }
-    }
+        for (int c = 0; c < 3; ++c) acc[q].c[s][c] = {bc(0.f), bc(0.f)};
   } else {
-    // res = A in2 + w H in; the site-local spinors stay in their loaded
-    // (unconverted) chunks until their block is multiplied
     RawSp<P> loc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -435,10 +390,54 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
         }
         blk_apply(k, xv, yv);
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
-          const C2 v = acc[q].c[2 * b + r / 3][r % 3];
-          res[q].c[2 * b + r / 3][r % 3] = {ffma(w, v.re, yv[r].re), ffma(w, v.im, yv[r].im)};
-        }
+        for (int r = 0; r < 6; ++r) acc[q].c[2 * b + r / 3][r % 3] = yv[r];
+      }
+    }
+  }
+  const F2 wf = mul(w, sf), wb = mul(w, sb);
+
+  auto hop = [&](auto mu_c) {
+    constexpr int MU = decltype(mu_c)::value;
+    Su3<float> u;
+    // forward: U_mu(x) (1 -/+ g) psi(x + mu)
+    load_u<FMT>(a.links, Vh, p, MU, i, u);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      RawSp<P> n0, n1;
+      n0.load(in[2 * q], Vh, jf[MU]);
+      n1.load(in[2 * q + 1], Vh, jf[MU]);
+      hop_pair<P, MU, SF, false>(u, n0, n1, acc[q], MU == 0 ? wf : w);
+    }
+    // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
+    load_u<FMT>(a.links, Vh, 1 - p, MU, jb[MU], u);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      RawSp<P> n0, n1;
+      n0.load(in[2 * q], Vh, jb[MU]);
+      n1.load(in[2 * q + 1], Vh, jb[MU]);
+      hop_pair<P, MU, -SF, true>(u, n0, n1, acc[q], MU == 0 ? wb : w);
+    }
+  };
+  hop(std::integral_constant<int, 0>{});
+  hop(std::integral_constant<int, 1>{});
+  hop(std::integral_constant<int, 2>{});
+  hop(std::integral_constant<int, 3>{});
+
+  Sp2 (&res)[NP] = acc;
+  if constexpr (MODE == HOP_P1) {
+    // res = A^{-1} (w H in), in place one clover block at a time
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      Blk k;
+      load_blk(a.cinv, Vh, p, b, i, k);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        C2 xv[6], yv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) xv[r] = acc[q].c[2 * b + r / 3][r % 3];
+        blk_apply(k, xv, yv);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) res[q].c[2 * b + r / 3][r % 3] = yv[r];
       }
     }
   }
@@ -458,49 +457,32 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       }
     }
   } else if constexpr (EPI == EPI_CG) {
-    // q = res; x += alpha p (x binary32); r -= alpha q; norm of the stored r
+    // q = res; x += alpha p (x binary32); r -= alpha q; norm of the stored r.
+    // One right-hand side at a time, from the loaded chunks, so that little
+    // besides the result stays live.
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      const int r0 = rhs0 + 2 * q < a.nrhs ? rhs0 + 2 * q : a.nrhs - 1;
-      const int r1 = rhs0 + 2 * q + 1 < a.nrhs ? rhs0 + 2 * q + 1 : a.nrhs - 1;
-      const F2 al = make_float2((float)a.cg[r0].alpha, (float)a.cg[r1].alpha);
-      const F2 nal = mul(al, bc(-1.f));
-      Spinor<float> t0, t1;
-      Sp2 pv, rv, xv;
-      load_sp<P>((const char*)a.ep_p + (long)r0 * a.ep_p_stride, Vh, i, t0);
-      load_sp<P>((const char*)a.ep_p + (long)r1 * a.ep_p_stride, Vh, i, t1);
-      join(t0, t1, pv);
-      load_sp<P>((const char*)a.ep_r + (long)r0 * a.ep_r_stride, Vh, i, t0);
-      load_sp<P>((const char*)a.ep_r + (long)r1 * a.ep_r_stride, Vh, i, t1);
-      join(t0, t1, rv);
-      load_sp<P_F32>((const char*)a.ep_x + (long)r0 * a.ep_x_stride, Vh, i, t0);
-      load_sp<P_F32>((const char*)a.ep_x + (long)r1 * a.ep_x_stride, Vh, i, t1);
-      join(t0, t1, xv);
+    for (int k = 0; k < NR; ++k) {
+      const int rr = rhs0 + k < a.nrhs ? rhs0 + k : a.nrhs - 1;
+      const float al = (float)a.cg[rr].alpha;
+      RawSp<P> pv, rv;
+      RawSp<P_F32> xv;
+      pv.load((const char*)a.ep_p + (long)rr * a.ep_p_stride, Vh, i);
+      rv.load((const char*)a.ep_r + (long)rr * a.ep_r_stride, Vh, i);
+      xv.load((const char*)a.ep_x + (long)rr * a.ep_x_stride, Vh, i);
+      Spinor<float> xo, ro;
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          xv.c[s][c].re = ffma(al, pv.c[s][c].re, xv.c[s][c].re);
-          xv.c[s][c].im = ffma(al, pv.c[s][c].im, xv.c[s][c].im);
-          rv.c[s][c].re = ffma(nal, res[q].c[s][c].re, rv.c[s][c].re);
-          rv.c[s][c].im = ffma(nal, res[q].c[s][c].im, rv.c[s][c].im);
-        }
-      Spinor<float> x0, x1, q0, q1;
-      lane<0>(xv, x0);
-      lane<1>(xv, x1);
-      lane<0>(rv, q0);
-      lane<1>(rv, q1);
-      round_trip<P>(q0);
-      round_trip<P>(q1);
-      if (live[2 * q]) {
-        store_sp<P_F32>((char*)a.ep_x + (long)r0 * a.ep_x_stride, Vh, i, x0);
-        store_sp<P>((char*)a.ep_r + (long)r0 * a.ep_r_stride, Vh, i, q0);
-        red[2 * q] = site_norm2(q0);
+      for (int m = 0; m < 12; ++m) {
+        const C2 qv = res[k / 2].c[m / 3][m % 3];
+        const float qre = (k & 1) ? qv.re.y : qv.re.x, qim = (k & 1) ? qv.im.y : qv.im.x;
+        const cx<float> pm = pv.get(m), rm = rv.get(m), xm = xv.get(m);
+        xo.c[m / 3][m % 3] = cx<float>{fmaf(al, pm.re, xm.re), fmaf(al, pm.im, xm.im)};
+        ro.c[m / 3][m % 3] = cx<float>{fmaf(-al, qre, rm.re), fmaf(-al, qim, rm.im)};
       }
-      if (live[2 * q + 1]) {
-        store_sp<P_F32>((char*)a.ep_x + (long)r1 * a.ep_x_stride, Vh, i, x1);
-        store_sp<P>((char*)a.ep_r + (long)r1 * a.ep_r_stride, Vh, i, q1);
-        red[2 * q + 1] = site_norm2(q1);
+      round_trip<P>(ro);
+      if (live[k]) {
+        store_sp<P_F32>((char*)a.ep_x + (long)rr * a.ep_x_stride, Vh, i, xo);
+        store_sp<P>((char*)a.ep_r + (long)rr * a.ep_r_stride, Vh, i, ro);
+        red[k] = site_norm2(ro);
       }
     }
   }
