@@ -540,7 +540,7 @@ def run_profile_case(args):
         h.dw_hat(b, a, prec, nrhs=nrhs, dagger=True)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "x".join(map(str, dims)), "prec": args.profile_prec, "nrhs": nrhs,
-                      "launches": h.kernel_launches()}))
+                      "tuner_launches": n_tune, "launches": h.kernel_launches()}))
     h.close()
     return 0
 
