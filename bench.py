@@ -630,14 +630,16 @@ def run_workload_c5(args):
     ada = oq.SolverParams(res=RES, nmx=2000, nkv=16, ncy=20, nmr=20, bs=(4, 4, 4, 4), sdtype=oq.F32, adaptive=1,
                           alpha=0.9)
     plain = oq.SolverParams(res=RES, nmx=5000, nkv=16, ncy=0, sdtype=oq.F32)
-    for name, prm, two in (("sap_gcr", sap, 0), ("sap_gcr_two_ctas", sap, 1), ("sap_gcr_adaptive", ada, 0),
-                           ("gcr", plain, 0)):
-        h.set_option(oq.OPT_SAP_TWO_CTAS, two)
+    # SAP block kernels: operands in shared memory (default), global operands one / two blocks per SM
+    for name, prm, kern in (("sap_gcr", sap, 0), ("sap_gcr_global_operands", sap, 1),
+                            ("sap_gcr_global_operands_two_ctas", sap, 2), ("sap_gcr_adaptive", ada, 0),
+                            ("gcr", plain, 0)):
+        h.set_option(oq.OPT_SAP_KERNEL, kern)
         h.sap_gcr(eta, psi, prm)
         t, (rc, st) = _timed(lambda: h.sap_gcr(eta, psi, prm))
         out[name] = {"s": t, "rc": rc, **{k: st[0][k] for k in ("steps", "restarts", "cycles", "mr_avg",
                                                                  "true_rel_res")}}
-    h.set_option(oq.OPT_SAP_TWO_CTAS, 0)
+    h.set_option(oq.OPT_SAP_KERNEL, 0)
     # training pairs (r, e = D^-1 r) from the binary64 SAP-GCR solver
     ntrain = args.nn_pairs
     r = synth.make_source(dims, 500, nrhs=ntrain)

@@ -221,10 +221,14 @@ int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int 
  *   tensor-core layers of oq_nnprec_apply_tc; default 0 = the binary32
  *   CUDA-core layers of oq_nnprec_apply (measured faster on GB300 for this
  *   small network). */
-/* OQ_OPT_SAP_TWO_CTAS: 1 (default) = the SAP block kernel caps its
- *   registers so that two 256-site blocks run per SM (a few spills to L1);
- *   0 = one block per SM with ~217 registers. */
-enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2, OQ_OPT_NN_TENSOR_CORES = 3, OQ_OPT_SAP_TWO_CTAS = 4 };
+/* OQ_OPT_SAP_KERNEL: the SAP block kernel (one CTA per block, one thread per
+ *   block site).  0 (default) = the block's links (18 reals) and clover
+ *   blocks are staged in shared memory once and the MR steps read only shared
+ *   memory (falls back to 2 when they do not fit in 227 KB); 1 = operands from
+ *   global memory, ~217 registers, one 256-site block per SM; 2 = operands
+ *   from global memory, registers capped so that two blocks run per SM.
+ *   Other values: OQ_ERR_ARG. */
+enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2, OQ_OPT_NN_TENSOR_CORES = 3, OQ_OPT_SAP_KERNEL = 4 };
 int oq_set_option(oq_handle h, int key, int value);
 
 /* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and

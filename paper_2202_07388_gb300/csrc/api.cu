@@ -326,7 +326,10 @@ extern "C" int oq_set_option(oq_handle h, int key, int value) {
     case OQ_OPT_DF64_RESETS: h->df64_resets = value != 0; return OQ_OK;
     case OQ_OPT_TEST_TC_SKIP_MMA: h->hook_tc_skip_commit = value != 0; return OQ_OK;
     case OQ_OPT_NN_TENSOR_CORES: h->nn_tensor_cores = value != 0; return OQ_OK;
-    case OQ_OPT_SAP_TWO_CTAS: h->sap_two_ctas = value != 0; return OQ_OK;
+    case OQ_OPT_SAP_KERNEL:
+      if (value < 0 || value > 2) return OQ_ERR_ARG;
+      h->sap_kernel = value;
+      return OQ_OK;
   }
   return OQ_ERR_ARG;
 }

@@ -92,7 +92,7 @@ struct oq_ctx {
   bool hook_tc_skip_commit = false;
   // SAP block kernel with registers capped for two CTAs per SM (measured ~5 %
   // faster on GB300 than one CTA with ~217 registers)
-  bool sap_two_ctas = true;
+  int sap_kernel = 0;        // OQ_OPT_SAP_KERNEL
   // NN-preconditioned GCR applies the network with the tensor-core layers
   // instead of the (measured faster) binary32 CUDA-core ones
   bool nn_tensor_cores = false;

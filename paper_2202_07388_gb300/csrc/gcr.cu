@@ -227,7 +227,7 @@ extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, c
     for (int colour = 0; colour < 2; ++colour) {
       h->launches += 1;
       if (sap_colour(L.g, prm->bs, colour, L.link_fmt, L.u32.p, L.a32.p, rho_dev, phi_dev, prm->nmr, prm->adaptive,
-                     alpha, mr_tol, nullptr, h->sap_two_ctas ? 1 : 0, s) != cudaSuccess)
+                     alpha, mr_tol, nullptr, h->sap_kernel, s) != cudaSuccess)
         return OQ_ERR_CUDA;
     }
   return OQ_OK;
@@ -381,7 +381,7 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
             for (int colour = 0; colour < 2; ++colour)
               KL(sap_colour(L.g, prm->bs, colour, L.link_fmt, L.u32.p, L.a32.p, rho, phik, prm->nmr, prm->adaptive,
                             (float)(prm->alpha > 0.0 ? prm->alpha : 0.9), prm->res * eta_n / nblk,
-                            (unsigned*)mrc, h->sap_two_ctas ? 1 : 0, s));
+                            (unsigned*)mrc, h->sap_kernel, s));
             cycles_total += 1;
             if (prm->adaptive) {
               // cycle test on the global SAP residual ||rho - D phi||

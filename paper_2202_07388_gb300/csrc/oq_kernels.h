@@ -45,6 +45,6 @@ int nnprec_forward_tc(struct ::oq_ctx* h, int lat, const float* master, const vo
 // one SAP half cycle: every block of `colour` (binary32 fields)
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
                        const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
-                       unsigned* mr_steps, int two_ctas, cudaStream_t s);
+                       unsigned* mr_steps, int kernel, cudaStream_t s);
 
 }  // namespace oq

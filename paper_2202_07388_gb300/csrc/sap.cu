@@ -17,6 +17,8 @@
 //      below tol = res ||eta|| / n_blocks; every decision is block-uniform;
 //   3. phi_i += x.
 // Block reductions are binary64.  Arithmetic and storage binary32.
+// sap_smem_kernel (the default) stages the block's links and clover in
+// shared memory first; sap_kernel reads them from global memory.
 #include "oq_internal.h"
 #include "oq_kernels.h"
 #include "hop_impl.cuh"
@@ -244,9 +246,258 @@ __global__ void __launch_bounds__(256, MINB) sap_kernel(const SapArgs a) {
   if (a.mr_steps && t == 0) atomicAdd(a.mr_steps, (unsigned)steps);
 }
 
+// ---------------------------------------------------------------------------
+// The same block solve with the block's operands staged in shared memory
+// once: the 4 forward links of every block site (18 reals, rebuilt from 12
+// where stored compressed) and its two clover blocks.  The MR steps then
+// read only shared memory (the residual, the links, the clover) instead of
+// fetching ~670 bytes per site and step from L2.  Static MR (not adaptive)
+// needs no norm reduction per step, only the barrier before the residual is
+// read again.  Shared memory: 24 + 4*18 + 72 floats per block site.
+// ---------------------------------------------------------------------------
+struct SapSm {
+  float* r;        // [24][nsite] block residual
+  float2* u;       // [mu][9][nsite] forward links, 18 reals
+  float4* a;       // [18][nsite] clover (two blocks: 6 diagonal + 15 complex each)
+  int nsite;
+};
+
+__device__ __forceinline__ void sm_link(const SapSm& m, int mu, int t, Su3<float>& u) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float2 v = m.u[(mu * 9 + k) * m.nsite + t];
+    u.m[k / 3][k % 3] = cx<float>{v.x, v.y};
+  }
+}
+
+__device__ __forceinline__ void sm_clover(const SapSm& m, int t, const Spinor<float>& in, Spinor<float>& out) {
+  const cx<float>* v = &in.c[0][0];
+  cx<float>* o = &out.c[0][0];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    float r[36];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 w = m.a[(9 * b + k) * m.nsite + t];
+      r[4 * k] = w.x;
+      r[4 * k + 1] = w.y;
+      r[4 * k + 2] = w.z;
+      r[4 * k + 3] = w.w;
+    }
+    const cx<float>* x = v + 6 * b;
+    cx<float>* y = o + 6 * b;
+#pragma unroll
+    for (int r0 = 0; r0 < 6; ++r0) y[r0] = r[r0] * x[r0];
+    int k = 0;
+#pragma unroll
+    for (int r0 = 0; r0 < 6; ++r0)
+#pragma unroll
+      for (int c0 = r0 + 1; c0 < 6; ++c0) {
+        const cx<float> off{r[6 + 2 * k], r[7 + 2 * k]};
+        cfma(y[r0], off, x[c0]);
+        cfmac(y[c0], off, x[r0]);
+        ++k;
+      }
+  }
+}
+
+// in-block hop along +mu / -mu, all operands from shared memory
+template <int MU>
+__device__ __forceinline__ void sm_block_hop(const SapSm& m, const int bs[4], int t, const int l[4],
+                                             Spinor<float>& acc) {
+  int stride = 1;
+  for (int nu = 3; nu > MU; --nu) stride *= bs[nu];
+  if (l[MU] + 1 < bs[MU]) {
+    Spinor<float> nb;
+    load_smem(m.r, m.nsite, t + stride, nb);
+    HalfSpinor<float> h, r;
+    project<MU, -1>(nb, h);
+    Su3<float> u;
+    sm_link(m, MU, t, u);
+    su3_mul(u, h, r);
+    accum_reconstruct<MU, -1>(acc, r, -0.5f);
+  }
+  if (l[MU] > 0) {
+    Spinor<float> nb;
+    load_smem(m.r, m.nsite, t - stride, nb);
+    HalfSpinor<float> h, r;
+    project<MU, +1>(nb, h);
+    Su3<float> u;
+    sm_link(m, MU, t - stride, u);  // U_mu(x - mu): the forward link of the site below
+    su3_dag_mul(u, h, r);
+    accum_reconstruct<MU, +1>(acc, r, -0.5f);
+  }
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) sap_smem_kernel(const SapArgs a) {
+  extern __shared__ float4 sm4[];
+  const int nsite = a.bs[0] * a.bs[1] * a.bs[2] * a.bs[3];
+  SapSm m;
+  m.nsite = nsite;
+  m.a = sm4;                                                   // 18 float4 per site
+  m.u = reinterpret_cast<float2*>(sm4 + 18 * nsite);           // 36 float2 per site
+  m.r = reinterpret_cast<float*>(m.u + 36 * nsite);            // 24 floats per site
+  double* red = reinterpret_cast<double*>(m.r + 24 * nsite);
+  const int t = threadIdx.x;
+  const bool act = t < nsite;
+  const int half3 = a.nb[3] / 2;
+  int row = blockIdx.x / half3;
+  const int mb = blockIdx.x % half3;
+  const int bc2 = row % a.nb[2];
+  row /= a.nb[2];
+  const int bc1 = row % a.nb[1];
+  const int bc0 = row / a.nb[1];
+  const int bc3 = 2 * mb + ((a.colour + bc0 + bc1 + bc2) & 1);
+  int l[4], x[4];
+  {
+    int tt = act ? t : 0;
+    l[3] = tt % a.bs[3];
+    tt /= a.bs[3];
+    l[2] = tt % a.bs[2];
+    tt /= a.bs[2];
+    l[1] = tt % a.bs[1];
+    l[0] = tt / a.bs[1];
+  }
+  x[0] = bc0 * a.bs[0] + l[0];
+  x[1] = bc1 * a.bs[1] + l[1];
+  x[2] = bc2 * a.bs[2] + l[2];
+  x[3] = bc3 * a.bs[3] + l[3];
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const long i = eo_index(a.g, x);
+
+  Spinor<float> r;
+  if (act) {
+    // stage the operands: forward links (18 reals) and clover of this site
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      Su3<float> u;
+      load_link<float, FMT>(a.links, a.g.Vh, p, mu, i, u);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) m.u[(mu * 9 + k) * nsite + t] = make_float2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
+    }
+    const float4* q = reinterpret_cast<const float4*>(a.clov) + (long)p * 18 * a.g.Vh;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) m.a[k * nsite + t] = __ldg(q + k * a.g.Vh + i);
+    // 1. block residual r = rho - D phi (full stencil, global operands)
+    HopArgs ha;
+    ha.g = a.g;
+    ha.links = a.links;
+    const char* nbf = a.phi + (long)(1 - p) * a.half_bytes;
+    Spinor<float> acc;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc.c[s][c] = cx<float>{0.f, 0.f};
+    hop_dir<P_F32, FMT, 0, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 1, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 2, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 3, false>(ha, nbf, p, i, x, acc, -0.5f);
+    Spinor<float> ph, aph, rh;
+    load_spinor<P_F32>(a.phi + (long)p * a.half_bytes, a.g.Vh, i, ph);
+    clover_apply<float>(a.clov, a.g.Vh, p, i, ph, aph);
+    load_spinor<P_F32>(a.rho + (long)p * a.half_bytes, a.g.Vh, i, rh);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r.c[s][c] = rh.c[s][c] - (aph.c[s][c] + acc.c[s][c]);
+    store_smem(m.r, nsite, t, r);
+  }
+  double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+  if (a.adaptive) {
+    if (act) n0 = site_norm2(r);
+    block_sum3(n0, z1, z2, red);  // also the barrier after the staging
+  } else {
+    __syncthreads();
+  }
+  double rn_prev = sqrt(n0);
+
+  // 2. MR on D_i, operands in shared memory
+  Spinor<float> xs;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xs.c[s][c] = cx<float>{0.f, 0.f};
+  int steps = 0;
+  for (int k = 1; k <= a.nmr; ++k) {
+    Spinor<float> pv;
+    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
+    if (act) {
+      Spinor<float> own;
+      load_smem(m.r, nsite, t, own);
+      sm_clover(m, t, own, pv);
+      sm_block_hop<0>(m, a.bs, t, l, pv);
+      sm_block_hop<1>(m, a.bs, t, l, pv);
+      sm_block_hop<2>(m, a.bs, t, l, pv);
+      sm_block_hop<3>(m, a.bs, t, l, pv);
+      float ar = 0.f, ai = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cx<float> q2 = pv.c[s][c], v = own.c[s][c];
+          ar += q2.re * v.re + q2.im * v.im;
+          ai += q2.re * v.im - q2.im * v.re;
+          a2 += q2.re * q2.re + q2.im * q2.im;
+        }
+      pr_re = ar;
+      pr_im = ai;
+      pp = a2;
+    }
+    block_sum3(pr_re, pr_im, pp, red);  // contains __syncthreads: all neighbour reads done
+    float om_re = 0.f, om_im = 0.f;
+    if (pp > 0.0) {
+      om_re = (float)(pr_re / pp);
+      om_im = (float)(pr_im / pp);
+    }
+    const cx<float> om{om_re, om_im};
+    double n1 = 0.0, y1 = 0.0, y2 = 0.0;
+    if (act) {
+      Spinor<float> own;
+      load_smem(m.r, nsite, t, own);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cfma(xs.c[s][c], om, own.c[s][c]);
+          own.c[s][c] = own.c[s][c] - om * pv.c[s][c];
+        }
+      store_smem(m.r, nsite, t, own);
+      n1 = site_norm2(own);
+    }
+    steps = k;
+    if (a.adaptive) {
+      block_sum3(n1, y1, y2, red);
+      const double rn_new = sqrt(n1);
+      if ((k >= 4 && rn_new > (double)a.alpha * rn_prev) || rn_new > rn_prev || rn_new < a.tol) break;
+      rn_prev = rn_new;
+    } else {
+      __syncthreads();  // the updated residual is read by the neighbours next step
+    }
+  }
+  // 3. phi_i += x
+  if (act) {
+    char* pp = a.phi + (long)p * a.half_bytes;
+    Spinor<float> ph;
+    load_spinor<P_F32>(pp, a.g.Vh, i, ph);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ph.c[s][c] = ph.c[s][c] + xs.c[s][c];
+    store_spinor<P_F32>(pp, a.g.Vh, i, ph);
+  }
+  if (a.mr_steps && t == 0) atomicAdd(a.mr_steps, (unsigned)steps);
+}
+
+size_t sap_smem_bytes(const int bs[4]) {
+  const int nsite = bs[0] * bs[1] * bs[2] * bs[3];
+  const int threads = (nsite + 31) / 32 * 32;
+  return sizeof(float) * (72 + 72 + 24) * (size_t)nsite + sizeof(double) * 3 * (threads / 32);
+}
+
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
                        const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
-                       unsigned* mr_steps, int two_ctas, cudaStream_t s) {
+                       unsigned* mr_steps, int kernel, cudaStream_t s) {
   SapArgs a;
   a.g = g;
   int nblk = 1;
@@ -270,7 +521,22 @@ cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, cons
   const int threads = (nsite + 31) / 32 * 32;
   const size_t smem = sizeof(float) * 24 * nsite + sizeof(double) * 3 * (threads / 32);
   dim3 grid(nblk / 2), block(threads);
-  if (two_ctas) {
+  if (kernel == 0) {
+    // operands in shared memory (the default), if they fit
+    const size_t sm2 = sap_smem_bytes(bs);
+    if (sm2 <= 227 * 1024) {
+      if (fmt == LINK_12) {
+        cudaFuncSetAttribute(sap_smem_kernel<LINK_12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        sap_smem_kernel<LINK_12><<<grid, block, sm2, s>>>(a);
+      } else {
+        cudaFuncSetAttribute(sap_smem_kernel<LINK_18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        sap_smem_kernel<LINK_18><<<grid, block, sm2, s>>>(a);
+      }
+      return cudaGetLastError();
+    }
+    kernel = 2;
+  }
+  if (kernel == 2) {
     if (fmt == LINK_12)
       sap_kernel<LINK_12, 2><<<grid, block, smem, s>>>(a);
     else

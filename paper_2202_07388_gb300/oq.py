@@ -23,7 +23,7 @@ F64, F32, BF16, F16, DF64 = 0, 1, 2, 3, 4
 LINK_18, LINK_12 = 0, 1
 EVEN, ODD, FULL = 0, 1, 2
 PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16, "df64": DF64}
-OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA, OPT_NN_TENSOR_CORES, OPT_SAP_TWO_CTAS = 1, 2, 3, 4
+OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA, OPT_NN_TENSOR_CORES, OPT_SAP_KERNEL = 1, 2, 3, 4
 
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_NOCONV, ERR_STATE = -1, -2, -3, -4, -5, -6, -7

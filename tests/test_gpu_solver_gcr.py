@@ -27,12 +27,16 @@ def _true_res(u, a, eta, x):
                                              ((4, 4, 4, 4), (2, 2, 2, 2), 1, 5),
                                              ((8, 4, 4, 8), (2, 2, 2, 4), 3, 2)])
 @pytest.mark.parametrize("link_fmt", [0, 1])
-def test_sap_apply_matches_oracle(dims, bs, ncy, nmr, link_fmt):
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_sap_apply_matches_oracle(dims, bs, ncy, nmr, link_fmt, kernel):
+    """Every SAP block kernel: operands in shared memory (0), global operands
+    with one (1) or two (2) blocks per SM."""
     oq = _oq()
     u, a, ainv = oracle_case(dims, 0.5, 21, 0.1365, 1.0)
     rho = synth.make_source(dims, 22)
     ref = solvers.sap(u, a, rho, bs, ncy, nmr)
     h = make_handle(dims, u, 0.1365, 1.0, link_fmt)
+    h.set_option(oq.OPT_SAP_KERNEL, kernel)
     prho, pphi = h.new_packed(oq.F32), h.new_packed(oq.F32)
     h.pack(to_dev(rho), prho, oq.F32)
     h.sap_apply(prho, pphi, oq.SolverParams(ncy=ncy, nmr=nmr, bs=bs))
@@ -77,13 +81,15 @@ def test_sap_reduces_gcr_steps_and_matches_oracle_solution():
     assert rel_err(x, ref.x) < 1e-8
 
 
-def test_adaptive_sap_gcr():
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_adaptive_sap_gcr(kernel):
     """Sec. 3.2: ncy, nmr are maxima (20, 20), alpha = 0.9."""
     oq = _oq()
     dims = (8, 8, 8, 8)
     u, a, ainv = oracle_case(dims, 0.5, 51, 0.1365, 1.0)
     eta = synth.make_source(dims, 52)
     h = make_handle(dims, u, 0.1365, 1.0, oq.LINK_12)
+    h.set_option(oq.OPT_SAP_KERNEL, kernel)
     psi = to_dev(np.zeros_like(eta))
     rc, st = h.sap_gcr(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=300, nkv=16, ncy=20, nmr=20,
                                                          bs=(4, 4, 4, 4), sdtype=oq.F32, adaptive=1, alpha=0.9))
