@@ -14,7 +14,8 @@ roofline = the dominant stencil kernel: its algorithmic bytes per launch /
 e2e      = the same bytes / time of the public call with host buffers
            (pinned host -> device copy of eta, solve, device -> host psi)
 tts      = time to solution of one right-hand side: binary64-only CGNE vs
-           the mixed-precision solves (the "vs plain FP64 GPU" comparison)
+           the mixed-precision solves (the "vs plain FP64 GPU" comparison),
+           and the precision ladders (one and 12 right-hand sides)
 
 --impl reference times the FP64 CPU oracle instead (a bounded sample: the
 oracle's Dhat^dag Dhat on one right-hand side of a 4 x 32^3 slab with the
@@ -308,6 +309,8 @@ def run_ours(args):
     if not args.no_tts:
         for pname, pc in (("f64", oq.F64), ("df64", oq.DF64), ("f32", oq.F32), ("bf16", oq.BF16), ("f16", oq.F16)):
             tuned[f"{pname}x1"] = {MODE_NAMES[m]: v for m, v in h.autotune(pc, nrhs=1).items()}
+        # the binary32 phase of the batched precision ladder
+        tuned[f"f32x{NRHS}"] = {MODE_NAMES[m]: v for m, v in h.autotune(oq.F32, nrhs=NRHS).items()}
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
 
@@ -423,6 +426,30 @@ def run_ours(args):
             torch.cuda.synchronize()
             tts[name] = {"s": time.perf_counter() - s0, "steps": st1[0]["steps"], "resets": st1[0]["resets"],
                          "true_rel_res": st1[0]["true_rel_res"], "converged": st1[0]["converged"]}
+        # precision ladders (Sec. 2, after Fig. 4): the storage type rises from
+        # one inner solve to the next once the residual is below its epsilon
+        for name, lad in (("ladder_fp16_fp32", (oq.F16, oq.F32)), ("ladder_fp16_fp32_fp64", (oq.F16, oq.F32, oq.F64)),
+                          ("ladder_bf16_fp32", (oq.BF16, oq.F32))):
+            p1 = oq.SolverParams(res=RES, nmx=50000, ladder=lad)
+            h.cgne(eta1, psi1, p1, nrhs=1)
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            rc, st1 = h.cgne(eta1, psi1, p1, nrhs=1)
+            torch.cuda.synchronize()
+            tts[name] = {"s": time.perf_counter() - s0, "steps": st1[0]["steps"], "resets": st1[0]["resets"],
+                         "steps_per_type": st1[0]["ladder_steps"][:len(lad)],
+                         "true_rel_res": st1[0]["true_rel_res"], "converged": st1[0]["converged"]}
+        for name, lad in (("batched_12rhs_ladder_fp16_fp32", (oq.F16, oq.F32)),
+                          ("batched_12rhs_ladder_fp16_fp32_fp64", (oq.F16, oq.F32, oq.F64))):
+            pl = oq.SolverParams(res=RES, nmx=20000, ladder=lad)
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            rc, stl = h.cgne(eta, psi, pl, nrhs=NRHS)
+            torch.cuda.synchronize()
+            tts[name] = {"s_per_rhs": (time.perf_counter() - s0) / NRHS,
+                         "max_true_rel_res": max(x["true_rel_res"] for x in stl),
+                         "resets": [x["resets"] for x in stl],
+                         "steps_per_type": [x["ladder_steps"][:len(lad)] for x in stl]}
         tts["speedup_fp16_vs_fp64"] = tts["fp64"]["s"] / tts["fp16"]["s"]
         tts["batched_12rhs_f16_s_per_rhs"] = (t_ms * 1e-3 / args.steps) / NRHS
         tts["speedup_batched_f16_vs_fp64_per_rhs"] = tts["fp64"]["s"] / tts["batched_12rhs_f16_s_per_rhs"]

@@ -97,6 +97,17 @@ typedef struct {
   double delta;      /* CGNE reset when ||r_rec|| <= delta ||r_reset||; <= 0: 10 eps of sdtype (max 0.1) */
   int adaptive;      /* SAP: adaptive cycle / MR counts (Sec. 3.2) */
   double alpha;      /* SAP adaptive MR ratio threshold (Sec. 3.2, default 0.9) */
+  /* CGNE precision ladder (Sec. 2, after Fig. 4): nladder = 0 (zero-initialised
+   * struct) runs every regular step in sdtype.  nladder in 1..4: the storage
+   * types ladder[0..nladder-1] (each OQ_F64 / OQ_F32 / OQ_BF16 / OQ_F16) replace
+   * sdtype; the regular steps of a right-hand side move from ladder[i] to
+   * ladder[i+1] at the first reset whose binary64 relative residual is
+   * <= ladder_c * eps(ladder[i]) (eps = 2^-10 / 2^-7 / 2^-23 for binary16 /
+   * bfloat16 / binary32; ladder_c <= 0 means 1), and delta follows the
+   * current type when it is <= 0.  oq_cgne_solve only (the batch: OQ_ERR_ARG). */
+  int nladder;
+  int ladder[4];
+  double ladder_c;
 } oq_solver_params;
 
 typedef struct {
@@ -107,6 +118,8 @@ typedef struct {
   double true_rel_res; /* binary64 ||eta - A psi|| / ||eta|| at exit */
   int cycles;          /* SAP-GCR: Schwarz cycles run in total */
   double mr_avg;       /* SAP-GCR: mean MR steps per block solve */
+  int ladder_steps[4]; /* CGNE: regular steps run in each storage type of the
+                          precision ladder (ladder[i]; index 0 = sdtype without one) */
 } oq_status;
 
 /* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no

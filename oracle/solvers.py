@@ -36,6 +36,7 @@ __all__ = [
     "norm",
     "CgneResult",
     "cgne",
+    "precision_ladder",
     "default_reset_delta",
     "block_index",
     "sap",
@@ -75,10 +76,22 @@ class CgneResult:
     converged: bool
     rel_res: float            # exact ||eta - A x|| / ||eta|| (binary64)
     history: list = field(default_factory=list)   # (step, exact, recursive)
+    phases: list = field(default_factory=list)    # storage type of every inner solve
+    reset_at: list = field(default_factory=list)  # value of status at every reset step
+
+
+def precision_ladder(types=("fp16", "fp32", "fp64")):
+    """The precision ladder of Sec. 2 (after Fig. 4): start the small-type CG
+    in the first type and move to the next one once the relative residual has
+    fallen below the machine epsilon of the current type (the paper asks for
+    a threshold that scales with epsilon; the factor 1 is the reading used
+    here).  Returns (type, switch_below) pairs; the last type never switches.
+    """
+    return [(t, machine_eps(t) if k + 1 < len(types) else 0.0) for k, t in enumerate(types)]
 
 
 def cgne(apply_a, eta, res, nmx, store="fp64", delta=None, history=False,
-         ncomp=None) -> CgneResult:
+         ncomp=None, ladder=None, scaled=True) -> CgneResult:
     """Solve A x = eta, A = Dhat^dag Dhat, by CG with binary64 reset steps.
 
     ``apply_a`` applies A in binary64.  The small type ``store`` is emulated
@@ -88,11 +101,23 @@ def cgne(apply_a, eta, res, nmx, store="fp64", delta=None, history=False,
     Between resets the small-type CG solves A x_s = r / s for the current
     exact residual r, scaled by s = ||r|| / sqrt(n) so that the stored
     components are O(1) (the per-vector scale that keeps binary16 inside its
-    range); n = ``ncomp`` complex components (default: all of ``eta``).  A reset adds s * x_s to the binary64 solution and recomputes
-    the residual exactly.  A reset is triggered when the recursive residual
+    range); n = ``ncomp`` complex components (default: all of ``eta``).
+    ``scaled=False`` takes s = 1 instead: the residual is cast to the small
+    type as it is, which is what the paper's simulation did (Fig. 4: binary16
+    then stalls once the residual components leave its range).  A reset adds
+    s * x_s to the binary64 solution and recomputes the residual exactly.  A reset is triggered when the recursive residual
     has fallen below delta times its value at the last reset, or below the
     target, or when ``nmx`` regular steps have been used.
+
+    ``ladder`` (optional, see ``precision_ladder``): the storage type of each
+    inner solve is chosen at its start from the relative binary64 residual:
+    the ladder moves to its next type while the residual is below the
+    current type's switch value; delta is then that type's default.
     """
+    stages = list(ladder) if ladder is not None else [(store, 0.0)]
+    stage = 0
+    store = stages[0][0]
+    fixed_delta = delta
     if delta is None:
         delta = default_reset_delta(store)
 
@@ -108,10 +133,18 @@ def cgne(apply_a, eta, res, nmx, store="fp64", delta=None, history=False,
     status = 0
     resets = 0
     hist = []
+    phases = []
+    reset_at = []
     if rn <= tol or rn == 0.0:
-        return CgneResult(x, 0, 0, True, rn / eta_norm if eta_norm else 0.0, hist)
+        return CgneResult(x, 0, 0, True, rn / eta_norm if eta_norm else 0.0, hist, phases, reset_at)
     while True:
-        s = rn / np.sqrt(n)
+        while stage + 1 < len(stages) and rn <= stages[stage][1] * eta_norm:
+            stage += 1
+        if stages[stage][0] != store:
+            store = stages[stage][0]
+            delta = fixed_delta if fixed_delta is not None else default_reset_delta(store)
+        phases.append(store)
+        s = rn / np.sqrt(n) if scaled else 1.0
         rs = rnd(r / s)
         p = rs.copy()
         xs = np.zeros_like(eta)
@@ -139,10 +172,11 @@ def cgne(apply_a, eta, res, nmx, store="fp64", delta=None, history=False,
         r = eta - apply_a(x)
         rn = norm(r)
         resets += 1
+        reset_at.append(status)
         if rn <= tol:
-            return CgneResult(x, status, resets, True, rn / eta_norm, hist)
+            return CgneResult(x, status, resets, True, rn / eta_norm, hist, phases, reset_at)
         if status >= nmx:
-            return CgneResult(x, status, resets, False, rn / eta_norm, hist)
+            return CgneResult(x, status, resets, False, rn / eta_norm, hist, phases, reset_at)
 
 
 # ---------------------------------------------------------------------------

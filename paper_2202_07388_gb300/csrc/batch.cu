@@ -166,7 +166,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
                                    void* stream) {
   if (!h || nsys < 1 || nsys > 64 || !lats || !prm || !eta_dev || !psi_dev || !st) return OQ_ERR_ARG;
   const int P = prm->sdtype;
-  if (P < 0 || P > 3 || !(prm->res > 0.0) || prm->nmx < 1) return OQ_ERR_ARG;
+  if (P < 0 || P > 3 || !(prm->res > 0.0) || prm->nmx < 1 || prm->nladder != 0) return OQ_ERR_ARG;
   int fmt = -1;
   for (int s = 0; s < nsys; ++s) {
     if (lats[s] < 0 || lats[s] >= (int)h->lats.size() || !eta_dev[s] || !psi_dev[s]) return OQ_ERR_ARG;
@@ -573,6 +573,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     st[k].restarts = 0;
     st[k].cycles = 0;
     st[k].mr_avg = 0.0;
+    for (int i = 0; i < 4; ++i) st[k].ladder_steps[i] = i == 0 ? cs[k].steps : 0;
     st[k].true_rel_res = eta_n[k] > 0.0 ? sqrt(cs[k].rd2) / eta_n[k] : 0.0;
     st[k].converged = (isfinite(cs[k].rd2) && st[k].true_rel_res <= prm->res) ? 1 : 0;
     if (!isfinite(cs[k].rd2)) ret = OQ_ERR_NONFINITE;

@@ -189,9 +189,15 @@ __global__ void __launch_bounds__(256) cg_restart_kernel(const char* rd, char* r
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          v.c[s][c] = cx<R>{(R)(__fadd_rn(d.c[s][c].re.hi, d.c[s][c].re.lo) * invf),
-                            (R)(__fadd_rn(d.c[s][c].im.hi, d.c[s][c].im.lo) * invf)};
+        for (int c = 0; c < 3; ++c) {
+          if constexpr (P == P_F64) {  // binary64 phase of a precision ladder: keep both words
+            v.c[s][c] = cx<R>{((double)d.c[s][c].re.hi + (double)d.c[s][c].re.lo) * inv,
+                              ((double)d.c[s][c].im.hi + (double)d.c[s][c].im.lo) * inv};
+          } else {
+            v.c[s][c] = cx<R>{(R)(__fadd_rn(d.c[s][c].re.hi, d.c[s][c].re.lo) * invf),
+                              (R)(__fadd_rn(d.c[s][c].im.hi, d.c[s][c].im.lo) * invf)};
+          }
+        }
     } else {
       Spinor<double> d;
       load_spinor<P_F64>(rd + rhs * sd, Vh, i, d);
@@ -222,6 +228,7 @@ cudaError_t cg_restart(int prec, const void* rd, int rd_prec, void* rs, void* p,
   cg_restart_kernel<PP, XX, RR><<<grid, block, 0, s>>>(d, r, pp, x, Vh, stride_d, stride_s, stride_xs, nrhs, ra)
   if (rd_prec == P_DF64) {
     switch (prec) {
+      case P_F64: OQ_RESTART(P_F64, P_F64, P_DF64); break;
       case P_F32: OQ_RESTART(P_F32, P_F32, P_DF64); break;
       case P_BF16: OQ_RESTART(P_BF16, P_F32, P_DF64); break;
       case P_F16: OQ_RESTART(P_F16, P_F32, P_DF64); break;

@@ -17,6 +17,15 @@
 // CTA of each fused grid reduction; the host looks at the per-rhs state once
 // every CHUNK iterations.
 //
+// Precision ladder (Sec. 2, after Fig. 4): the storage type of the regular
+// steps may change from one inner solve to the next, e.g. binary16 until the
+// binary64 residual is below eps(binary16) ||eta||, then binary32, then
+// binary64.  All right-hand sides of one call share the kernels of one type
+// (the phase): a right-hand side whose reset qualifies it for the next type
+// is parked (no kernel acts on it) until every other one is parked or done;
+// then the phase advances and the parked ones restart in the new type.  Each
+// right-hand side thus runs the same sequence of inner solves as alone.
+//
 // One iteration = 5 launches:
 //   P1(p -> t)  ;  P2(t, p -> u = Dhat p) + ||u||^2 -> alpha
 //   P1^dag(u -> t) ; P2^dag(t, u -> q) fused with x += alpha p, r -= alpha q,
@@ -36,10 +45,14 @@ namespace {
 
 const int CHUNK = 8;
 
+// unit of least precision at 1 of a storage type (0 for binary64 storage)
+double type_eps(int prec) {
+  return prec == P_F32 ? ldexp(1.0, -23) : prec == P_BF16 ? ldexp(1.0, -7)
+       : prec == P_F16 ? ldexp(1.0, -10) : 0.0;
+}
+
 double default_delta(int prec) {
-  const double eps = prec == P_F32 ? ldexp(1.0, -23) : prec == P_BF16 ? ldexp(1.0, -7)
-                   : prec == P_F16 ? ldexp(1.0, -10) : 0.0;
-  double d = 10.0 * eps;
+  double d = 10.0 * type_eps(prec);
   return d > 0.1 ? 0.1 : d;
 }
 
@@ -48,14 +61,32 @@ double default_delta(int prec) {
 extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev,
                              double* psi_dev, int nrhs, oq_status* st, void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
-  const int P = prm->sdtype;
-  if (P < 0 || P > 3 || !(prm->res > 0.0) || prm->nmx < 1) return OQ_ERR_ARG;
+  if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nladder < 0 || prm->nladder > 4) return OQ_ERR_ARG;
+  // the storage types of the phases: sdtype alone, or the ladder
+  std::vector<int> phase_prec;
+  if (prm->nladder == 0) phase_prec.push_back(prm->sdtype);
+  for (int i = 0; i < prm->nladder; ++i) phase_prec.push_back(prm->ladder[i]);
+  for (int q : phase_prec)
+    if (q < 0 || q > 3) return OQ_ERR_ARG;
+  const double ladder_c = prm->ladder_c > 0.0 ? prm->ladder_c : 1.0;
+  const int nphase = (int)phase_prec.size();
+  int phase = 0;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   const long Vh = L.g.Vh;
-  const int XP = P == P_F64 ? P_F64 : P_F32;
-  const size_t h64 = spinor_half_bytes(Vh, P_F64), hP = spinor_half_bytes(Vh, P), hX = spinor_half_bytes(Vh, XP);
+  // small type of the current phase (P), its solution type (XP) and sizes;
+  // buffers are sized for the largest type of any phase
+  int P = phase_prec[0];
+  int XP = P == P_F64 ? P_F64 : P_F32;
+  const size_t h64 = spinor_half_bytes(Vh, P_F64);
+  size_t hP = spinor_half_bytes(Vh, P), hX = spinor_half_bytes(Vh, XP);
+  size_t hPmax = 0, hXmax = 0;
+  for (int q : phase_prec) {
+    const size_t a = spinor_half_bytes(Vh, q), b = spinor_half_bytes(Vh, q == P_F64 ? P_F64 : P_F32);
+    hPmax = a > hPmax ? a : hPmax;
+    hXmax = b > hXmax ? b : hXmax;
+  }
   const size_t canon_field = sizeof(double) * 24 * 2 * Vh;
   void *eta64, *xd, *rd, *t64, *u64v, *pv, *rv, *uv, *tv, *xs;
   int rc = 0;
@@ -64,11 +95,11 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   rc |= h->workspace(lat, "cg_rd", h64 * nrhs, &rd);
   rc |= h->workspace(lat, "cg_t64", h64 * nrhs, &t64);
   rc |= h->workspace(lat, "cg_u64", h64 * nrhs, &u64v);
-  rc |= h->workspace(lat, "cg_p", hP * nrhs, &pv);
-  rc |= h->workspace(lat, "cg_r", hP * nrhs, &rv);
-  rc |= h->workspace(lat, "cg_u", hP * nrhs, &uv);
-  rc |= h->workspace(lat, "cg_t", hP * nrhs, &tv);
-  rc |= h->workspace(lat, "cg_xs", hX * nrhs, &xs);
+  rc |= h->workspace(lat, "cg_p", hPmax * nrhs, &pv);
+  rc |= h->workspace(lat, "cg_r", hPmax * nrhs, &rv);
+  rc |= h->workspace(lat, "cg_u", hPmax * nrhs, &uv);
+  rc |= h->workspace(lat, "cg_t", hPmax * nrhs, &tv);
+  rc |= h->workspace(lat, "cg_xs", hXmax * nrhs, &xs);
   if (rc) return OQ_ERR_NOMEM;
   const long grid_hop = (Vh + 31) / 32;  // upper bound on CTAs of any stencil launch
   rc = h->ensure_reduce(2 * nrhs, grid_hop > reduce_grid(Vh) ? grid_hop : reduce_grid(Vh));
@@ -93,7 +124,7 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   // eta -> packed binary64 even field; x_d = 0, x_s = 0
   KL(pack_spinor(L.g, P_F64, OQ_EVEN, eta_dev, eta64, 1.0, nrhs, 2 * Vh * 12, (long)h64, s));
   CK(cudaMemsetAsync(xd, 0, h64 * nrhs, s));
-  CK(cudaMemsetAsync(xs, 0, hX * nrhs, s));
+  CK(cudaMemsetAsync(xs, 0, hXmax * nrhs, s));
   CK(cudaMemcpyAsync(rd, eta64, h64 * nrhs, cudaMemcpyDeviceToDevice, s));
   {
     RedArgs ra = h->red_args(FIN_STORE, 0);
@@ -103,7 +134,7 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   CK(cudaStreamSynchronize(s));
   std::vector<double> eta_n(nrhs);
   std::vector<int> resets(nrhs, 0);
-  const double delta = prm->delta > 0.0 ? prm->delta : default_delta(P);
+  std::vector<int> phase_steps(4 * (size_t)nrhs, 0), steps_before(nrhs, 0);
   const double ncomp = 12.0 * (double)Vh;
   CgState* cs = h->cg_host;
   for (int k = 0; k < nrhs; ++k) {
@@ -112,12 +143,14 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     cs[k].mode = MODE_RESET;
     cs[k].rd2 = h->results_host[k];
     cs[k].nmx = prm->nmx;
-    cs[k].delta2 = delta * delta;
   }
 
-  // decide, per rhs in MODE_RESET, between DONE and a restart of the small CG
+  // decide, per rhs in MODE_RESET, between DONE, PARK (a later phase of the
+  // ladder) and a restart of the small CG in the current phase
   auto decide = [&](bool count) -> int {
     int pending = 0;
+    const double delta = prm->delta > 0.0 ? prm->delta : default_delta(P);
+    const double sw = phase + 1 < nphase ? ladder_c * type_eps(P) : 0.0;
     for (int k = 0; k < nrhs; ++k) {
       CgState& c = cs[k];
       if (c.mode != MODE_RESET) continue;
@@ -128,6 +161,11 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
         c.mode = MODE_DONE;
         continue;
       }
+      if (rn <= sw * eta_n[k]) {
+        c.mode = MODE_PARK;
+        continue;
+      }
+      c.delta2 = delta * delta;
       c.scale = rn / sqrt(ncomp);
       const double t = prm->res * eta_n[k] / c.scale;
       c.tol2 = t * t;
@@ -145,10 +183,18 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     CK(cudaStreamSynchronize(s));
     return OQ_OK;
   };
-  // storage of r_d: binary64, or double-float after a double-float reset
-  // (every rhs that restarts was reset by the latest reset step)
-  int rd_prec = P_F64;
+  // storage of r_d per rhs: binary64, or double-float after a double-float
+  // reset.  The rhs that restart together share it: they were reset by the
+  // same reset step, or (parked rhs at a phase change) are made to share it.
+  std::vector<int> rd_fmt(nrhs, P_F64);
   auto restart = [&]() -> int {
+    int rd_prec = -1;
+    for (int k = 0; k < nrhs; ++k)
+      if (cs[k].mode == MODE_RESET) {
+        if (rd_prec >= 0 && rd_fmt[k] != rd_prec) return OQ_ERR_STATE;
+        rd_prec = rd_fmt[k];
+      }
+    if (rd_prec < 0) return OQ_OK;
     RedArgs ra = h->red_args(FIN_RESTART, MODE_RESET);
     KL(cg_restart(P, rd, rd_prec, rv, pv, xs, XP, Vh, (long)h64, (long)hP, (long)hX, nrhs, ra, s));
     return OQ_OK;
@@ -193,17 +239,22 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     a.ep_eta = eta_in; a.ep_eta_stride = (long)h64;
     a.red = h->red_args(FIN_RD2, MODE_RESET);
     RK(h->run_hop(h->hop_launch(lat, rp, HOP_P2, 1, EPI_RESID64, nrhs), a, s));
-    rd_prec = rp;
+    for (int k = 0; k < nrhs; ++k)
+      if (cs[k].mode == MODE_RESET) rd_fmt[k] = rp;
     return OQ_OK;
   };
 
   // one regular step for all rhs in MODE_RUN
-  HopArgs it = h->hop_args(lat, P);
-  it.nrhs = nrhs;
-  it.cg = h->cg_dev;
-  it.gate = MODE_RUN;
-  it.in_stride = it.in2_stride = it.out_stride = (long)hP;
-  it.half_bytes = (long)hP;
+  HopArgs it;
+  auto set_phase_args = [&]() {
+    it = h->hop_args(lat, P);
+    it.nrhs = nrhs;
+    it.cg = h->cg_dev;
+    it.gate = MODE_RUN;
+    it.in_stride = it.in2_stride = it.out_stride = (long)hP;
+    it.half_bytes = (long)hP;
+  };
+  set_phase_args();
   auto iteration = [&]() -> int {
     HopArgs a = it;
     a.in = pv; a.out = tv; a.p = 1;
@@ -227,18 +278,55 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   // The intermediate resets of a low-precision solve use double-float
   // arithmetic (OQ_OPT_DF64_RESETS, default; else binary64 as in the
   // paper); every convergence decision is still taken in binary64.
-  int reset_prec = (P != P_F64 && h->df64_resets) ? P_DF64 : P_F64;
+  // A binary64 phase resets in binary64 (its inner solve reaches the target).
+  bool df_ok = h->df64_resets;
+  auto reset_prec_of = [&]() { return (P != P_F64 && df_ok) ? P_DF64 : P_F64; };
   int pending = decide(false);
   RK(upload());
   if (pending) RK(restart());
   for (;;) {
     RK(download());
-    int run = 0, rst = 0;
+    int run = 0, rst = 0, park = 0;
     for (int k = 0; k < nrhs; ++k) {
       run += cs[k].mode == MODE_RUN;
       rst += cs[k].mode == MODE_RESET;
+      park += cs[k].mode == MODE_PARK;
+    }
+    if (!run && !rst && park) {
+      // every live rhs waits for the next type: advance the phase and decide
+      // again for the parked ones (they may skip further phases)
+      for (int k = 0; k < nrhs; ++k) {
+        phase_steps[4 * k + phase] = cs[k].steps - steps_before[k];
+        steps_before[k] = cs[k].steps;
+      }
+      phase += 1;
+      P = phase_prec[phase];
+      XP = P == P_F64 ? P_F64 : P_F32;
+      hP = spinor_half_bytes(Vh, P);
+      hX = spinor_half_bytes(Vh, XP);
+      set_phase_args();
+      int fmt = -1;
+      bool mixed = false;
+      for (int k = 0; k < nrhs; ++k)
+        if (cs[k].mode == MODE_PARK) {
+          cs[k].mode = MODE_RESET;
+          mixed |= fmt >= 0 && rd_fmt[k] != fmt;
+          fmt = rd_fmt[k];
+        }
+      if (mixed) {
+        // a binary64 confirmation reset some of them after others were parked:
+        // recompute every parked residual in binary64 (x_d unchanged)
+        RK(upload());
+        RK(reset_step(P_F64, false));
+        RK(download());
+      }
+      pending = decide(false);
+      RK(upload());
+      if (pending) RK(restart());
+      continue;
     }
     if (rst) {
+      const int reset_prec = reset_prec_of();
       RK(reset_step(reset_prec, true));
       RK(download());
       if (reset_prec == P_DF64) {
@@ -256,7 +344,7 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
           for (int k = 0; k < nrhs; ++k)
             if (cs[k].mode == MODE_RESET && sqrt(df[k]) <= prm->res * eta_n[k] &&
                 sqrt(cs[k].rd2) > prm->res * eta_n[k])
-              reset_prec = P_F64;
+              df_ok = false;
         }
       }
       pending = decide(true);
@@ -274,9 +362,13 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   CK(cudaStreamSynchronize(s));
   int ret = OQ_OK;
   for (int k = 0; k < nrhs; ++k) {
+    phase_steps[4 * k + phase] = cs[k].steps - steps_before[k];
+    for (int i = 0; i < 4; ++i) st[k].ladder_steps[i] = phase_steps[4 * k + i];
     st[k].steps = cs[k].steps;
     st[k].resets = resets[k];
     st[k].restarts = 0;
+    st[k].cycles = 0;
+    st[k].mr_avg = 0.0;
     st[k].true_rel_res = eta_n[k] > 0.0 ? sqrt(cs[k].rd2) / eta_n[k] : 0.0;
     st[k].converged = (isfinite(cs[k].rd2) && st[k].true_rel_res <= prm->res) ? 1 : 0;
     if (!isfinite(cs[k].rd2)) ret = OQ_ERR_NONFINITE;

@@ -482,6 +482,7 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
     st[r].converged = (!nonfinite && rn <= tol) ? 1 : 0;
     st[r].cycles = cycles_total;
     st[r].mr_avg = (precs > 0 && nblk > 0) ? (double)mr_total / ((double)cycles_total * nblk) : 0.0;
+    for (int i = 0; i < 4; ++i) st[r].ladder_steps[i] = 0;
     if (nonfinite) ret = OQ_ERR_NONFINITE;
     else if (!st[r].converged && ret == OQ_OK) ret = OQ_ERR_NOCONV;
   }

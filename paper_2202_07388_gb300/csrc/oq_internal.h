@@ -20,12 +20,14 @@ struct CgState {
   double delta2;    // reset threshold factor delta^2
   double scale;     // s: the small-type system is A x_s = r_d / s
   double rd2;       // ||r_d||^2 of the binary64 residual after a reset
-  int mode;         // MODE_RUN, MODE_RESET, MODE_DONE
+  int mode;         // MODE_RUN, MODE_RESET, MODE_DONE, MODE_PARK
   int reason;       // why regular steps stopped
   int steps;        // regular steps so far
   int nmx;
 };
-enum { MODE_RUN = 0, MODE_RESET = 1, MODE_DONE = 2 };
+// MODE_PARK: reset, waiting for the next storage type of a precision ladder
+// (no kernel acts on it)
+enum { MODE_RUN = 0, MODE_RESET = 1, MODE_DONE = 2, MODE_PARK = 3 };
 enum { WHY_NONE = 0, WHY_DELTA = 1, WHY_TOL = 2, WHY_NMX = 3, WHY_NONFINITE = 4, WHY_BREAKDOWN = 5 };
 
 // reduction finishers run by the last CTA of a grid reduction

@@ -37,13 +37,14 @@ class OqSolverParams(C.Structure):
     _fields_ = [
         ("res", C.c_double), ("nmx", C.c_int), ("nkv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
         ("bs", C.c_int * 4), ("sdtype", C.c_int), ("delta", C.c_double), ("adaptive", C.c_int),
-        ("alpha", C.c_double),
+        ("alpha", C.c_double), ("nladder", C.c_int), ("ladder", C.c_int * 4), ("ladder_c", C.c_double),
     ]
 
 
 class OqStatus(C.Structure):
     _fields_ = [("steps", C.c_int), ("resets", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
-                ("true_rel_res", C.c_double), ("cycles", C.c_int), ("mr_avg", C.c_double)]
+                ("true_rel_res", C.c_double), ("cycles", C.c_int), ("mr_avg", C.c_double),
+                ("ladder_steps", C.c_int * 4)]
 
 
 class OqKernelTime(C.Structure):
@@ -151,6 +152,8 @@ class SolverParams:
     delta: float = 0.0
     adaptive: int = 0
     alpha: float = 0.9
+    ladder: tuple = ()        # CGNE precision ladder, e.g. (F16, F32, F64); () = sdtype throughout
+    ladder_c: float = 0.0     # switch constant (x eps of the current type); <= 0: 1
 
     def c(self):
         p = OqSolverParams()
@@ -158,12 +161,19 @@ class SolverParams:
         for k in range(4):
             p.bs[k] = self.bs[k]
         p.sdtype, p.delta, p.adaptive, p.alpha = self.sdtype, self.delta, self.adaptive, self.alpha
+        if len(self.ladder) > 4:
+            raise ValueError("a precision ladder has at most 4 types")
+        p.nladder = len(self.ladder)
+        for k, t in enumerate(self.ladder):
+            p.ladder[k] = t
+        p.ladder_c = self.ladder_c
         return p
 
 
 def status_dict(s: OqStatus) -> dict:
     return {"steps": s.steps, "resets": s.resets, "restarts": s.restarts, "converged": bool(s.converged),
-            "true_rel_res": s.true_rel_res, "cycles": s.cycles, "mr_avg": s.mr_avg}
+            "true_rel_res": s.true_rel_res, "cycles": s.cycles, "mr_avg": s.mr_avg,
+            "ladder_steps": list(s.ladder_steps)}
 
 
 class Handle:

@@ -189,3 +189,111 @@ def test_gcr_fp32_krylov_vectors_restart_to_binary64():
     pre = lambda v: solvers.sap(u, a, v, (2, 2, 2, 2), 1, 4, store="fp32")
     r = solvers.fgcr(d, pre, eta, 1e-10, 200, 6, store="fp32")
     assert r.converged and r.rel_res <= 1e-10 and r.restarts >= 2
+
+
+# ---------------------------------------------------------------------------
+# Fig. 4 storage-type sweep and the precision ladder (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def _fig4_case():
+    u, a, ainv = gauge_case()
+    dh, dhd = _even_ops(u, a, ainv)
+    eta = dirac.even_part(rand_spinor(u.shape[:4], 34))
+    return (lambda v: dhd(dh(v))), eta
+
+
+def _read_rows(name):
+    rows = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.strip() and line[0] != "#":
+            f = line.split()
+            rows[f[0]] = f[1:]
+    return rows
+
+
+def test_fig4_reset_counts_match_the_paper():
+    """Sec. 2 (after Fig. 4): binary32 -> tensorfloat32 -> bfloat16 each cost
+    4 more reset steps; the reset counts (2, 6, 10) are those the paper
+    states.  The reset rule (delta ~ 10 eps of the type) decides them."""
+    apply_a, eta = _fig4_case()
+    paper = _read_rows("fig4_paper_counts.txt")
+    got = {t: solvers.cgne(apply_a, eta, 1e-12, 3000, t, ncomp=1536) for t in ("fp32", "tf32", "bf16")}
+    for t, r in got.items():
+        assert r.converged and r.rel_res <= 1e-12
+        assert r.resets == int(paper[t][1]), (t, r.resets)
+    # the less precision, the more regular steps (the paper: +1 each; here a few)
+    assert got["fp32"].status <= got["tf32"].status <= got["bf16"].status
+    assert got["bf16"].status - got["fp32"].status <= 10
+
+
+def test_fig4_hierarchy_and_first_resets():
+    """Sec. 2, the step hierarchy binary64 < binary32 <= tensorfloat32 <=
+    {binary16, bfloat16}, and the order of the first reset: bfloat16 first,
+    then binary16 and tensorfloat32 together (both 10 mantissa bits), then
+    binary32; binary64 never resets before the end."""
+    apply_a, eta = _fig4_case()
+    r = {t: solvers.cgne(apply_a, eta, 1e-12, 3000, t, ncomp=1536) for t in ("fp64", "fp32", "tf32", "bf16", "fp16")}
+    assert r["fp64"].status < r["fp32"].status <= r["tf32"].status <= min(r["bf16"].status, r["fp16"].status)
+    first = {t: v.reset_at[0] for t, v in r.items()}
+    assert first["bf16"] < first["fp16"] == first["tf32"] < first["fp32"] < first["fp64"]
+    assert r["fp64"].resets == 1 and r["fp64"].reset_at == [r["fp64"].status]
+
+
+def test_fig4_unscaled_binary16_stalls():
+    """Sec. 2: cast to binary16 as it is (no per-reset scale), the residual
+    components leave binary16's range and CG stalls far above the 1e-12
+    target; with the scale the same type converges."""
+    apply_a, eta = _fig4_case()
+    r = solvers.cgne(apply_a, eta, 1e-12, 300, "fp16", ncomp=1536, scaled=False)
+    assert not r.converged and r.status == 300 and 1e-8 < r.rel_res < 1e-4
+    assert solvers.cgne(apply_a, eta, 1e-12, 300, "fp16", ncomp=1536).converged
+
+
+def test_ladder_single_type_equals_plain_cgne():
+    """A one-type ladder is the plain CGNE of that type, bit for bit; a
+    ladder whose switch values are never reached runs only its first type."""
+    apply_a, eta = _fig4_case()
+    plain = solvers.cgne(apply_a, eta, 1e-12, 3000, "bf16", ncomp=1536)
+    for lad in ([("bf16", 0.0)], [("bf16", 1e-30), ("fp32", 0.0)]):
+        r = solvers.cgne(apply_a, eta, 1e-12, 3000, ncomp=1536, ladder=lad)
+        assert np.array_equal(r.x, plain.x) and r.status == plain.status and r.resets == plain.resets
+        assert set(r.phases) == {"bf16"}
+
+
+def test_ladder_switch_rule():
+    """Precision ladder (Sec. 2, after Fig. 4): binary16 until the binary64
+    residual is below eps(binary16), binary32 until below eps(binary32), then
+    binary64.  Up to the switch the run is the plain binary16 run (same
+    history); each phase starts at the first reset that passes its switch
+    value; the ladder needs fewer regular and reset steps than binary16 alone
+    and reaches the same target."""
+    apply_a, eta = _fig4_case()
+    lad = solvers.precision_ladder(("fp16", "fp32", "fp64"))
+    assert lad == [("fp16", 2.0 ** -10), ("fp32", 2.0 ** -23), ("fp64", 0.0)]
+    r = solvers.cgne(apply_a, eta, 1e-12, 3000, ncomp=1536, ladder=lad, history=True)
+    p16 = solvers.cgne(apply_a, eta, 1e-12, 3000, "fp16", ncomp=1536, history=True)
+    assert r.converged and r.rel_res <= 1e-12
+    assert r.phases == sorted(r.phases, key=["fp16", "fp32", "fp64"].index)
+    n16 = r.phases.count("fp16")
+    assert 1 <= n16 < len(r.phases)
+    cut = r.reset_at[n16 - 1]
+    assert r.history[:cut] == p16.history[:cut]
+    # the exact residual at every reset decides the next phase
+    ex = {h[0]: h[1] for h in r.history}
+    for i, t in enumerate(r.phases[1:], start=1):
+        rel = ex[r.reset_at[i - 1]]
+        prev_sw = dict(lad)[r.phases[i - 1]]
+        assert (t != r.phases[i - 1]) == (rel <= prev_sw), (i, t, rel)
+    assert r.status < p16.status and r.resets < p16.resets
+
+
+def test_fig4_sweep_fixture_is_current():
+    """The stored sweep (written by make_fig4_sweep.py from the oracle, read by
+    the GPU parity tests) matches the oracle as it stands."""
+    rows = _read_rows("fig4_sweep_4x4x4x4.txt")
+    apply_a, eta = _fig4_case()
+    for name, kw in (("bf16", dict(store="bf16")),
+                     ("ladder_fp16_fp32_fp64", dict(ladder=solvers.precision_ladder(("fp16", "fp32", "fp64"))))):
+        r = solvers.cgne(apply_a, eta, 1e-12, 3000, ncomp=1536, **kw)
+        assert (r.status, r.resets, r.reset_at[0]) == tuple(int(v) for v in rows[name][:3])
+        assert ",".join(r.phases) == rows[name][5]
