@@ -584,32 +584,33 @@ def _timed(fn):
 def run_workload_c4(args):
     """Uneven batch (QCD+QED): U(3) links with charges 2/3 and -1/3 on 8^4,
     32x16^3 and 48x24^3 lattices; batched CGNE (tile-list launches, graph
-    replay) against the same systems solved one after the other."""
+    replay) against the same systems solved one after the other; then the
+    batch again with the clover of separate SU(3) and U(1) coefficients."""
     import torch
-    from oracle import dirac as _unused  # noqa: F401  (keeps the import layout of the other modes)
     from paper_2202_07388_gb300 import oq, synth
     from paper_2202_07388_gb300 import build as _build
     _build.build()
     lats = [(8, 8, 8, 8), (32, 16, 16, 16), (48, 24, 24, 24)]
     charges = [2.0 / 3.0, -1.0 / 3.0]
-    dims_all, links = [], []
+    dims_all, fields = [], []
     for k, dims in enumerate(lats):
         su3 = synth.make_gauge(dims, 0.5, 4 + 10 * k)
         a1 = synth.make_u1_field(dims, 0.2, 5 + 10 * k)
         for q in charges:
             dims_all.append(dims)
-            links.append(synth.apply_u1(su3, a1, q))
+            fields.append((su3, a1, q))
     h = oq.Handle(dims_all)
     etas, psis = [], []
-    for lat, (dims, u) in enumerate(zip(dims_all, links)):
-        h.gauge_upload(to_dev(u), oq.LINK_18, lat=lat)
+    for lat, (dims, (su3, a1, q)) in enumerate(zip(dims_all, fields)):
+        # U(3) links U exp(i q A) formed by the library; clover of the U(3) links
+        h.gauge_upload_qed(to_dev(su3), to_dev(np.ascontiguousarray(a1)), q, lat=lat)
         h.clover_build(KAPPA, CSW, lat=lat)
         e = synth.make_source(dims, 40 + lat)
         x = np.indices(dims).sum(axis=0) % 2 == 1
         e[x] = 0.0
         etas.append(to_dev(e))
         psis.append(torch.zeros_like(etas[-1]))
-    del links
+    del fields
     out = {"workload": "uneven batch 8^4 + 32x16^3 + 48x24^3, U(3) links, q = 2/3, -1/3 (6 systems)"}
     for pname, pc in (("f32", oq.F32), ("f16", oq.F16)):
         prm = oq.SolverParams(res=RES, nmx=20000, sdtype=pc)
@@ -624,6 +625,66 @@ def run_workload_c4(args):
         out[pname] = {"batched_s": tb, "sequential_s": ts, "speedup": ts / tb, "rc": rc,
                       "steps": [s["steps"] for s in st], "resets": [s["resets"] for s in st],
                       "max_true_rel_res": max(s["true_rel_res"] for s in st)}
+    # openQ*D's clover with separate SU(3) and U(1) coefficients (both c_sw)
+    tc, _ = _timed(lambda: [h.clover_build(KAPPA, CSW, lat=lat, csw_qed=CSW) for lat in range(len(dims_all))])
+    prm = oq.SolverParams(res=RES, nmx=20000, sdtype=oq.F16)
+    h.cgne_batch(list(range(len(dims_all))), etas, psis, prm)
+    tb, (rc, st) = _timed(lambda: h.cgne_batch(list(range(len(dims_all))), etas, psis, prm))
+    out["f16_qed_split_clover"] = {"batched_s": tb, "clover_build_s": tc, "rc": rc,
+                                   "steps": [s["steps"] for s in st], "resets": [s["resets"] for s in st],
+                                   "max_true_rel_res": max(s["true_rel_res"] for s in st)}
+    print(json.dumps(out), flush=True)
+    h.close()
+    return 0
+
+
+def run_workload_sf(args):
+    """Schroedinger-functional time boundaries (openQCD boundary type 1) on the
+    bench lattice: 64x32^3 with zero boundary fields, c_F = 1 (tree level),
+    12 point sources on the first active slice (site (1, 1, 0, 0), even),
+    eta = Dhat^dag b_e; the batched F16 CGNE to 1e-10 (double-float resets)
+    against the one-rhs binary64 CGNE, with the stencil bytes per second of
+    the batched solve."""
+    import torch
+    from paper_2202_07388_gb300 import oq, synth
+    from paper_2202_07388_gb300 import build as _build
+    _build.build()
+    h = oq.Handle(DIMS, bc_t=0)
+    ud = to_dev(synth.make_gauge_sf(DIMS, EPS, SEED))
+    h.gauge_upload(ud, oq.LINK_12)
+    h.clover_build(KAPPA, CSW, cF=1.0)
+    del ud
+    src = to_dev(synth.make_point_sources(DIMS, site=(1, 1, 0, 0)))
+    pk, pk2 = h.new_packed(oq.F64, oq.EVEN, nrhs=NRHS), h.new_packed(oq.F64, oq.EVEN, nrhs=NRHS)
+    h.pack(src, pk, oq.F64, oq.EVEN, nrhs=NRHS)
+    h.dw_hat(pk, pk2, oq.F64, nrhs=NRHS, dagger=True)
+    eta = torch.zeros_like(src)
+    h.unpack(pk2, eta, oq.F64, oq.EVEN, nrhs=NRHS)
+    del pk, pk2, src
+    for pc, nr in ((oq.F16, NRHS), (oq.F64, NRHS), (oq.DF64, NRHS), (oq.F64, 1)):
+        h.autotune(pc, nrhs=nr)
+    psi = torch.zeros_like(eta)
+    prm = oq.SolverParams(res=RES, nmx=20000, sdtype=oq.F16)
+    h.cgne(eta, psi, prm, nrhs=NRHS)  # warm-up
+    h.profile_start()
+    reps = 2
+    t, st = _timed(lambda: [h.cgne(eta, psi, prm, nrhs=NRHS) for _ in range(reps)])
+    prof = h.profile_stop()
+    st = st[-1][1]
+    byts = sum(p["bytes"] for p in prof)
+    eta1 = eta.view(NRHS, -1)[0:1].contiguous()
+    psi1 = torch.zeros_like(eta1)
+    p64 = oq.SolverParams(res=RES, nmx=50000, sdtype=oq.F64)
+    h.cgne(eta1, psi1, p64)
+    t64, (rc64, st64) = _timed(lambda: h.cgne(eta1, psi1, p64))
+    out = {"workload": "Schroedinger-functional 64x32^3 (openQCD boundary type 1), 12 point-source rhs at "
+                       "(1,1,0,0), batched F16 CGNE to 1e-10",
+           "batched_12rhs_f16_s_per_rhs": t / reps / NRHS, "stencil_gbs": byts / t / 1e9,
+           "steps": [s["steps"] for s in st], "resets": [s["resets"] for s in st],
+           "max_true_rel_res": max(s["true_rel_res"] for s in st),
+           "fp64_1rhs_s": t64, "fp64_steps": st64[0]["steps"], "fp64_true_rel_res": st64[0]["true_rel_res"],
+           "speedup_batched_f16_vs_fp64_per_rhs": t64 / (t / reps / NRHS),
+           "kernels": [{"kernel": kernel_key(p), "launches": p["launches"], "ms": p["total_ms"]} for p in prof]}
     print(json.dumps(out), flush=True)
     h.close()
     return 0
@@ -725,7 +786,7 @@ def run_workload_c5(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c4", "c5", "sf"])
     ap.add_argument("--nn-pairs", type=int, default=16)
     ap.add_argument("--nn-steps", type=int, default=100)
     ap.add_argument("--nn-lr", type=float, default=0.01)
@@ -750,6 +811,8 @@ def main():
         return run_workload_c4(args)
     if args.workload == "c5":
         return run_workload_c5(args)
+    if args.workload == "sf":
+        return run_workload_sf(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

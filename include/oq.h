@@ -80,7 +80,9 @@ enum {
 
 typedef struct {
   int L[4];  /* L[0] = T, all extents even and >= 2 */
-  int bc_t;  /* fermion factor across the time boundary: -1 antiperiodic, +1 periodic */
+  int bc_t;  /* time boundary: -1 antiperiodic, +1 periodic (the fermion factor of a hop
+                across x0 = T-1 <-> 0), or 0 = Schroedinger functional (openQCD boundary
+                type 1, Sec. 2 footnote): quark fields vanish at x0 = 0 and x0 = T */
 } oq_lattice;
 
 /* Solver settings, after Table 2 of the paper (res, nmx, nkv, ncy, nmr, bs)
@@ -124,7 +126,7 @@ typedef struct {
 
 /* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no
  * device: the current CUDA device at creation is used for every call.
- * Every extent must be even and >= 2, bc_t +1 or -1, and the volume at most
+ * Every extent must be even and >= 2, bc_t +1, -1 or 0, and the volume at most
  * 2^29 sites (half volume <= 2^28, so site offsets fit 32-bit arithmetic);
  * otherwise OQ_ERR_ARG. */
 int oq_create(oq_handle* h, const oq_lattice* lats, int nlat);
@@ -141,10 +143,44 @@ size_t oq_spinor_bytes(oq_handle h, int lat, int prec, int subset);
  * (QCD+QED with O(a)-improved Wilson fermions). */
 int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int link_fmt, void* stream);
 
+/* QCD+QED upload (Sec. 1; openQ*D): U_dev the SU(3) links (canonical), A_dev
+ * the U(1) potential A_mu(x) (canonical: site-lexicographic, then mu; 4 V
+ * binary64 values, device memory) and q the charge.  The hopping term uses
+ * the U(3) links U_mu(x) exp(i q A_mu(x)) (18-real binary32 copy); the SU(3)
+ * links and the angles are kept for oq_clover_build_ex. */
+int oq_gauge_upload_qed(oq_handle h, int lat, const double* U_dev, const double* A_dev, double q,
+                        void* stream);
+
+/* Schroedinger-functional lattices (bc_t = 0): the hopping copies of the
+ * time-like links of slices x0 = 0 and x0 = T-1 are zero (no hop reaches
+ * the x0 = 0 slice), the clover is built from the links as uploaded (the
+ * spatial links of slice 0 are the boundary field at x0 = 0 and, by
+ * periodicity, at x0 = T), and oq_spinor_pack sets the x0 = 0 slice to zero.
+ * Every operator and solver then maps fields that vanish at x0 = 0 to fields
+ * that vanish there, as the quark fields of openQCD boundary type 1. */
+
 /* Clover term A(x) and A^{-1}(x) (odd sites) from the uploaded links:
  * clover-leaf field strength, two Hermitian 6x6 chiral blocks per site,
- * built and inverted in binary64, stored in binary64 and binary32. */
+ * built and inverted in binary64, stored in binary64 and binary32.
+ * A(x) = 4 + m0 + c_sw (i/4) sum sigma_{mu nu} F_{mu nu}(x), m0 = 1/(2 kappa) - 4;
+ * after oq_gauge_upload_qed, F is that of the U(3) links.  Singular block:
+ * OQ_ERR_NONFINITE. */
 int oq_clover_build(oq_handle h, int lat, double kappa, double csw, void* stream);
+
+typedef struct {
+  double kappa;    /* hopping parameter, 4 + m0 = 1/(2 kappa) */
+  double csw;      /* coefficient of the SU(3) (or, without qed_split, U(3)) field strength */
+  double cF;       /* Schroedinger-functional boundary coefficient: 4 + m0 + cF - 1 at
+                      x0 = 1 and x0 = T-1 (bc_t = 0 lattices; 1 = none; ignored otherwise) */
+  double csw_qed;  /* qed_split: coefficient of the U(1) field strength of exp(i q A) */
+  int qed_split;   /* 1: c_sw F^{SU(3)} + c_sw^QED F^{U(1)} 1_colour (needs oq_gauge_upload_qed);
+                      0: c_sw F of the hopping links (U(3) after oq_gauge_upload_qed) */
+} oq_clover_params;
+
+/* oq_clover_build with the boundary coefficient c_F of Schroedinger-functional
+ * lattices and the separate QED clover coefficient of openQ*D.  qed_split
+ * without oq_gauge_upload_qed: OQ_ERR_STATE. */
+int oq_clover_build_ex(oq_handle h, int lat, const oq_clover_params* p, void* stream);
 
 /* Convert canonical binary64 spinors (device) to packed `prec` fields and
  * back.  pack multiplies by `scale` before rounding (round to nearest even),

@@ -56,6 +56,13 @@ __all__ = [
     "assemble_dense",
     "dw_site",
     "apply_gamma5",
+    "sf_project",
+    "clover_field_sf",
+    "dw_sf",
+    "dw_sf_dagger",
+    "dw_hat_sf",
+    "dw_hat_sf_dagger",
+    "clover_field_qed",
 ]
 
 
@@ -325,3 +332,87 @@ def dw_site(u, a, psi, x, bc_t=-1.0) -> np.ndarray:
         ub = u[tuple(xb) + (mu,)]
         out = out - 0.5 * (pf @ uf.T + pb @ np.conj(ub))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Schroedinger-functional time boundaries (openQCD boundary type 1, the
+# boundary conditions of the 4^4 matrix of Fig. 4, Sec. 2 footnote)
+# ---------------------------------------------------------------------------
+#
+# The stored time slices are x0 = 0 .. T-1.  Quark fields live on the active
+# slices 1 <= x0 <= T-1 and vanish at x0 = 0 and x0 = T; the operator maps
+# active fields to active fields.  The gauge links at the boundaries (the
+# spatial links of slice 0, which by periodicity also stand for those of
+# slice T) enter only through the clover leaves of slices 1 and T-1.  The
+# boundary-improvement term adds (c_F - 1) to the diagonal at x0 = 1 and
+# x0 = T-1.
+
+def sf_project(psi: np.ndarray) -> np.ndarray:
+    """Set the x0 = 0 slice to zero (the field there vanishes)."""
+    out = psi.copy()
+    out[0] = 0.0
+    return out
+
+
+def clover_field_sf(u: np.ndarray, m0: float, csw: float, cf: float) -> np.ndarray:
+    """The clover field plus the boundary term (c_F - 1) at x0 = 1, T-1."""
+    a = clover_field(u, m0, csw)
+    t = u.shape[0]
+    for x0 in {1, t - 1}:
+        a[x0] += (cf - 1.0) * np.eye(12)
+    return a
+
+
+def dw_sf(u, a, psi):
+    """D psi for Schroedinger-functional boundaries: the fields at x0 = 0 and
+    x0 = T are zero (input and output), so no hop crosses x0 = 0 <-> T-1 and
+    the output at x0 = 0 is zero.  ``a`` from ``clover_field_sf``."""
+    return sf_project(dw(u, a, sf_project(psi), bc_t=0.0))
+
+
+def dw_sf_dagger(u, a, psi):
+    return apply_gamma5(dw_sf(u, a, apply_gamma5(psi)))
+
+
+def dw_hat_sf(u, a, ainv, psi_e):
+    """The even-odd Schur complement of ``dw_sf`` on the active even sites:
+    A_ee psi_e - D_eo A_oo^{-1} D_oe psi_e with every intermediate field
+    vanishing at x0 = 0."""
+    psi_e = sf_project(even_part(psi_e))
+    t_o = sf_project(odd_part(_hop_term(u, psi_e, 0.0)))
+    t_o = odd_part(apply_site_matrix(ainv, t_o))
+    s_e = even_part(_hop_term(u, t_o, 0.0))
+    return sf_project(even_part(apply_site_matrix(a, psi_e)) - s_e)
+
+
+def dw_hat_sf_dagger(u, a, ainv, psi_e):
+    return apply_gamma5(dw_hat_sf(u, a, ainv, apply_gamma5(psi_e)))
+
+
+# ---------------------------------------------------------------------------
+# QCD+QED clover term with separate coefficients (openQ*D, Sec. 1)
+# ---------------------------------------------------------------------------
+
+def clover_field_qed(u_su3, a_u1, q, m0, csw, csw_qed):
+    """A(x) = (4 + m0) + (i/4) sum_{mu != nu} sigma_{mu nu}
+                 [c_sw F^{SU(3)}_{mu nu}(x) + c_sw^{QED} F^{U(1)}_{mu nu}(x) 1_colour]
+
+    F^{SU(3)} is the clover-leaf field strength of the SU(3) links,
+    F^{U(1)} that of the charged U(1) links exp(i q A_mu(x)) (the same
+    clover-leaf formula applied to the phases).  The hopping term uses the
+    product links U_mu(x) exp(i q A_mu(x)).
+    """
+    dims = u_su3.shape[:4]
+    z = np.exp(1j * q * np.asarray(a_u1))[..., None, None] * np.eye(3)
+    f3 = field_strength(u_su3)
+    f1 = field_strength(z)
+    a = np.zeros(dims + (12, 12), dtype=np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            s = sigma_munu(mu, nu)
+            f = csw * f3[(mu, nu)] + csw_qed * f1[(mu, nu)]
+            a += 0.25j * np.einsum("st,...ab->...satb", s, f).reshape(dims + (12, 12))
+    a += (4.0 + m0) * np.eye(12)
+    return a

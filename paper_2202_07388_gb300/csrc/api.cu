@@ -56,7 +56,7 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
   for (int k = 0; k < nlat; ++k) {
     for (int mu = 0; mu < 4; ++mu)
       if (lats[k].L[mu] < 2 || (lats[k].L[mu] & 1)) return OQ_ERR_ARG;
-    if (lats[k].bc_t != 1 && lats[k].bc_t != -1) return OQ_ERR_ARG;
+    if (lats[k].bc_t != 1 && lats[k].bc_t != -1 && lats[k].bc_t != 0) return OQ_ERR_ARG;
     const double v = (double)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3];
     if (v > (double)(1L << 29)) return OQ_ERR_ARG;  // Vh <= 2^28: 32-bit site offsets
   }
@@ -93,10 +93,14 @@ extern "C" size_t oq_spinor_bytes(oq_handle h, int lat, int prec, int subset) {
   return subset == OQ_FULL ? 2 * half : half;
 }
 
-extern "C" int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int link_fmt, void* stream) {
+// shared by oq_gauge_upload and oq_gauge_upload_qed (A_dev != nullptr)
+static int gauge_upload(oq_handle h, int lat, const double* U_dev, const double* A_dev, double q, int link_fmt,
+                        void* stream) {
   if (!h || !U_dev || lat < 0 || lat >= (int)h->lats.size()) return OQ_ERR_ARG;
   if (link_fmt != OQ_LINK_18 && link_fmt != OQ_LINK_12) return OQ_ERR_ARG;
+  if (A_dev && (link_fmt != OQ_LINK_18 || !isfinite(q))) return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
+  const bool sf = L.g.bc_t == 0.f;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n64 = sizeof(double) * 2 * 4 * 18 * L.g.Vh;
   const size_t n32 = sizeof(float) * 2 * 4 * (link_fmt == OQ_LINK_12 ? 12 : 18) * L.g.Vh;
@@ -110,20 +114,60 @@ extern "C" int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int li
     rc = h->alloc(&L.u32_18, sizeof(float) * 2 * 4 * 18 * L.g.Vh);
     if (rc) return rc;
   }
+  // the clover's own copy of the links: unmasked (SF) or without the phase (QED)
+  if (sf || A_dev) {
+    rc = h->alloc(&L.uclov, n64);
+    if (rc) return rc;
+  }
+  if (A_dev) {
+    rc = h->alloc(&L.au1, sizeof(double) * 2 * 4 * L.g.Vh);
+    if (rc) return rc;
+  }
   L.link_fmt = link_fmt;
-  if (pack_links(L.g, U_dev, (double*)L.u64.p, L.u32.p, link_fmt, link_fmt == OQ_LINK_12 ? L.u32_18.p : nullptr,
+  void* u18 = link_fmt == OQ_LINK_12 ? L.u32_18.p : nullptr;
+  if (pack_links(L.g, U_dev, (double*)L.u64.p, L.u32.p, link_fmt, u18, A_dev, q,
+                 (sf || A_dev) ? (double*)L.uclov.p : nullptr, A_dev ? (double*)L.au1.p : nullptr,
                  s) != cudaSuccess)
     return OQ_ERR_CUDA;
+  if (sf && sf_mask_links(L.g, (double*)L.u64.p, L.u32.p, link_fmt, u18, s) != cudaSuccess) return OQ_ERR_CUDA;
+  L.uclov_valid = sf || A_dev;
+  L.has_u1 = A_dev != nullptr;
+  L.qcharge = A_dev ? q : 0.0;
   L.has_gauge = true;
   L.has_clover = false;
   L.df_ready = false;
   return OQ_OK;
 }
 
+extern "C" int oq_gauge_upload(oq_handle h, int lat, const double* U_dev, int link_fmt, void* stream) {
+  return gauge_upload(h, lat, U_dev, nullptr, 0.0, link_fmt, stream);
+}
+
+extern "C" int oq_gauge_upload_qed(oq_handle h, int lat, const double* U_dev, const double* A_dev, double q,
+                                   void* stream) {
+  if (!A_dev) return OQ_ERR_ARG;
+  return gauge_upload(h, lat, U_dev, A_dev, q, OQ_LINK_18, stream);
+}
+
 extern "C" int oq_clover_build(oq_handle h, int lat, double kappa, double csw, void* stream) {
-  if (!h || lat < 0 || lat >= (int)h->lats.size() || !(kappa > 0.0) || !isfinite(csw)) return OQ_ERR_ARG;
+  oq_clover_params p;
+  p.kappa = kappa;
+  p.csw = csw;
+  p.cF = 1.0;
+  p.csw_qed = 0.0;
+  p.qed_split = 0;
+  return oq_clover_build_ex(h, lat, &p, stream);
+}
+
+extern "C" int oq_clover_build_ex(oq_handle h, int lat, const oq_clover_params* prm, void* stream) {
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm) return OQ_ERR_ARG;
+  const double kappa = prm->kappa, csw = prm->csw;
+  if (!(kappa > 0.0) || !isfinite(csw) || !isfinite(prm->cF) || !isfinite(prm->csw_qed) ||
+      (prm->qed_split != 0 && prm->qed_split != 1))
+    return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_gauge) return OQ_ERR_STATE;
+  if (prm->qed_split && !L.has_u1) return OQ_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n64 = sizeof(double) * 2 * 72 * L.g.Vh, n32 = sizeof(float) * 2 * 72 * L.g.Vh;
   int rc = h->alloc(&L.a64, n64);
@@ -133,8 +177,10 @@ extern "C" int oq_clover_build(oq_handle h, int lat, double kappa, double csw, v
   if (!rc) rc = h->ensure_scratch();
   if (rc) return rc;
   if (cudaMemsetAsync(h->status_dev, 0, sizeof(int), s) != cudaSuccess) return OQ_ERR_CUDA;
-  if (build_clover(L.g, (const double*)L.u64.p, kappa, csw, (double*)L.a64.p, (float*)L.a32.p, (double*)L.i64.p,
-                   (float*)L.i32.p, h->status_dev, s) != cudaSuccess)
+  const double* links = L.uclov_valid ? (const double*)L.uclov.p : (const double*)L.u64.p;
+  if (build_clover(L.g, links, L.has_u1 ? (const double*)L.au1.p : nullptr, L.qcharge, prm->qed_split, kappa, csw,
+                   prm->csw_qed, prm->cF, (double*)L.a64.p, (float*)L.a32.p, (double*)L.i64.p, (float*)L.i32.p,
+                   h->status_dev, s) != cudaSuccess)
     return OQ_ERR_CUDA;
   int st = 0;
   if (cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return OQ_ERR_CUDA;
@@ -142,6 +188,8 @@ extern "C" int oq_clover_build(oq_handle h, int lat, double kappa, double csw, v
   if (st) return OQ_ERR_NONFINITE;  // a singular clover block
   L.kappa = kappa;
   L.csw = csw;
+  L.cF = prm->cF;
+  L.csw_qed = prm->qed_split ? prm->csw_qed : 0.0;
   L.has_clover = true;
   L.df_ready = false;
   return OQ_OK;

@@ -1,4 +1,7 @@
 // Clover term: A(x) = (4 + m0) + c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x)
+// (QCD+QED with separate coefficients: c_sw F -> c_sw F^{SU(3)} + c_sw^QED
+// F^{U(1)} 1_colour; Schroedinger-functional lattices: 4 + m0 + c_F - 1 at
+// x0 = 1 and T-1)
 // with the clover-leaf field strength F = (Q - Q^dag)/8, Q the sum of the four
 // plaquettes at x in the (mu, nu) plane.  In the chiral basis
 // sigma_{0k} = diag(s_k, -s_k) and sigma_{jk} = -eps_{jkl} diag(s_l, s_l), so A
@@ -62,8 +65,9 @@ __device__ __forceinline__ M3 dmul(const M3& a, const M3& b) {
   return c;
 }
 
+// the link U_mu(y), y = x + d1 mu1 + d2 mu2; with au1 times exp(i q A_mu(y))
 __device__ __forceinline__ M3 link_at(const Geom& g, const double2* u64, const int x[4], int mu, int d1, int mu1,
-                                      int d2, int mu2) {
+                                      int d2, int mu2, const double* au1 = nullptr, double q = 0.0) {
   int y[4] = {x[0], x[1], x[2], x[3]};
   if (d1) y[mu1] = (y[mu1] + d1 + g.L[mu1]) % g.L[mu1];
   if (d2) y[mu2] = (y[mu2] + d2 + g.L[mu2]) % g.L[mu2];
@@ -71,28 +75,35 @@ __device__ __forceinline__ M3 link_at(const Geom& g, const double2* u64, const i
   const long j = eo_index(g, y);
   Su3<double> u;
   load_link<double, LINK_18>(u64, g.Vh, p, mu, j, u);
+  cd ph = cd{1.0, 0.0};
+  if (au1) {
+    double sn, cs;
+    sincos(q * au1[(long)(p * 4 + mu) * g.Vh + j], &sn, &cs);
+    ph = cd{cs, sn};
+  }
   M3 r;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) r.m[a][b] = u.m[a][b];
+    for (int b = 0; b < 3; ++b) r.m[a][b] = au1 ? u.m[a][b] * ph : u.m[a][b];
   return r;
 }
 
-// F_{mu nu}(x) = (Q - Q^dag) / 8
-__device__ M3 field_strength(const Geom& g, const double2* u64, const int x[4], int mu, int nu) {
-  M3 umx = link_at(g, u64, x, mu, 0, 0, 0, 0);
-  M3 unx = link_at(g, u64, x, nu, 0, 0, 0, 0);
-  M3 un_xpm = link_at(g, u64, x, nu, +1, mu, 0, 0);
-  M3 um_xpn = link_at(g, u64, x, mu, +1, nu, 0, 0);
-  M3 um_xmm = link_at(g, u64, x, mu, -1, mu, 0, 0);
-  M3 un_xmm = link_at(g, u64, x, nu, -1, mu, 0, 0);
-  M3 um_xmm_pn = link_at(g, u64, x, mu, -1, mu, +1, nu);
-  M3 um_xmn = link_at(g, u64, x, mu, -1, nu, 0, 0);
-  M3 un_xmn = link_at(g, u64, x, nu, -1, nu, 0, 0);
-  M3 um_xmm_mn = link_at(g, u64, x, mu, -1, mu, -1, nu);
-  M3 un_xmm_mn = link_at(g, u64, x, nu, -1, mu, -1, nu);
-  M3 un_xpm_mn = link_at(g, u64, x, nu, +1, mu, -1, nu);
+// F_{mu nu}(x) = (Q - Q^dag) / 8 (au1: of the links times exp(i q A))
+__device__ M3 field_strength(const Geom& g, const double2* u64, const int x[4], int mu, int nu,
+                             const double* au1 = nullptr, double qc = 0.0) {
+  M3 umx = link_at(g, u64, x, mu, 0, 0, 0, 0, au1, qc);
+  M3 unx = link_at(g, u64, x, nu, 0, 0, 0, 0, au1, qc);
+  M3 un_xpm = link_at(g, u64, x, nu, +1, mu, 0, 0, au1, qc);
+  M3 um_xpn = link_at(g, u64, x, mu, +1, nu, 0, 0, au1, qc);
+  M3 um_xmm = link_at(g, u64, x, mu, -1, mu, 0, 0, au1, qc);
+  M3 un_xmm = link_at(g, u64, x, nu, -1, mu, 0, 0, au1, qc);
+  M3 um_xmm_pn = link_at(g, u64, x, mu, -1, mu, +1, nu, au1, qc);
+  M3 um_xmn = link_at(g, u64, x, mu, -1, nu, 0, 0, au1, qc);
+  M3 un_xmn = link_at(g, u64, x, nu, -1, nu, 0, 0, au1, qc);
+  M3 um_xmm_mn = link_at(g, u64, x, mu, -1, mu, -1, nu, au1, qc);
+  M3 un_xmm_mn = link_at(g, u64, x, nu, -1, mu, -1, nu, au1, qc);
+  M3 un_xpm_mn = link_at(g, u64, x, nu, +1, mu, -1, nu, au1, qc);
   // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
   M3 q = mul_d(mul_d(mul(umx, un_xpm), um_xpn), unx);
   // leaf 2: U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
@@ -111,6 +122,32 @@ __device__ M3 field_strength(const Geom& g, const double2* u64, const int x[4], 
 #pragma unroll
     for (int b = 0; b < 3; ++b) f.m[a][b] = 0.125 * (q.m[a][b] - conj(q.m[b][a]));
   return f;
+}
+
+// U(1) angle A_mu(y) at y = x + d1 mu1 + d2 mu2 (packed [parity][mu][site])
+__device__ __forceinline__ double angle_at(const Geom& g, const double* au1, const int x[4], int mu, int d1,
+                                           int mu1, int d2, int mu2) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  if (d1) y[mu1] = (y[mu1] + d1 + g.L[mu1]) % g.L[mu1];
+  if (d2) y[mu2] = (y[mu2] + d2 + g.L[mu2]) % g.L[mu2];
+  const int p = (y[0] + y[1] + y[2] + y[3]) & 1;
+  return au1[(long)(p * 4 + mu) * g.Vh + eo_index(g, y)];
+}
+
+// U(1) clover-leaf field strength of the charged links exp(i q A):
+// F = (Q - Q^*) / 8 = (i/4) sum over the four leaves of sin(q theta_leaf),
+// theta_leaf the oriented sum of the angles around the leaf (the same four
+// leaves as field_strength); returns f with F = i f
+__device__ double u1_field_strength(const Geom& g, const double* au1, double q, const int x[4], int mu, int nu) {
+  const double t1 = angle_at(g, au1, x, mu, 0, 0, 0, 0) + angle_at(g, au1, x, nu, +1, mu, 0, 0) -
+                    angle_at(g, au1, x, mu, +1, nu, 0, 0) - angle_at(g, au1, x, nu, 0, 0, 0, 0);
+  const double t2 = angle_at(g, au1, x, nu, 0, 0, 0, 0) - angle_at(g, au1, x, mu, -1, mu, +1, nu) -
+                    angle_at(g, au1, x, nu, -1, mu, 0, 0) + angle_at(g, au1, x, mu, -1, mu, 0, 0);
+  const double t3 = -angle_at(g, au1, x, mu, -1, mu, 0, 0) - angle_at(g, au1, x, nu, -1, mu, -1, nu) +
+                    angle_at(g, au1, x, mu, -1, mu, -1, nu) + angle_at(g, au1, x, nu, -1, nu, 0, 0);
+  const double t4 = -angle_at(g, au1, x, nu, -1, nu, 0, 0) + angle_at(g, au1, x, mu, -1, nu, 0, 0) +
+                    angle_at(g, au1, x, nu, +1, mu, -1, nu) - angle_at(g, au1, x, mu, 0, 0, 0, 0);
+  return 0.25 * (sin(q * t1) + sin(q * t2) + sin(q * t3) + sin(q * t4));
 }
 
 // invert a general 6x6 complex matrix in place (Gauss-Jordan, partial pivoting)
@@ -178,21 +215,50 @@ __device__ __forceinline__ void store_block(const Geom& g, int p, long i, int b,
         make_float4((float)r[4 * c], (float)r[4 * c + 1], (float)r[4 * c + 2], (float)r[4 * c + 3]);
 }
 
-__global__ void __launch_bounds__(128) clover_kernel(Geom g, const double2* __restrict__ u64, double c0, double csw,
-                                                     double2* a64, float4* a32, double2* i64, float4* i32,
-                                                     int* status) {
+// qed: 0 = F of the links alone; 1 = F of the links times exp(i q A) (the
+// U(3) clover); 2 = csw F(links) + csw_qed F(exp(i q A)) 1_colour
+__global__ void __launch_bounds__(128) clover_kernel(Geom g, const double2* __restrict__ u64,
+                                                     const double* __restrict__ au1, double q, int qed, double c0,
+                                                     double csw, double csw_qed, double cF, double2* a64,
+                                                     float4* a32, double2* i64, float4* i32, int* status) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (i >= g.Vh) return;
   int x[4];
   eo_coords(g, p, i, x);
-  M3 f01 = field_strength(g, u64, x, 0, 1);
-  M3 f02 = field_strength(g, u64, x, 0, 2);
-  M3 f03 = field_strength(g, u64, x, 0, 3);
-  M3 f12 = field_strength(g, u64, x, 1, 2);
-  M3 f13 = field_strength(g, u64, x, 1, 3);
-  M3 f23 = field_strength(g, u64, x, 2, 3);
-  const double h = 0.5 * csw;
+  const double* ph = qed == 1 ? au1 : nullptr;
+  M3 f01 = field_strength(g, u64, x, 0, 1, ph, q);
+  M3 f02 = field_strength(g, u64, x, 0, 2, ph, q);
+  M3 f03 = field_strength(g, u64, x, 0, 3, ph, q);
+  M3 f12 = field_strength(g, u64, x, 1, 2, ph, q);
+  M3 f13 = field_strength(g, u64, x, 1, 3, ph, q);
+  M3 f23 = field_strength(g, u64, x, 2, 3, ph, q);
+  // scale by c_sw here, so that a separate U(1) term adds with its own coefficient
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      f01.m[a][c] = csw * f01.m[a][c]; f02.m[a][c] = csw * f02.m[a][c]; f03.m[a][c] = csw * f03.m[a][c];
+      f12.m[a][c] = csw * f12.m[a][c]; f13.m[a][c] = csw * f13.m[a][c]; f23.m[a][c] = csw * f23.m[a][c];
+    }
+  if (qed == 2) {
+    // U(1) field strength i f (x) 1_colour, weighted by c_sw^QED
+    const double e01 = csw_qed * u1_field_strength(g, au1, q, x, 0, 1);
+    const double e02 = csw_qed * u1_field_strength(g, au1, q, x, 0, 2);
+    const double e03 = csw_qed * u1_field_strength(g, au1, q, x, 0, 3);
+    const double e12 = csw_qed * u1_field_strength(g, au1, q, x, 1, 2);
+    const double e13 = csw_qed * u1_field_strength(g, au1, q, x, 1, 3);
+    const double e23 = csw_qed * u1_field_strength(g, au1, q, x, 2, 3);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      f01.m[a][a] = f01.m[a][a] + cd{0.0, e01}; f02.m[a][a] = f02.m[a][a] + cd{0.0, e02};
+      f03.m[a][a] = f03.m[a][a] + cd{0.0, e03}; f12.m[a][a] = f12.m[a][a] + cd{0.0, e12};
+      f13.m[a][a] = f13.m[a][a] + cd{0.0, e13}; f23.m[a][a] = f23.m[a][a] + cd{0.0, e23};
+    }
+  }
+  // Schroedinger-functional boundary improvement: + (c_F - 1) at x0 = 1, T-1
+  if (g.bc_t == 0.f && (x[0] == 1 || x[0] == g.L[0] - 1)) c0 += cF - 1.0;
+  const double h = 0.5;
   for (int b = 0; b < 2; ++b) {
     // X_k = (i c_sw/2) G_k, G_k = F_0k - Fd_k (b = 0) or -(F_0k + Fd_k) (b = 1)
     cd X[3][3][3];
@@ -229,11 +295,13 @@ __global__ void __launch_bounds__(128) clover_kernel(Geom g, const double2* __re
   }
 }
 
-cudaError_t build_clover(const Geom& g, const double* u64, double kappa, double csw, double* a64, float* a32,
+cudaError_t build_clover(const Geom& g, const double* links, const double* au1, double q, int qed_split,
+                         double kappa, double csw, double csw_qed, double cF, double* a64, float* a32,
                          double* i64, float* i32, int* status_dev, cudaStream_t s) {
   const double c0 = 1.0 / (2.0 * kappa);
+  const int qed = au1 ? (qed_split ? 2 : 1) : 0;
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), 2);
-  clover_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<const double2*>(u64), c0, csw,
+  clover_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<const double2*>(links), au1, q, qed, c0, csw, csw_qed, cF,
                                        reinterpret_cast<double2*>(a64), reinterpret_cast<float4*>(a32),
                                        reinterpret_cast<double2*>(i64), reinterpret_cast<float4*>(i32), status_dev);
   return cudaGetLastError();

@@ -32,6 +32,12 @@ struct LatCtx {
   // clover, made on the first DF64 use after an upload / clover build
   DevBuf udf, adf, idf;
   bool df_ready = false;
+  // Schroedinger-functional lattices (bc_t = 0) and QCD+QED uploads keep the
+  // unmasked binary64 links the clover is built from (SU(3) part for QCD+QED)
+  // and the packed U(1) angles with their charge
+  DevBuf uclov, au1;
+  bool uclov_valid = false, has_u1 = false;
+  double qcharge = 0.0, cF = 1.0, csw_qed = 0.0;
   std::map<std::string, DevBuf> ws;
 };
 
@@ -335,7 +341,7 @@ struct oq_ctx {
 
   void release() {
     for (auto& L : lats) {
-      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18, &L.udf, &L.adf, &L.idf};
+      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18, &L.udf, &L.adf, &L.idf, &L.uclov, &L.au1};
       for (auto* b : bs) cudaFree(b->p);
       for (auto& kv : L.ws) cudaFree(kv.second.p);
     }

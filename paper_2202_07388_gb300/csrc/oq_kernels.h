@@ -6,15 +6,27 @@ struct oq_ctx;
 
 namespace oq {
 
+// A (optional): canonical U(1) angles A_mu(x) multiplied into the links as
+// exp(i q A); uclov (optional): the packed binary64 links before the phase;
+// au1 (optional): the packed angles
 cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, void* u18,
-                       cudaStream_t s);
+                       const double* A, double q, double* uclov, double* au1, cudaStream_t s);
+// Schroedinger-functional boundaries: zero the time-like links of slices
+// x0 = 0 and x0 = T-1 in every hopping copy
+cudaError_t sf_mask_links(const Geom& g, double* u64, void* u32, int fmt, void* u18, cudaStream_t s);
 cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
                         int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s);
 cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
                           int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s);
 // binary64 array of n values -> n double-float (hi, lo) pairs
 cudaError_t split_f64(const double* in, void* out, size_t n, cudaStream_t s);
-cudaError_t build_clover(const Geom& g, const double* u64, double kappa, double csw, double* a64, float* a32,
+// links: packed binary64 links of the field strength; au1 (optional):
+// packed U(1) angles with charge q, used as separate U(1) field strength
+// with coefficient csw_qed (qed_split) or multiplied into the links
+// (the U(3) clover); cF: Schroedinger-functional boundary coefficient
+// (bc_t = 0 lattices)
+cudaError_t build_clover(const Geom& g, const double* links, const double* au1, double q, int qed_split,
+                         double kappa, double csw, double csw_qed, double cF, double* a64, float* a32,
                          double* i64, float* i32, int* status_dev, cudaStream_t s);
 
 // binary64 reductions over packed half fields of Vh sites per rhs

@@ -12,9 +12,13 @@ __device__ __forceinline__ long lex_of(const Geom& g, const int x[4]) {
 }
 
 // one thread per (eo site, parity, mu); u18 (optional) receives an 18-real
-// binary32 copy next to a 12-real one
+// binary32 copy next to a 12-real one; A (optional) multiplies the link by
+// exp(i q A_mu(x)) (QCD+QED), uclov / au1 (optional) keep the link before
+// the phase and the angle
 __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, double2* __restrict__ u64,
-                                  void* __restrict__ u32, int fmt, float2* __restrict__ u18) {
+                                  void* __restrict__ u32, int fmt, float2* __restrict__ u18,
+                                  const double* __restrict__ A, double q, double2* __restrict__ uclov,
+                                  double* __restrict__ au1) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   const int mu = blockIdx.z;
@@ -25,6 +29,19 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, dou
   double2 m[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) m[k] = src[k];
+  if (uclov) {
+    double2* d = uclov + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k * g.Vh + i] = m[k];
+  }
+  if (A) {
+    const double a = A[lex_of(g, x) * 4 + mu];
+    double sn, cs;
+    sincos(q * a, &sn, &cs);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = make_double2(m[k].x * cs - m[k].y * sn, m[k].x * sn + m[k].y * cs);
+    au1[(long)(p * 4 + mu) * g.Vh + i] = a;
+  }
   double2* d64 = u64 + ((long)(p * 4 + mu) * 9) * g.Vh;
 #pragma unroll
   for (int k = 0; k < 9; ++k) d64[k * g.Vh + i] = m[k];
@@ -46,11 +63,51 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, dou
 }
 
 cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, void* u18,
-                       cudaStream_t s) {
+                       const double* A, double q, double* uclov, double* au1, cudaStream_t s) {
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), 2, 4);
   pack_links_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<const double2*>(canon),
                                            reinterpret_cast<double2*>(u64), u32, fmt,
-                                           reinterpret_cast<float2*>(u18));
+                                           reinterpret_cast<float2*>(u18), A, q,
+                                           reinterpret_cast<double2*>(uclov), au1);
+  return cudaGetLastError();
+}
+
+// one thread per (eo site, parity): the time-like link U_0(x) of the slices
+// x0 = 0 (hops 0 <-> 1) and x0 = T-1 (hops T-1 <-> T, i.e. across the
+// boundary) becomes zero in every hopping copy, so that no hop reaches the
+// x0 = 0 slice, where Schroedinger-functional quark fields vanish
+__global__ void sf_mask_links_kernel(Geom g, double2* __restrict__ u64, void* __restrict__ u32, int fmt,
+                                     float2* __restrict__ u18) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (i >= g.Vh) return;
+  int x[4];
+  eo_coords(g, p, i, x);
+  if (x[0] != 0 && x[0] != g.L[0] - 1) return;
+  const int mu = 0;
+  double2* d64 = u64 + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d64[k * g.Vh + i] = make_double2(0.0, 0.0);
+  if (fmt == LINK_18) {
+    float2* d = reinterpret_cast<float2*>(u32) + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k * g.Vh + i] = make_float2(0.f, 0.f);
+  } else {
+    float4* d = reinterpret_cast<float4*>(u32) + ((long)(p * 4 + mu) * 3) * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k * g.Vh + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (u18) {
+    float2* e = u18 + ((long)(p * 4 + mu) * 9) * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) e[k * g.Vh + i] = make_float2(0.f, 0.f);
+  }
+}
+
+cudaError_t sf_mask_links(const Geom& g, double* u64, void* u32, int fmt, void* u18, cudaStream_t s) {
+  dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), 2);
+  sf_mask_links_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<double2*>(u64), u32, fmt,
+                                              reinterpret_cast<float2*>(u18));
   return cudaGetLastError();
 }
 
@@ -67,6 +124,8 @@ __global__ void pack_spinor_kernel(Geom g, const double2* __restrict__ canon, ch
   int x[4];
   eo_coords(g, p, i, x);
   const double2* src = canon + rhs * canon_stride + lex_of(g, x) * 12;
+  // Schroedinger-functional lattices: the field vanishes at x0 = 0
+  if (g.bc_t == 0.f && x[0] == 0) scale = 0.0;
   Spinor<R> s;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {

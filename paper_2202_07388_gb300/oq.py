@@ -41,6 +41,11 @@ class OqSolverParams(C.Structure):
     ]
 
 
+class OqCloverParams(C.Structure):
+    _fields_ = [("kappa", C.c_double), ("csw", C.c_double), ("cF", C.c_double), ("csw_qed", C.c_double),
+                ("qed_split", C.c_int)]
+
+
 class OqStatus(C.Structure):
     _fields_ = [("steps", C.c_int), ("resets", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("true_rel_res", C.c_double), ("cycles", C.c_int), ("mr_avg", C.c_double),
@@ -63,6 +68,8 @@ _SIGS = {
     "oq_spinor_bytes": (C.c_size_t, [_P, C.c_int, C.c_int, C.c_int]),
     "oq_gauge_upload": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),
     "oq_clover_build": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _P]),
+    "oq_gauge_upload_qed": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, _P]),
+    "oq_clover_build_ex": (C.c_int, [_P, C.c_int, C.POINTER(OqCloverParams), _P]),
     "oq_spinor_pack": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
     "oq_spinor_unpack": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
     "oq_dw_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P]),
@@ -217,8 +224,20 @@ class Handle:
     def gauge_upload(self, u_dev, link_fmt=LINK_12, lat=0, stream=None):
         _check(lib().oq_gauge_upload(self.h, lat, _ptr(u_dev), link_fmt, _stream(stream)), "oq_gauge_upload")
 
-    def clover_build(self, kappa, csw, lat=0, stream=None):
-        _check(lib().oq_clover_build(self.h, lat, kappa, csw, _stream(stream)), "oq_clover_build")
+    def gauge_upload_qed(self, u_dev, a_dev, q, lat=0, stream=None):
+        """SU(3) links and U(1) potential A_mu(x) with charge q (U(3) hopping links)."""
+        _check(lib().oq_gauge_upload_qed(self.h, lat, _ptr(u_dev), _ptr(a_dev), q, _stream(stream)),
+               "oq_gauge_upload_qed")
+
+    def clover_build(self, kappa, csw, lat=0, stream=None, cF=None, csw_qed=None):
+        """cF: Schroedinger-functional boundary coefficient; csw_qed: separate
+        coefficient of the U(1) field strength (after gauge_upload_qed)."""
+        if cF is None and csw_qed is None:
+            _check(lib().oq_clover_build(self.h, lat, kappa, csw, _stream(stream)), "oq_clover_build")
+            return
+        p = OqCloverParams(kappa, csw, 1.0 if cF is None else cF, 0.0 if csw_qed is None else csw_qed,
+                           0 if csw_qed is None else 1)
+        _check(lib().oq_clover_build_ex(self.h, lat, C.byref(p), _stream(stream)), "oq_clover_build_ex")
 
     # layouts -----------------------------------------------------------
     def pack(self, canon_dev, packed_dev, prec, subset=FULL, scale=1.0, nrhs=1, lat=0, stream=None):

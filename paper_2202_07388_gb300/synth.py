@@ -118,6 +118,15 @@ def make_gauge(dims, eps: float, seed: int, chunk: int = 1 << 20) -> np.ndarray:
     return out.reshape(dims + (4, 3, 3))
 
 
+def make_gauge_sf(dims, eps: float, seed: int) -> np.ndarray:
+    """SU(3) field for Schroedinger-functional boundaries with zero boundary
+    fields: ``make_gauge`` with the spatial links of slice x0 = 0 (the
+    boundary at x0 = 0 and, by periodicity, at x0 = T) set to the identity."""
+    u = make_gauge(dims, eps, seed)
+    u[0, :, :, :, 1:] = np.eye(3)
+    return u
+
+
 def make_u1_field(dims, sigma: float, seed: int) -> np.ndarray:
     """Real U(1) gauge potential A_mu(x) ~ N(0, sigma^2), shape dims + (4,)."""
     dims = tuple(int(v) for v in dims)

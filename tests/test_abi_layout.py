@@ -17,6 +17,7 @@ STRUCTS = {
     "oq_solver_params": oq.OqSolverParams,
     "oq_status": oq.OqStatus,
     "oq_kernel_time": oq.OqKernelTime,
+    "oq_clover_params": oq.OqCloverParams,
 }
 
 
