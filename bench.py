@@ -718,10 +718,16 @@ def run_workload_c5(args):
     ada = oq.SolverParams(res=RES, nmx=2000, nkv=16, ncy=20, nmr=20, bs=(4, 4, 4, 4), sdtype=oq.F32, adaptive=1,
                           alpha=0.9)
     plain = oq.SolverParams(res=RES, nmx=5000, nkv=16, ncy=0, sdtype=oq.F32)
+    # even-odd reduced block solver (MR on the blocks' Schur complements)
+    import dataclasses
+    sap_eo = dataclasses.replace(sap, sap_eo=1)
+    sap_eo3 = dataclasses.replace(sap, sap_eo=1, nmr=3)
+    ada_eo = dataclasses.replace(ada, sap_eo=1)
     # SAP block kernels: operands in shared memory (default), global operands one / two blocks per SM
     for name, prm, kern in (("sap_gcr", sap, 0), ("sap_gcr_global_operands", sap, 1),
                             ("sap_gcr_global_operands_two_ctas", sap, 2), ("sap_gcr_adaptive", ada, 0),
-                            ("gcr", plain, 0)):
+                            ("sap_gcr_eo_blocks", sap_eo, 0), ("sap_gcr_eo_blocks_nmr3", sap_eo3, 0),
+                            ("sap_gcr_adaptive_eo_blocks", ada_eo, 0), ("gcr", plain, 0)):
         h.set_option(oq.OPT_SAP_KERNEL, kern)
         h.sap_gcr(eta, psi, prm)
         t, (rc, st) = _timed(lambda: h.sap_gcr(eta, psi, prm))

@@ -110,6 +110,9 @@ typedef struct {
   int nladder;
   int ladder[4];
   double ladder_c;
+  int sap_eo;        /* SAP block solver: 0 = MR on the block operator D_i; 1 = MR on the block's
+                        even-odd Schur complement A_ee - D_eo A_oo^-1 D_oe, odd sites solved
+                        exactly afterwards (openQCD's block solver, Sec. 3) */
 } oq_solver_params;
 
 typedef struct {

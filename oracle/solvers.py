@@ -40,6 +40,7 @@ __all__ = [
     "default_reset_delta",
     "block_index",
     "sap",
+    "eo_block_solve",
     "fgcr",
     "GcrResult",
     "dense_solve",
@@ -256,8 +257,41 @@ def mr_block(apply_dc, b, bid, sel_site, nblk, nmr, adaptive=False, alpha=0.9,
     return x, r, steps
 
 
+def eo_block_solve(u, a, ainv, r, mask, mask_e, mask_o, bid, sel, nblk, nmr, adaptive, alpha, mr_tol, store,
+                   bc_t=-1.0):
+    """Approximate solution of D_i delta = r_i on every block of one colour
+    through the block's even-odd Schur complement (the even-odd reduced block
+    solver of openQCD's SAP, Sec. 3):
+
+        rhat_e  = r_e - D_eo A_oo^{-1} r_o
+        Dhat_i  = A_ee - D_eo A_oo^{-1} D_oe        (MR on the even block sites)
+        delta_o = A_oo^{-1} (r_o - D_oe delta_e)
+
+    with D_eo, D_oe the hops inside the blocks (Dirichlet boundaries).
+    Returns (delta, steps_per_block)."""
+    def hop_c(v):
+        # in-block hopping part of D: the colour's blocks never touch
+        return np.where(mask, -0.5 * dirac.hopping(u, np.where(mask, v, 0.0), bc_t), 0.0)
+
+    def on(m, v):
+        return np.where(m, v, 0.0)
+
+    r_e, r_o = on(mask_e, r), on(mask_o, r)
+    rhat = r_e - on(mask_e, hop_c(dirac.apply_site_matrix(ainv, r_o)))
+
+    def apply_dhat(v):
+        v = on(mask_e, v)
+        t = on(mask_o, dirac.apply_site_matrix(ainv, on(mask_o, hop_c(v))))
+        return on(mask_e, dirac.apply_site_matrix(a, v) - hop_c(t))
+
+    d_e, _, st = mr_block(apply_dhat, rhat, bid, sel, nblk, nmr, adaptive, alpha, mr_tol, store)
+    d_e = on(mask_e, d_e)
+    d_o = on(mask_o, dirac.apply_site_matrix(ainv, r_o - on(mask_o, hop_c(d_e))))
+    return d_e + d_o, st
+
+
 def sap(u, a, rho, bs, ncy, nmr, bc_t=-1.0, adaptive=False, alpha=0.9, mr_tol=0.0,
-        store="fp64", info=None):
+        store="fp64", info=None, eo=False, ainv=None):
     """Approximate D^{-1} rho by SAP (Sec. 3), starting from phi = 0.
 
     One cycle: for colour 0 ("black") then colour 1 ("white"): take the
@@ -265,10 +299,15 @@ def sap(u, a, rho, bs, ncy, nmr, bc_t=-1.0, adaptive=False, alpha=0.9, mr_tol=0.
     colour by MR, add the block corrections to phi.  ``adaptive`` ends the
     cycles once a cycle did not lower ||rho - D phi|| (at least one cycle;
     ``ncy`` is then the maximum) and switches on the MR exit rules with
-    ``mr_tol`` = res ||eta|| / n_blocks.
+    ``mr_tol`` = res ||eta|| / n_blocks.  ``eo`` runs the MR steps on the
+    blocks' even-odd Schur complements instead (``eo_block_solve``; ``ainv``
+    the per-site inverse of ``a``).
     """
     dims = rho.shape[:4]
     bid, colour, nblk = block_index(dims, bs)
+    odd = dirac.parity_mask(dims)
+    if eo and ainv is None:
+        ainv = np.linalg.inv(a)
     phi = np.zeros_like(rho)
     prev = norm(rho)
     cycles = 0
@@ -282,7 +321,13 @@ def sap(u, a, rho, bs, ncy, nmr, bc_t=-1.0, adaptive=False, alpha=0.9, mr_tol=0.
                 return np.where(mask, dirac.dw(u, a, np.where(mask, v, 0.0), bc_t), 0.0)
 
             r = np.where(mask, rho - dirac.dw(u, a, phi, bc_t), 0.0)
-            dx, _, st = mr_block(apply_dc, r, bid, sel, nblk, nmr, adaptive, alpha, mr_tol, store)
+            if eo:
+                mask_e = (sel & ~odd)[..., None, None]
+                mask_o = (sel & odd)[..., None, None]
+                dx, st = eo_block_solve(u, a, ainv, r, mask, mask_e, mask_o, bid, sel, nblk, nmr, adaptive,
+                                        alpha, mr_tol, store, bc_t)
+            else:
+                dx, _, st = mr_block(apply_dc, r, bid, sel, nblk, nmr, adaptive, alpha, mr_tol, store)
             phi = round_complex(phi + dx, store)
             mr_steps.append(st[np.unique(bid[sel])])
         cycles += 1

@@ -208,7 +208,8 @@ using namespace oq;
 
 extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, const void* rho_dev, void* phi_dev,
                             double mr_tol, void* stream) {
-  if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !rho_dev || !phi_dev || prm->ncy < 1 || prm->nmr < 0)
+  if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !rho_dev || !phi_dev || prm->ncy < 1 || prm->nmr < 0 ||
+      (prm->sap_eo != 0 && prm->sap_eo != 1))
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
@@ -226,8 +227,8 @@ extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, c
   for (int cy = 0; cy < prm->ncy; ++cy)
     for (int colour = 0; colour < 2; ++colour) {
       h->launches += 1;
-      if (sap_colour(L.g, prm->bs, colour, L.link_fmt, L.u32.p, L.a32.p, rho_dev, phi_dev, prm->nmr, prm->adaptive,
-                     alpha, mr_tol, nullptr, h->sap_kernel, s) != cudaSuccess)
+      if (sap_colour(L.g, prm->bs, colour, L.link_fmt, L.u32.p, L.a32.p, L.i32.p, rho_dev, phi_dev, prm->nmr,
+                     prm->adaptive, alpha, mr_tol, nullptr, h->sap_kernel, prm->sap_eo, s) != cudaSuccess)
         return OQ_ERR_CUDA;
     }
   return OQ_OK;
@@ -250,7 +251,8 @@ extern "C" int oq_nn_gcr_solve(oq_handle h, int lat, const oq_solver_params* prm
 static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const float* nn_w, const double* eta_dev,
                     double* psi_dev, int nrhs, oq_status* st, void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
-  if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nkv < 1 || prm->nkv > 64 || prm->ncy < 0 || prm->nmr < 0)
+  if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nkv < 1 || prm->nkv > 64 || prm->ncy < 0 || prm->nmr < 0 ||
+      (prm->sap_eo != 0 && prm->sap_eo != 1))
     return OQ_ERR_ARG;
   if (prm->sdtype != OQ_F32) return OQ_ERR_ARG;  // SAP and the Krylov vectors run in binary32
   LatCtx& L = h->lats[lat];
@@ -379,9 +381,9 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
           }
           for (int cy = 0; cy < prm->ncy; ++cy) {
             for (int colour = 0; colour < 2; ++colour)
-              KL(sap_colour(L.g, prm->bs, colour, L.link_fmt, L.u32.p, L.a32.p, rho, phik, prm->nmr, prm->adaptive,
-                            (float)(prm->alpha > 0.0 ? prm->alpha : 0.9), prm->res * eta_n / nblk,
-                            (unsigned*)mrc, h->sap_kernel, s));
+              KL(sap_colour(L.g, prm->bs, colour, L.link_fmt, L.u32.p, L.a32.p, L.i32.p, rho, phik, prm->nmr,
+                            prm->adaptive, (float)(prm->alpha > 0.0 ? prm->alpha : 0.9), prm->res * eta_n / nblk,
+                            (unsigned*)mrc, h->sap_kernel, prm->sap_eo, s));
             cycles_total += 1;
             if (prm->adaptive) {
               // cycle test on the global SAP residual ||rho - D phi||

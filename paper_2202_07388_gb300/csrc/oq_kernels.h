@@ -54,9 +54,12 @@ int nnprec_forward(struct ::oq_ctx* h, int lat, const void* r, void* y, cudaStre
 // takes the binary32 master weights, synchronises s, OQ_ERR_TIMEOUT on a failed wait
 int nnprec_forward_tc(struct ::oq_ctx* h, int lat, const float* master, const void* r, void* y, cudaStream_t s);
 
-// one SAP half cycle: every block of `colour` (binary32 fields)
+// one SAP half cycle: every block of `colour` (binary32 fields); eo: MR on
+// the blocks' even-odd Schur complements (needs clov_inv and blocks whose
+// operands fit in shared memory, else cudaErrorInvalidValue)
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
-                       const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
-                       unsigned* mr_steps, int kernel, cudaStream_t s);
+                       const void* clov_inv, const void* rho, void* phi, int nmr, int adaptive, float alpha,
+                       double tol, unsigned* mr_steps, int kernel, int eo, cudaStream_t s);
+size_t sap_smem_bytes(const int bs[4]);
 
 }  // namespace oq

@@ -16,7 +16,8 @@
 //      4 steps, ||r|| > alpha ||r_prev||, when ||r|| grew, or when ||r|| fell
 //      below tol = res ||eta|| / n_blocks; every decision is block-uniform;
 //   3. phi_i += x.
-// Block reductions are binary64.  Arithmetic and storage binary32.
+// sap_smem_eo_kernel replaces 2 by MR steps on the block's even-odd Schur
+// complement (see below).  Block reductions are binary64.  Arithmetic and storage binary32.
 // sap_smem_kernel (the default) stages the block's links and clover in
 // shared memory first; sap_kernel reads them from global memory.
 #include "oq_internal.h"
@@ -32,6 +33,7 @@ struct SapArgs {
   int colour;
   const void* links;   // binary32 packed links
   const void* clov;    // binary32 packed clover
+  const void* clov_inv;  // binary32 packed inverse clover (even-odd block solver)
   const char* rho;     // packed binary32 full field
   char* phi;           // packed binary32 full field, updated in place
   long half_bytes;
@@ -489,6 +491,222 @@ __global__ void __launch_bounds__(256) sap_smem_kernel(const SapArgs a) {
   if (a.mr_steps && t == 0) atomicAdd(a.mr_steps, (unsigned)steps);
 }
 
+// ---------------------------------------------------------------------------
+// Even-odd reduced block solver (openQCD's choice for SAP, Sec. 3): per block
+//   rhat_e = r_e - D_eo A_oo^{-1} r_o,
+//   MR steps on Dhat_i = A_ee - D_eo A_oo^{-1} D_oe (even block sites),
+//   delta_o = A_oo^{-1} (r_o - D_oe delta_e),
+// D_eo, D_oe the in-block hops.  The shared field holds the even vector at
+// even sites and the odd intermediate at odd sites, so one MR step is two
+// half passes (odd threads, then even threads) separated by a barrier; the
+// staged clover is A at even and A^{-1} at odd sites.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void zero_spinor(Spinor<float>& v) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v.c[s][c] = cx<float>{0.f, 0.f};
+}
+
+// acc = D_hop v (in-block hops of the shared field)
+__device__ __forceinline__ void sm_dhop(const SapSm& m, const int bs[4], int t, const int l[4], Spinor<float>& acc) {
+  zero_spinor(acc);
+  sm_block_hop<0>(m, bs, t, l, acc);
+  sm_block_hop<1>(m, bs, t, l, acc);
+  sm_block_hop<2>(m, bs, t, l, acc);
+  sm_block_hop<3>(m, bs, t, l, acc);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
+  extern __shared__ float4 sm4[];
+  const int nsite = a.bs[0] * a.bs[1] * a.bs[2] * a.bs[3];
+  SapSm m;
+  m.nsite = nsite;
+  m.a = sm4;
+  m.u = reinterpret_cast<float2*>(sm4 + 18 * nsite);
+  m.r = reinterpret_cast<float*>(m.u + 36 * nsite);
+  double* red = reinterpret_cast<double*>(m.r + 24 * nsite);
+  const int t = threadIdx.x;
+  const bool act = t < nsite;
+  const int half3 = a.nb[3] / 2;
+  int row = blockIdx.x / half3;
+  const int mb = blockIdx.x % half3;
+  const int bc2 = row % a.nb[2];
+  row /= a.nb[2];
+  const int bc1 = row % a.nb[1];
+  const int bc0 = row / a.nb[1];
+  const int bc3 = 2 * mb + ((a.colour + bc0 + bc1 + bc2) & 1);
+  int l[4], x[4];
+  {
+    int tt = act ? t : 0;
+    l[3] = tt % a.bs[3];
+    tt /= a.bs[3];
+    l[2] = tt % a.bs[2];
+    tt /= a.bs[2];
+    l[1] = tt % a.bs[1];
+    l[0] = tt / a.bs[1];
+  }
+  x[0] = bc0 * a.bs[0] + l[0];
+  x[1] = bc1 * a.bs[1] + l[1];
+  x[2] = bc2 * a.bs[2] + l[2];
+  x[3] = bc3 * a.bs[3] + l[3];
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const long i = eo_index(a.g, x);
+  const bool ev = act && p == 0, od = act && p == 1;
+
+  Spinor<float> r;  // block residual (kept for the odd sites' final solve)
+  if (act) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      Su3<float> u;
+      load_link<float, FMT>(a.links, a.g.Vh, p, mu, i, u);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) m.u[(mu * 9 + k) * nsite + t] = make_float2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
+    }
+    const float4* q = reinterpret_cast<const float4*>(p ? a.clov_inv : a.clov) + (long)p * 18 * a.g.Vh;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) m.a[k * nsite + t] = __ldg(q + k * a.g.Vh + i);
+    HopArgs ha;
+    ha.g = a.g;
+    ha.links = a.links;
+    const char* nbf = a.phi + (long)(1 - p) * a.half_bytes;
+    Spinor<float> acc;
+    zero_spinor(acc);
+    hop_dir<P_F32, FMT, 0, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 1, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 2, false>(ha, nbf, p, i, x, acc, -0.5f);
+    hop_dir<P_F32, FMT, 3, false>(ha, nbf, p, i, x, acc, -0.5f);
+    Spinor<float> ph, aph, rh;
+    load_spinor<P_F32>(a.phi + (long)p * a.half_bytes, a.g.Vh, i, ph);
+    clover_apply<float>(a.clov, a.g.Vh, p, i, ph, aph);
+    load_spinor<P_F32>(a.rho + (long)p * a.half_bytes, a.g.Vh, i, rh);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r.c[s][c] = rh.c[s][c] - (aph.c[s][c] + acc.c[s][c]);
+  }
+  __syncthreads();  // the staged links and clover are read by the neighbours below
+  // odd sites: w_o = A^{-1} r_o into the shared field
+  if (od) {
+    Spinor<float> w;
+    sm_clover(m, t, r, w);
+    store_smem(m.r, nsite, t, w);
+  }
+  __syncthreads();
+  // even sites: rhat_e = r_e - D_eo w_o (written at the even positions, read
+  // by no one in this phase)
+  Spinor<float> rh;
+  zero_spinor(rh);
+  if (ev) {
+    Spinor<float> acc;
+    sm_dhop(m, a.bs, t, l, acc);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rh.c[s][c] = r.c[s][c] - acc.c[s][c];
+    store_smem(m.r, nsite, t, rh);
+  }
+  double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+  if (a.adaptive) {
+    if (ev) n0 = site_norm2(rh);
+    block_sum3(n0, z1, z2, red);
+  } else {
+    __syncthreads();
+  }
+  double rn_prev = sqrt(n0);
+
+  Spinor<float> xs;
+  zero_spinor(xs);
+  int steps = 0;
+  for (int k = 1; k <= a.nmr; ++k) {
+    // odd half pass: t_o = A^{-1} D_oe rhat_e
+    if (od) {
+      Spinor<float> acc, w;
+      sm_dhop(m, a.bs, t, l, acc);
+      sm_clover(m, t, acc, w);
+      store_smem(m.r, nsite, t, w);
+    }
+    __syncthreads();
+    // even half pass: q_e = A rhat_e - D_eo t_o, then <q, rhat>, <q, q>
+    Spinor<float> pv;
+    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
+    if (ev) {
+      Spinor<float> own, acc;
+      load_smem(m.r, nsite, t, own);
+      sm_clover(m, t, own, pv);
+      sm_dhop(m, a.bs, t, l, acc);
+      float ar = 0.f, ai = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pv.c[s][c] = pv.c[s][c] - acc.c[s][c];
+          cx<float> q2 = pv.c[s][c], v = own.c[s][c];
+          ar += q2.re * v.re + q2.im * v.im;
+          ai += q2.re * v.im - q2.im * v.re;
+          a2 += q2.re * q2.re + q2.im * q2.im;
+        }
+      pr_re = ar;
+      pr_im = ai;
+      pp = a2;
+    }
+    block_sum3(pr_re, pr_im, pp, red);  // barrier: every read of this step is done
+    float om_re = 0.f, om_im = 0.f;
+    if (pp > 0.0) {
+      om_re = (float)(pr_re / pp);
+      om_im = (float)(pr_im / pp);
+    }
+    const cx<float> om{om_re, om_im};
+    double n1 = 0.0, y1 = 0.0, y2 = 0.0;
+    if (ev) {
+      Spinor<float> own;
+      load_smem(m.r, nsite, t, own);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cfma(xs.c[s][c], om, own.c[s][c]);
+          own.c[s][c] = own.c[s][c] - om * pv.c[s][c];
+        }
+      store_smem(m.r, nsite, t, own);
+      n1 = site_norm2(own);
+    }
+    steps = k;
+    if (a.adaptive) {
+      block_sum3(n1, y1, y2, red);
+      const double rn_new = sqrt(n1);
+      if ((k >= 4 && rn_new > (double)a.alpha * rn_prev) || rn_new > rn_prev || rn_new < a.tol) break;
+      rn_prev = rn_new;
+    } else {
+      __syncthreads();  // the odd half pass of the next step reads the even residual
+    }
+  }
+  // delta_e = x_e into the shared field; delta_o = A^{-1} (r_o - D_oe delta_e)
+  if (ev) store_smem(m.r, nsite, t, xs);
+  __syncthreads();
+  if (od) {
+    Spinor<float> acc, w;
+    sm_dhop(m, a.bs, t, l, acc);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w.c[s][c] = r.c[s][c] - acc.c[s][c];
+    sm_clover(m, t, w, xs);
+  }
+  if (act) {
+    char* pp = a.phi + (long)p * a.half_bytes;
+    Spinor<float> ph;
+    load_spinor<P_F32>(pp, a.g.Vh, i, ph);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ph.c[s][c] = ph.c[s][c] + xs.c[s][c];
+    store_spinor<P_F32>(pp, a.g.Vh, i, ph);
+  }
+  if (a.mr_steps && t == 0) atomicAdd(a.mr_steps, (unsigned)steps);
+}
+
 size_t sap_smem_bytes(const int bs[4]) {
   const int nsite = bs[0] * bs[1] * bs[2] * bs[3];
   const int threads = (nsite + 31) / 32 * 32;
@@ -496,8 +714,8 @@ size_t sap_smem_bytes(const int bs[4]) {
 }
 
 cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, const void* links, const void* clov,
-                       const void* rho, void* phi, int nmr, int adaptive, float alpha, double tol,
-                       unsigned* mr_steps, int kernel, cudaStream_t s) {
+                       const void* clov_inv, const void* rho, void* phi, int nmr, int adaptive, float alpha,
+                       double tol, unsigned* mr_steps, int kernel, int eo, cudaStream_t s) {
   SapArgs a;
   a.g = g;
   int nblk = 1;
@@ -509,6 +727,7 @@ cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, cons
   a.colour = colour;
   a.links = links;
   a.clov = clov;
+  a.clov_inv = clov_inv;
   a.rho = (const char*)rho;
   a.phi = (char*)phi;
   a.half_bytes = spinor_half_bytes(g.Vh, P_F32);
@@ -521,6 +740,19 @@ cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, cons
   const int threads = (nsite + 31) / 32 * 32;
   const size_t smem = sizeof(float) * 24 * nsite + sizeof(double) * 3 * (threads / 32);
   dim3 grid(nblk / 2), block(threads);
+  if (eo) {
+    // even-odd reduced block solver: shared-memory operands only
+    const size_t sm2 = sap_smem_bytes(bs);
+    if (sm2 > 227 * 1024 || !clov_inv) return cudaErrorInvalidValue;
+    if (fmt == LINK_12) {
+      cudaFuncSetAttribute(sap_smem_eo_kernel<LINK_12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+      sap_smem_eo_kernel<LINK_12><<<grid, block, sm2, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(sap_smem_eo_kernel<LINK_18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+      sap_smem_eo_kernel<LINK_18><<<grid, block, sm2, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   if (kernel == 0) {
     // operands in shared memory (the default), if they fit
     const size_t sm2 = sap_smem_bytes(bs);

@@ -38,6 +38,7 @@ class OqSolverParams(C.Structure):
         ("res", C.c_double), ("nmx", C.c_int), ("nkv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
         ("bs", C.c_int * 4), ("sdtype", C.c_int), ("delta", C.c_double), ("adaptive", C.c_int),
         ("alpha", C.c_double), ("nladder", C.c_int), ("ladder", C.c_int * 4), ("ladder_c", C.c_double),
+        ("sap_eo", C.c_int),
     ]
 
 
@@ -161,6 +162,7 @@ class SolverParams:
     alpha: float = 0.9
     ladder: tuple = ()        # CGNE precision ladder, e.g. (F16, F32, F64); () = sdtype throughout
     ladder_c: float = 0.0     # switch constant (x eps of the current type); <= 0: 1
+    sap_eo: int = 0           # SAP block solver on the even-odd Schur complement
 
     def c(self):
         p = OqSolverParams()
@@ -174,6 +176,7 @@ class SolverParams:
         for k, t in enumerate(self.ladder):
             p.ladder[k] = t
         p.ladder_c = self.ladder_c
+        p.sap_eo = self.sap_eo
         return p
 
 
