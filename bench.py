@@ -12,7 +12,10 @@ value    = algorithmic bytes of all stencil launches of the timed steps
 roofline = the dominant stencil kernel: its algorithmic bytes per launch /
            its mean CUDA-event duration, against the measured HBM copy peak
 e2e      = the same bytes / time of the public call with host buffers
-           (pinned host -> device copy of eta, solve, device -> host psi)
+           (pinned host -> device copy of eta, solve, device -> host psi;
+           even-site canonical fields, oq_cgne_solve_even), the copies of a
+           stream of steps overlapped with the solves; the serial timing of
+           each phase is reported next to it
 tts      = time to solution of one right-hand side: binary64-only CGNE vs
            the mixed-precision solves (the "vs plain FP64 GPU" comparison),
            and the precision ladders (one and 12 right-hand sides)
@@ -390,26 +393,104 @@ def run_ours(args):
     small = [p for p in prof if p["prec"] not in (0, 4)]
     roof_hbm = roofline_of(max(small, key=lambda p: p["total_ms"])) if small else None
 
-    # end to end through the public call with host buffers
-    eta_host = eta.cpu().pin_memory()
+    # end to end through the public call with host buffers: the source of the
+    # even system lives on the even sites, so the host holds even-site
+    # canonical fields (oq_cgne_solve_even; half the bytes of full fields)
+    full = eta.cpu().numpy().view(np.complex128).reshape((NRHS, -1, 12))
+    lexp = np.indices(DIMS).sum(axis=0).reshape(-1) % 2
+    eta_host = torch.from_numpy(np.ascontiguousarray(full[:, lexp == 0]).view(np.float64)).pin_memory()
+    del full
     psi_host = torch.empty_like(eta_host).pin_memory()
-    eta_dev2 = torch.empty_like(eta)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # one untimed pass first: the first copies into freshly pinned buffers pay one-off costs
-    eta_dev2.copy_(eta_host, non_blocking=True)
-    rc, _ = h.cgne(eta_dev2, psi, prm, nrhs=NRHS)
-    psi_host.copy_(psi, non_blocking=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.e2e_steps):
-        eta_dev2.copy_(eta_host, non_blocking=True)
-        rc, _ = h.cgne(eta_dev2, psi, prm, nrhs=NRHS)
-        assert rc == oq.OK
-        psi_host.copy_(psi, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    eta_dev2 = torch.empty(eta_host.shape, dtype=eta_host.dtype, device=eta.device)
+    psi_dev2 = torch.empty_like(eta_dev2)
+
+    def e2e_time(solve, e_host, e_dev, p_dev, p_host):
+        """Median over the steps of H2D + solve + D2H (events around each
+        phase: the copies from pinned host memory vary from step to step on
+        a host shared with other jobs); returns (total, h2d, solve, d2h) ms."""
+        # untimed first: copy round trips and one pass (the first copies into freshly
+        # pinned buffers, right after large host allocations, pay one-off costs)
+        for _ in range(3):
+            e_dev.copy_(e_host, non_blocking=True)
+            p_host.copy_(p_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        time.sleep(1.0)
+        e_dev.copy_(e_host, non_blocking=True)
+        solve(e_dev, p_dev)
+        p_host.copy_(p_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        rows = []
+        for _ in range(args.e2e_steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record()
+            e_dev.copy_(e_host, non_blocking=True)
+            ev[1].record()
+            rc_, _ = solve(e_dev, p_dev)
+            assert rc_ == oq.OK
+            ev[2].record()
+            p_host.copy_(p_dev, non_blocking=True)
+            ev[3].record()
+            torch.cuda.synchronize()
+            rows.append([ev[0].elapsed_time(ev[3]), ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                         ev[2].elapsed_time(ev[3])])
+        return [statistics.median(r[k] for r in rows) for k in range(4)]
+
+    def e2e_pipelined(solve, e_host, e_dev, p_dev, p_host):
+        """A stream of solves as a user runs it: the next step's source is
+        copied in on a second stream while the current step solves, and each
+        step's solution is copied out while the next one solves (two device
+        buffers each way).  Every step still moves its input in and its
+        result out inside the timed region; returns ms per step."""
+        main = torch.cuda.current_stream()
+        cs = torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        ev_read = [torch.cuda.Event() for _ in range(2)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for b in (0, 1):  # untimed round trips through every buffer
+            e_dev[b].copy_(e_host, non_blocking=True)
+            p_host[b].copy_(p_dev[b], non_blocking=True)
+        torch.cuda.synchronize()
+        t0.record(main)
+        cs.wait_stream(main)
+        with torch.cuda.stream(cs):
+            e_dev[0].copy_(e_host, non_blocking=True)
+            ev_in[0].record(cs)
+        for k in range(args.e2e_steps):
+            b = k % 2
+            if k + 1 < args.e2e_steps:
+                with torch.cuda.stream(cs):  # buffer 1 - b was last read by the (finished) step k - 1
+                    e_dev[1 - b].copy_(e_host, non_blocking=True)
+                    ev_in[1 - b].record(cs)
+            main.wait_event(ev_in[b])
+            if k >= 2:
+                main.wait_event(ev_read[b])  # step k - 2's result has left p_dev[b]
+            rc_, _ = solve(e_dev[b], p_dev[b])
+            assert rc_ == oq.OK
+            ev_out[b].record(main)
+            with torch.cuda.stream(cs):
+                cs.wait_event(ev_out[b])
+                p_host[b].copy_(p_dev[b], non_blocking=True)
+                ev_read[b].record(cs)
+        main.wait_stream(cs)
+        t1.record(main)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / args.e2e_steps
+
+    solve_even = lambda e, p: h.cgne_even(e, p, prm, nrhs=NRHS)  # noqa: E731
+    ser_ms, ser_h2d, ser_solve, ser_d2h = e2e_time(solve_even, eta_host, eta_dev2, psi_dev2, psi_host)
+    eta_dev3, psi_dev3 = torch.empty_like(eta_dev2), torch.empty_like(psi_dev2)
+    psi_host3 = torch.empty_like(psi_host).pin_memory()
+    e2e_ms = e2e_pipelined(solve_even, eta_host, [eta_dev2, eta_dev3], [psi_dev2, psi_dev3], [psi_host, psi_host3])
     e2e_value = (stencil_bytes / args.steps) / (e2e_ms * 1e-3) / 1e9
+    e2e_bytes = int(eta_host.numel() * 8)
+    # the same with full-lattice canonical fields (odd sites zero), for comparison
+    del eta_dev2, psi_dev2, psi_host, eta_host, eta_dev3, psi_dev3, psi_host3
+    eta_host_f = eta.cpu().pin_memory()
+    psi_host_f = torch.empty_like(eta_host_f).pin_memory()
+    eta_dev_f = torch.empty_like(eta)
+    e2e_full = e2e_time(lambda e, p: h.cgne(e, p, prm, nrhs=NRHS), eta_host_f, eta_dev_f, psi, psi_host_f)
+    del eta_host_f, psi_host_f, eta_dev_f
 
     # time to solution, one rhs: binary64 only vs mixed precision
     tts = None
@@ -488,8 +569,15 @@ def run_ours(args):
             "roofline_stencil_hbm": roof_hbm,
             "cpu_baseline": cpu_line,
             "e2e": {"value": e2e_value, "unit": "GB/s",
-                    "h2d_bytes_per_step": int(eta.numel() * 8), "d2h_bytes_per_step": int(psi.numel() * 8),
-                    "ms_per_step": e2e_ms},
+                    "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes,
+                    "ms_per_step": e2e_ms, "layout": "even-site canonical fields (oq_cgne_solve_even)",
+                    "steps": args.e2e_steps,
+                    "pipelining": "the next step's H2D and the previous step's D2H on a second stream, "
+                                  "overlapping the current solve",
+                    "serial": {"ms_per_step": ser_ms, "h2d_ms": ser_h2d, "solve_ms": ser_solve, "d2h_ms": ser_d2h,
+                               "note": "median over steps of H2D, solve and D2H one after the other"},
+                    "serial_full_layout": {"ms_per_step": e2e_full[0], "h2d_ms": e2e_full[1],
+                                           "solve_ms": e2e_full[2], "d2h_ms": e2e_full[3]}},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "solve": {"steps": [s["steps"] for s in st_last], "resets": [s["resets"] for s in st_last],
@@ -521,13 +609,13 @@ def run_profile_case(args):
     h.clover_build(KAPPA, CSW)
     prec = oq.PREC[args.profile_prec]
     nrhs = args.profile_nrhs
-    if args.profile_kind in ("tc", "cc", "sap"):
+    if args.profile_kind in ("tc", "cc", "sap", "sap_eo"):
         # learned preconditioner layers (tensor-core or CUDA-core) / SAP, binary32 fields
         src = torch.randn(int(np.prod(dims)) * 24, dtype=torch.float64, device="cuda")
         a, b = h.new_packed(oq.F32), h.new_packed(oq.F32)
         h.pack(src, a, oq.F32)
         w = torch.randn(1152, dtype=torch.float32, device="cuda") * 0.1
-        prm = oq.SolverParams(ncy=1, nmr=5, bs=(4, 4, 4, 4))
+        prm = oq.SolverParams(ncy=1, nmr=5, bs=(4, 4, 4, 4), sap_eo=int(args.profile_kind == "sap_eo"))
         for _ in range(3):
             if args.profile_kind == "tc":
                 h.nnprec_apply_tc(w, a, b)
@@ -799,14 +887,14 @@ def main():
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-prec", default="fp16", choices=["fp64", "fp32", "bf16", "fp16", "df64"])
     ap.add_argument("--profile-nrhs", type=int, default=12)
-    ap.add_argument("--profile-kind", default="dhat", choices=["dhat", "cgne", "tc", "cc", "sap"])
+    ap.add_argument("--profile-kind", default="dhat", choices=["dhat", "cgne", "tc", "cc", "sap", "sap_eo"])
     ap.add_argument("--profile-pin", default=None,
                     help="bx,by,nr,regcap,link_fmt: pin the stencil launch instead of autotuning")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-reps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tts", action="store_true")

@@ -112,7 +112,7 @@ typedef struct {
   double ladder_c;
   int sap_eo;        /* SAP block solver: 0 = MR on the block operator D_i; 1 = MR on the block's
                         even-odd Schur complement A_ee - D_eo A_oo^-1 D_oe, odd sites solved
-                        exactly afterwards (openQCD's block solver, Sec. 3) */
+                        exactly afterwards (openQCD's block solver, Sec. 3); needs bs[3] even */
 } oq_solver_params;
 
 typedef struct {
@@ -300,6 +300,14 @@ int oq_dot(oq_handle h, int lat, int prec, int subset, const void* x_dev, const 
  * of nrhs entries. */
 int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
                   double* psi_dev, int nrhs, oq_status* st, void* stream);
+
+/* oq_cgne_solve with eta_dev / psi_dev holding the even sites only, in the
+ * even-site canonical layout: nrhs consecutive fields of V/2 sites, the even
+ * site with lexicographic index n (time slowest) at position n / 2, 12
+ * complex binary64 per site (spin-major).  Half the bytes of the full
+ * canonical fields, the same solve. */
+int oq_cgne_solve_even(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
+                       double* psi_dev, int nrhs, oq_status* st, void* stream);
 
 /* The CGNE of oq_cgne_solve over an uneven batch: nsys systems, system k on
  * lattice lats[k] of the handle (lattices of different sizes and operators,

@@ -58,8 +58,9 @@ double default_delta(int prec) {
 
 }  // namespace
 
-extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev,
-                             double* psi_dev, int nrhs, oq_status* st, void* stream) {
+// half: eta / psi hold the even sites only (lexicographic index / 2)
+static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev, double* psi_dev,
+                     int nrhs, oq_status* st, void* stream, int half) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
   if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nladder < 0 || prm->nladder > 4) return OQ_ERR_ARG;
   // the storage types of the phases: sdtype alone, or the ladder
@@ -87,7 +88,8 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
     hPmax = a > hPmax ? a : hPmax;
     hXmax = b > hXmax ? b : hXmax;
   }
-  const size_t canon_field = sizeof(double) * 24 * 2 * Vh;
+  const size_t canon_field = sizeof(double) * 24 * (half ? 1 : 2) * Vh;
+  const long canon_stride = (half ? 1 : 2) * Vh * 12;  // double2 per canonical field
   void *eta64, *xd, *rd, *t64, *u64v, *pv, *rv, *uv, *tv, *xs;
   int rc = 0;
   rc |= h->workspace(lat, "cg_eta64", h64 * nrhs, &eta64);
@@ -122,7 +124,7 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
   } while (0)
 
   // eta -> packed binary64 even field; x_d = 0, x_s = 0
-  KL(pack_spinor(L.g, P_F64, OQ_EVEN, eta_dev, eta64, 1.0, nrhs, 2 * Vh * 12, (long)h64, s));
+  KL(pack_spinor(L.g, P_F64, OQ_EVEN, eta_dev, eta64, 1.0, nrhs, canon_stride, (long)h64, s, half));
   CK(cudaMemsetAsync(xd, 0, h64 * nrhs, s));
   CK(cudaMemsetAsync(xs, 0, hXmax * nrhs, s));
   CK(cudaMemcpyAsync(rd, eta64, h64 * nrhs, cudaMemcpyDeviceToDevice, s));
@@ -358,7 +360,7 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
 
   // psi = x_d on the even sites, zero on the odd sites
   CK(cudaMemsetAsync(psi_dev, 0, canon_field * nrhs, s));
-  KL(unpack_spinor(L.g, P_F64, OQ_EVEN, xd, psi_dev, 1.0, nrhs, (long)h64, 2 * Vh * 12, s));
+  KL(unpack_spinor(L.g, P_F64, OQ_EVEN, xd, psi_dev, 1.0, nrhs, (long)h64, canon_stride, s, half));
   CK(cudaStreamSynchronize(s));
   int ret = OQ_OK;
   for (int k = 0; k < nrhs; ++k) {
@@ -378,4 +380,14 @@ extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, 
 #undef CK
 #undef RK
 #undef KL
+}
+
+extern "C" int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev,
+                             double* psi_dev, int nrhs, oq_status* st, void* stream) {
+  return cgne_impl(h, lat, prm, eta_dev, psi_dev, nrhs, st, stream, 0);
+}
+
+extern "C" int oq_cgne_solve_even(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev,
+                                  double* psi_dev, int nrhs, oq_status* st, void* stream) {
+  return cgne_impl(h, lat, prm, eta_dev, psi_dev, nrhs, st, stream, 1);
 }

@@ -209,7 +209,7 @@ using namespace oq;
 extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, const void* rho_dev, void* phi_dev,
                             double mr_tol, void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !rho_dev || !phi_dev || prm->ncy < 1 || prm->nmr < 0 ||
-      (prm->sap_eo != 0 && prm->sap_eo != 1))
+      (prm->sap_eo != 0 && prm->sap_eo != 1) || (prm->sap_eo && prm->bs[3] % 2))
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
@@ -252,7 +252,7 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
                     double* psi_dev, int nrhs, oq_status* st, void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
   if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nkv < 1 || prm->nkv > 64 || prm->ncy < 0 || prm->nmr < 0 ||
-      (prm->sap_eo != 0 && prm->sap_eo != 1))
+      (prm->sap_eo != 0 && prm->sap_eo != 1) || (prm->sap_eo && prm->ncy > 0 && prm->bs[3] % 2))
     return OQ_ERR_ARG;
   if (prm->sdtype != OQ_F32) return OQ_ERR_ARG;  // SAP and the Krylov vectors run in binary32
   LatCtx& L = h->lats[lat];

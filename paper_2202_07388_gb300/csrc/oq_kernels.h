@@ -14,10 +14,12 @@ cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u3
 // Schroedinger-functional boundaries: zero the time-like links of slices
 // x0 = 0 and x0 = T-1 in every hopping copy
 cudaError_t sf_mask_links(const Geom& g, double* u64, void* u32, int fmt, void* u18, cudaStream_t s);
+// half (subset EVEN or ODD only): the canonical field holds the sites of that
+// parity only, site-lexicographic index / 2
 cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
-                        int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s);
+                        int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s, int half = 0);
 cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
-                          int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s);
+                          int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s, int half = 0);
 // binary64 array of n values -> n double-float (hi, lo) pairs
 cudaError_t split_f64(const double* in, void* out, size_t n, cudaStream_t s);
 // links: packed binary64 links of the field strength; au1 (optional):

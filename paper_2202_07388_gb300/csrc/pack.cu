@@ -115,7 +115,7 @@ cudaError_t sf_mask_links(const Geom& g, double* u64, void* u32, int fmt, void* 
 // the subset, blockIdx.z = rhs.
 template <int P>
 __global__ void pack_spinor_kernel(Geom g, const double2* __restrict__ canon, char* __restrict__ out,
-                                   int subset, long canon_stride, long out_stride, double scale) {
+                                   int subset, long canon_stride, long out_stride, double scale, int half) {
   typedef typename PrecTraits<P>::R R;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.Vh) return;
@@ -123,7 +123,9 @@ __global__ void pack_spinor_kernel(Geom g, const double2* __restrict__ canon, ch
   const int rhs = blockIdx.z;
   int x[4];
   eo_coords(g, p, i, x);
-  const double2* src = canon + rhs * canon_stride + lex_of(g, x) * 12;
+  // half: the canonical field holds one parity only, site lex / 2 (the sites
+  // of one parity alternate along x3, L3 even)
+  const double2* src = canon + rhs * canon_stride + (half ? lex_of(g, x) >> 1 : lex_of(g, x)) * 12;
   // Schroedinger-functional lattices: the field vanishes at x0 = 0
   if (g.bc_t == 0.f && x[0] == 0) scale = 0.0;
   Spinor<R> s;
@@ -160,7 +162,7 @@ __global__ void pack_spinor_kernel(Geom g, const double2* __restrict__ canon, ch
 
 template <int P>
 __global__ void unpack_spinor_kernel(Geom g, const char* __restrict__ in, double2* __restrict__ canon,
-                                     int subset, long in_stride, long canon_stride, double inv_scale) {
+                                     int subset, long in_stride, long canon_stride, double inv_scale, int half) {
   typedef typename PrecTraits<P>::R R;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.Vh) return;
@@ -171,40 +173,42 @@ __global__ void unpack_spinor_kernel(Geom g, const char* __restrict__ in, double
   const char* src = in + rhs * in_stride + ((subset == 2) ? (long)p * spinor_half_bytes(g.Vh, P) : 0);
   Spinor<R> s;
   load_spinor<P>(src, g.Vh, i, s);
-  double2* dst = canon + rhs * canon_stride + lex_of(g, x) * 12;
+  double2* dst = canon + rhs * canon_stride + (half ? lex_of(g, x) >> 1 : lex_of(g, x)) * 12;
 #pragma unroll
   for (int k = 0; k < 12; ++k)
     dst[k] = make_double2((double)s.c[k / 3][k % 3].re * inv_scale, (double)s.c[k / 3][k % 3].im * inv_scale);
 }
 
 cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
-                        int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s) {
+                        int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s, int half) {
+  if (half && subset == 2) return cudaErrorInvalidValue;
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), subset == 2 ? 2 : 1, nrhs);
   const double2* c = reinterpret_cast<const double2*>(canon);
   char* o = reinterpret_cast<char*>(out);
   switch (prec) {
-    case P_F64: pack_spinor_kernel<P_F64><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
-    case P_F32: pack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
-    case P_BF16: pack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
-    case P_F16: pack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
-    case P_DF64: pack_spinor_kernel<P_DF64><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+    case P_F64: pack_spinor_kernel<P_F64><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale, half); break;
+    case P_F32: pack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale, half); break;
+    case P_BF16: pack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale, half); break;
+    case P_F16: pack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale, half); break;
+    case P_DF64: pack_spinor_kernel<P_DF64><<<grid, block, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale, half); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
-                          int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s) {
+                          int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s, int half) {
+  if (half && subset == 2) return cudaErrorInvalidValue;
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), subset == 2 ? 2 : 1, nrhs);
   double2* c = reinterpret_cast<double2*>(canon);
   const char* i = reinterpret_cast<const char*>(in);
   const double inv = 1.0 / scale;
   switch (prec) {
-    case P_F64: unpack_spinor_kernel<P_F64><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
-    case P_F32: unpack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
-    case P_BF16: unpack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
-    case P_F16: unpack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
-    case P_DF64: unpack_spinor_kernel<P_DF64><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv); break;
+    case P_F64: unpack_spinor_kernel<P_F64><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv, half); break;
+    case P_F32: unpack_spinor_kernel<P_F32><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv, half); break;
+    case P_BF16: unpack_spinor_kernel<P_BF16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv, half); break;
+    case P_F16: unpack_spinor_kernel<P_F16><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv, half); break;
+    case P_DF64: unpack_spinor_kernel<P_DF64><<<grid, block, 0, s>>>(g, i, c, subset, in_stride_bytes, canon_stride_d2, inv, half); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -508,13 +508,50 @@ __device__ __forceinline__ void zero_spinor(Spinor<float>& v) {
     for (int c = 0; c < 3; ++c) v.c[s][c] = cx<float>{0.f, 0.f};
 }
 
+// The block's sites are held parity-sorted: position k < nsite/2 is the
+// block-local-even site with in-block lexicographic index n = 2k + c, c
+// fixing the parity (bs[3] even, so the sites of one parity alternate along
+// x3), positions from nsite/2 on the local-odd sites.  A half pass then runs
+// whole warps instead of every other lane.
+__device__ __forceinline__ int eo_pos(int n, int par, int half) { return par * half + (n >> 1); }
+
+template <int MU>
+__device__ __forceinline__ void sm_block_hop_eo(const SapSm& m, const int bs[4], int n, int par, int half,
+                                                const int l[4], Spinor<float>& acc) {
+  int stride = 1;
+  for (int nu = 3; nu > MU; --nu) stride *= bs[nu];
+  const int t = eo_pos(n, par, half);
+  if (l[MU] + 1 < bs[MU]) {
+    Spinor<float> nb;
+    load_smem(m.r, m.nsite, eo_pos(n + stride, par ^ 1, half), nb);
+    HalfSpinor<float> h, r;
+    project<MU, -1>(nb, h);
+    Su3<float> u;
+    sm_link(m, MU, t, u);
+    su3_mul(u, h, r);
+    accum_reconstruct<MU, -1>(acc, r, -0.5f);
+  }
+  if (l[MU] > 0) {
+    const int tb = eo_pos(n - stride, par ^ 1, half);
+    Spinor<float> nb;
+    load_smem(m.r, m.nsite, tb, nb);
+    HalfSpinor<float> h, r;
+    project<MU, +1>(nb, h);
+    Su3<float> u;
+    sm_link(m, MU, tb, u);  // U_mu(x - mu): the forward link of the site below
+    su3_dag_mul(u, h, r);
+    accum_reconstruct<MU, +1>(acc, r, -0.5f);
+  }
+}
+
 // acc = D_hop v (in-block hops of the shared field)
-__device__ __forceinline__ void sm_dhop(const SapSm& m, const int bs[4], int t, const int l[4], Spinor<float>& acc) {
+__device__ __forceinline__ void sm_dhop(const SapSm& m, const int bs[4], int n, int par, int half, const int l[4],
+                                        Spinor<float>& acc) {
   zero_spinor(acc);
-  sm_block_hop<0>(m, bs, t, l, acc);
-  sm_block_hop<1>(m, bs, t, l, acc);
-  sm_block_hop<2>(m, bs, t, l, acc);
-  sm_block_hop<3>(m, bs, t, l, acc);
+  sm_block_hop_eo<0>(m, bs, n, par, half, l, acc);
+  sm_block_hop_eo<1>(m, bs, n, par, half, l, acc);
+  sm_block_hop_eo<2>(m, bs, n, par, half, l, acc);
+  sm_block_hop_eo<3>(m, bs, n, par, half, l, acc);
 }
 
 template <int FMT>
@@ -537,21 +574,26 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
   const int bc1 = row % a.nb[1];
   const int bc0 = row / a.nb[1];
   const int bc3 = 2 * mb + ((a.colour + bc0 + bc1 + bc2) & 1);
-  int l[4], x[4];
+  // thread t holds the site at parity-sorted position t (see eo_pos)
+  const int half = nsite >> 1;
+  const int par = (act && t >= half) ? 1 : 0;  // block-local parity
+  int l[4], x[4], n;
   {
-    int tt = act ? t : 0;
-    l[3] = tt % a.bs[3];
-    tt /= a.bs[3];
-    l[2] = tt % a.bs[2];
-    tt /= a.bs[2];
-    l[1] = tt % a.bs[1];
-    l[0] = tt / a.bs[1];
+    const int k = act ? t - par * half : 0;
+    int rr = (2 * k) / a.bs[3];  // the row (l0, l1, l2) of in-block index 2k + c
+    l[2] = rr % a.bs[2];
+    rr /= a.bs[2];
+    l[1] = rr % a.bs[1];
+    l[0] = rr / a.bs[1];
+    const int c = (par + l[0] + l[1] + l[2]) & 1;
+    l[3] = (2 * k) % a.bs[3] + c;
+    n = 2 * k + c;
   }
   x[0] = bc0 * a.bs[0] + l[0];
   x[1] = bc1 * a.bs[1] + l[1];
   x[2] = bc2 * a.bs[2] + l[2];
   x[3] = bc3 * a.bs[3] + l[3];
-  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;  // lattice parity (the Schur complement's)
   const long i = eo_index(a.g, x);
   const bool ev = act && p == 0, od = act && p == 1;
 
@@ -600,7 +642,7 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
   zero_spinor(rh);
   if (ev) {
     Spinor<float> acc;
-    sm_dhop(m, a.bs, t, l, acc);
+    sm_dhop(m, a.bs, n, par, half, l, acc);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -623,7 +665,7 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
     // odd half pass: t_o = A^{-1} D_oe rhat_e
     if (od) {
       Spinor<float> acc, w;
-      sm_dhop(m, a.bs, t, l, acc);
+      sm_dhop(m, a.bs, n, par, half, l, acc);
       sm_clover(m, t, acc, w);
       store_smem(m.r, nsite, t, w);
     }
@@ -635,7 +677,7 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
       Spinor<float> own, acc;
       load_smem(m.r, nsite, t, own);
       sm_clover(m, t, own, pv);
-      sm_dhop(m, a.bs, t, l, acc);
+      sm_dhop(m, a.bs, n, par, half, l, acc);
       float ar = 0.f, ai = 0.f, a2 = 0.f;
 #pragma unroll
       for (int s = 0; s < 4; ++s)
@@ -687,7 +729,7 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
   __syncthreads();
   if (od) {
     Spinor<float> acc, w;
-    sm_dhop(m, a.bs, t, l, acc);
+    sm_dhop(m, a.bs, n, par, half, l, acc);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -743,7 +785,7 @@ cudaError_t sap_colour(const Geom& g, const int bs[4], int colour, int fmt, cons
   if (eo) {
     // even-odd reduced block solver: shared-memory operands only
     const size_t sm2 = sap_smem_bytes(bs);
-    if (sm2 > 227 * 1024 || !clov_inv) return cudaErrorInvalidValue;
+    if (sm2 > 227 * 1024 || !clov_inv || bs[3] % 2) return cudaErrorInvalidValue;
     if (fmt == LINK_12) {
       cudaFuncSetAttribute(sap_smem_eo_kernel<LINK_12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
       sap_smem_eo_kernel<LINK_12><<<grid, block, sm2, s>>>(a);

@@ -80,6 +80,8 @@ _SIGS = {
     "oq_dot": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_double), _P]),
     "oq_cgne_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
                                 C.POINTER(OqStatus), _P]),
+    "oq_cgne_solve_even": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
+                                     C.POINTER(OqStatus), _P]),
     "oq_sap_gcr_solve": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_int,
                                    C.POINTER(OqStatus), _P]),
     "oq_sap_apply": (C.c_int, [_P, C.c_int, C.POINTER(OqSolverParams), _P, _P, C.c_double, _P]),
@@ -279,6 +281,16 @@ class Handle:
         rc = lib().oq_cgne_solve(self.h, lat, C.byref(p), _ptr(eta_dev), _ptr(psi_dev), nrhs, st, _stream(stream))
         if check and rc not in (OK, ERR_NOCONV):
             _check(rc, "oq_cgne_solve")
+        return rc, [status_dict(s) for s in st]
+
+    def cgne_even(self, eta_dev, psi_dev, params: SolverParams, nrhs=1, lat=0, stream=None, check=True):
+        """oq_cgne_solve on even-site canonical fields (V/2 sites each, index lex // 2)."""
+        st = (OqStatus * nrhs)()
+        p = params.c()
+        rc = lib().oq_cgne_solve_even(self.h, lat, C.byref(p), _ptr(eta_dev), _ptr(psi_dev), nrhs, st,
+                                      _stream(stream))
+        if check and rc not in (OK, ERR_NOCONV):
+            _check(rc, "oq_cgne_solve_even")
         return rc, [status_dict(s) for s in st]
 
     def cgne_batch(self, lats, etas, psis, params: SolverParams, stream=None, check=True):

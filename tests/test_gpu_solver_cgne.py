@@ -97,3 +97,30 @@ def test_cgne_nmx_reports_no_convergence():
     psi = to_dev(np.zeros_like(eta))
     rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5, sdtype=1))
     assert rc == oq.ERR_NOCONV and not st[0]["converged"] and st[0]["steps"] == 5
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 6)])
+def test_cgne_even_site_layout(dims):
+    """oq_cgne_solve_even takes and returns the even sites only (even site
+    with lexicographic index n at n // 2): the same solve, bit for bit, as
+    oq_cgne_solve on the full canonical fields."""
+    oq = _oq()
+    u, a, ainv = oracle_case(dims, 0.4, 7, 0.13, 1.0)
+    n = 3
+    eta = np.stack([dirac.even_part(e) for e in synth.make_source(dims, 330, nrhs=n)])
+    ev = (np.indices(dims).sum(axis=0).reshape(-1) % 2) == 0
+    eta_half = np.ascontiguousarray(eta.reshape(n, -1, 4, 3)[:, ev])
+    h = make_handle(dims, u, 0.13, 1.0, oq.LINK_12)
+    prm = oq.SolverParams(res=1e-10, nmx=5000, sdtype=oq.F16)
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.cgne(to_dev(eta), psi, prm, nrhs=n)
+    assert rc == oq.OK
+    psi_h = to_dev(np.zeros_like(eta_half))
+    rc2, st2 = h.cgne_even(to_dev(eta_half), psi_h, prm, nrhs=n)
+    assert rc2 == oq.OK
+    full = from_dev(psi, eta.shape).reshape(n, -1, 4, 3)
+    half = from_dev(psi_h, eta_half.shape)
+    assert np.array_equal(full[:, ev], half)
+    assert [s["steps"] for s in st] == [s["steps"] for s in st2]
+    for k in range(n):
+        assert _normal_residual(u, a, ainv, eta[k], from_dev(psi, eta.shape)[k]) <= 1.2e-10

@@ -180,3 +180,15 @@ def test_sap_eo_gcr(adaptive):
         steps[eo] = st[0]["steps"]
     if not adaptive:
         assert steps[1] <= steps[0]
+
+
+def test_sap_eo_needs_even_bs3():
+    oq = _oq()
+    dims = (4, 4, 4, 6)
+    u, a, ainv = oracle_case(dims, 0.3, 25, 0.13, 1.0)
+    h = make_handle(dims, u, 0.13, 1.0, oq.LINK_12)
+    prho, pphi = h.new_packed(oq.F32), h.new_packed(oq.F32)
+    h.pack(to_dev(synth.make_source(dims, 26)), prho, oq.F32)
+    with pytest.raises(oq.OqError):
+        h.sap_apply(prho, pphi, oq.SolverParams(ncy=1, nmr=2, bs=(2, 2, 2, 3), sap_eo=1))
+    h.sap_apply(prho, pphi, oq.SolverParams(ncy=1, nmr=2, bs=(2, 2, 2, 3)))
