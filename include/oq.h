@@ -243,7 +243,8 @@ int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, 
  * clover blocks and indices of a site are loaded once for nr right-hand sides
  * and the arithmetic runs on packed pairs of them; bx*by <= 128), a register
  * cap (regcap 0/1) of the nr > 1 kernels and of the OQ_DF64 kernel (bx*by <=
- * 128, at most 128 registers per thread), and for binary32-arithmetic kernels
+ * 128; regcap 1: at most 128 registers per thread, 2: at most 168), and for
+ * binary32-arithmetic kernels
  * on 12-real links the 18-real copy the handle keeps (fewer instructions,
  * more bytes).  oq_tune_get reports the chosen launch and its time
  * (link_fmt, nr, regcap nullable; mode 0 = Dw, 1 = Dhat pass 1, 2 = Dhat

@@ -307,9 +307,15 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
 }
 
 // double-float only: at most 128 threads and 128 registers per thread, so
-// that 16 warps fit on an SM (the tuner weighs it against hop_kernel)
+// that 16 warps fit on an SM (the tuner weighs it against hop_kernel), or
+// 168 registers for 12 warps (fewer spills)
 template <int P, int FMT, int MODE, bool DAG, int EPI>
 __global__ void __launch_bounds__(128, 4) hop_kernel_capped(const HopArgs a) {
+  extern __shared__ double red_smem[];
+  hop_kernel_body<P, FMT, MODE, DAG, EPI>(a, red_smem);
+}
+template <int P, int FMT, int MODE, bool DAG, int EPI>
+__global__ void __launch_bounds__(128, 3) hop_kernel_capped3(const HopArgs a) {
   extern __shared__ double red_smem[];
   hop_kernel_body<P, FMT, MODE, DAG, EPI>(a, red_smem);
 }
@@ -356,7 +362,10 @@ static cudaError_t launch_one(const HopLaunch& L, const HopArgs& a, cudaStream_t
   if constexpr (P == P_DF64) {
     if (L.regcap) {
       if (L.bx * L.by > 128) return cudaErrorInvalidValue;
-      hop_kernel_capped<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
+      if (L.regcap == 2)
+        hop_kernel_capped3<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
+      else
+        hop_kernel_capped<P, FMT, MODE, DAG, EPI><<<grid, block, smem, s>>>(a);
       return cudaGetLastError();
     }
   }

@@ -36,11 +36,12 @@ std::vector<TuneVal> candidates(int prec, int nrhs) {
   if (prec == P_DF64) {
     const size_t n0 = c.size();
     for (size_t k = 0; k < n0; ++k)
-      if (c[k].bx * c[k].by <= 128) {
-        TuneVal v = c[k];
-        v.regcap = 1;
-        c.push_back(v);
-      }
+      if (c[k].bx * c[k].by <= 128)
+        for (int cap = 1; cap <= 2; ++cap) {
+          TuneVal v = c[k];
+          v.regcap = cap;
+          c.push_back(v);
+        }
   }
   // several right-hand sides per thread (binary32 arithmetic types)
   if (prec == P_F32 || prec == P_BF16 || prec == P_F16) {
@@ -67,7 +68,8 @@ bool valid_shape(const LatCtx& L, int prec, int nrhs, const TuneVal& v) {
   if (v.bx < 32 || v.bx % 32 != 0 || v.by < 1 || v.by > nrhs) return false;
   if (v.nr == 1) {
     if (v.bx * v.by > 256) return false;
-    if (v.regcap != 0 && !(prec == P_DF64 && v.regcap == 1 && v.bx * v.by <= 128)) return false;
+    if (v.regcap != 0 && !(prec == P_DF64 && (v.regcap == 1 || v.regcap == 2) && v.bx * v.by <= 128))
+      return false;
   } else if (v.nr == 2 || v.nr == 4) {
     if (prec != P_F32 && prec != P_BF16 && prec != P_F16) return false;
     if (v.bx * v.by > 128 || (v.regcap != 0 && v.regcap != 1)) return false;

@@ -106,6 +106,9 @@ def test_tune_set_rejects_inadmissible_launches():
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=1, regcap=1, check=False) == oq.ERR_ARG   # cap: nr > 1 or DF64
     assert h.tune_set(oq.DF64, 1, 4, 128, 2, nr=1, regcap=1, check=False) == oq.ERR_ARG  # capped: <= 128 threads
     assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=1) == oq.OK
+    assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=2) == oq.OK
+    assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=3, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, check=False) == oq.ERR_ARG
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=4, regcap=1) == oq.OK
     assert h.tune_get(oq.F16, 1, 4)[4:] == (4, 1)
     h2 = make_handle(dims, u, 0.13, 1.0, oq.LINK_18)
@@ -113,7 +116,7 @@ def test_tune_set_rejects_inadmissible_launches():
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("cap", [0, 1])
+@pytest.mark.parametrize("cap", [0, 1, 2])
 def test_double_float_kernels_pinned(case, cap):
     """Double-float storage and arithmetic (one rhs per thread), with and
     without the register cap, pinned with oq_tune_set: Dw, Dhat and their
