@@ -263,7 +263,9 @@ int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int 
  *   residual that meets the target is confirmed by a binary64 reset before
  *   the solve stops (so the reported true residual, and the stop decision,
  *   are binary64), and a double-float value found too optimistic switches the
- *   solve to binary64 resets.  0 = every reset in binary64 (the paper's
+ *   solve to binary64 resets.  A reset whose inner solves all stopped on the
+ *   target (the recursive residual claims convergence) runs in binary64 at
+ *   once.  0 = every reset in binary64 (the paper's
  *   scheme).  On GB300, whose binary64 rate is 1/64 of its binary32 rate, a
  *   double-float reset pass is ~3x faster than a binary64 one.
  * OQ_OPT_TEST_TC_SKIP_MMA: testing aid for failure detection; 1 = the

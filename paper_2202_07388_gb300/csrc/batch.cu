@@ -519,11 +519,20 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
         rst += cs[k].mode == MODE_RESET;
       }
       if (rst) {
-        r2 = reset_step(reset_prec, true);
+        // a reset whose inner solves all stopped on the target is expected to
+        // end the solve: binary64 right away, not double-float plus confirmation
+        int rp = reset_prec;
+        if (rp == P_DF64) {
+          bool all_tol = true;
+          for (int k = 0; k < nsys; ++k)
+            if (cs[k].mode == MODE_RESET && cs[k].reason != WHY_TOL) all_tol = false;
+          if (all_tol) rp = P_F64;
+        }
+        r2 = reset_step(rp, true);
         if (r2) return r2;
         r2 = download();
         if (r2) return r2;
-        if (reset_prec == P_DF64) {
+        if (rp == P_DF64) {
           // a double-float residual may only propose convergence: confirm in binary64
           bool claims = false;
           for (int k = 0; k < nsys; ++k)

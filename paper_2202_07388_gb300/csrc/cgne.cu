@@ -12,7 +12,8 @@
 // intermediate recomputations use double-float arithmetic (~48 bits, on the
 // binary32 pipes, 3x faster than binary64 on GB300) unless
 // OQ_OPT_DF64_RESETS is 0, and a residual that meets the target is always
-// confirmed by a binary64 recomputation.  The regular steps never wait for the host:
+// confirmed by a binary64 recomputation (a reset whose inner solves stopped on
+// the target is computed in binary64 right away).  The regular steps never wait for the host:
 // alpha, beta and the reset decision are computed on the device by the last
 // CTA of each fused grid reduction; the host looks at the per-rhs state once
 // every CHUNK iterations.
@@ -328,7 +329,17 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
       continue;
     }
     if (rst) {
-      const int reset_prec = reset_prec_of();
+      int reset_prec = reset_prec_of();
+      // a reset whose inner solves all stopped on the target (their recursive
+      // residual claims convergence) is the one expected to end the solve: it
+      // is computed in binary64 directly instead of double-float followed by
+      // the binary64 confirmation
+      if (reset_prec == P_DF64) {
+        bool all_tol = true;
+        for (int k = 0; k < nrhs; ++k)
+          if (cs[k].mode == MODE_RESET && cs[k].reason != WHY_TOL) all_tol = false;
+        if (all_tol) reset_prec = P_F64;
+      }
       RK(reset_step(reset_prec, true));
       RK(download());
       if (reset_prec == P_DF64) {
