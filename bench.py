@@ -12,10 +12,11 @@ value    = algorithmic bytes of all stencil launches of the timed steps
 roofline = the dominant stencil kernel: its algorithmic bytes per launch /
            its mean CUDA-event duration, against the measured HBM copy peak
 e2e      = the same bytes / time of the public call with host buffers
-           (pinned host -> device copy of eta, solve, device -> host psi),
-           the copies of a stream of steps overlapped with the solves; the
-           serial timing of each phase, and that of the even-site layout
-           (oq_cgne_solve_even), are reported next to it
+           (pinned host -> device copy of eta, solve, device -> host psi;
+           even-site canonical fields, oq_cgne_solve_even), the copies of a
+           stream of steps overlapped with the solves; the serial timing of
+           each phase, and that of full-lattice fields (oq_cgne_solve), are
+           reported next to it
 tts      = time to solution of one right-hand side: binary64-only CGNE vs
            the mixed-precision solves (the "vs plain FP64 GPU" comparison),
            and the precision ladders (one and 12 right-hand sides)
@@ -469,31 +470,31 @@ def run_ours(args):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / args.e2e_steps
 
-    # the buffers are made right before they are used: pinned buffers made at
+    # the buffers are made right before they are used (pinned buffers made at
     # set-up, before the tuning and the timed solves, copied at 20-60 GB/s
-    # instead of ~200 GB/s on the GPU machine (either layout), for reasons outside
-    # this program
-    eta_host = eta.cpu().pin_memory()
+    # instead of ~200 GB/s on the GPU machine).  The source of the even system
+    # lives on the even sites, so the headline stream uses even-site canonical
+    # fields (oq_cgne_solve_even, half the bytes of full fields).
+    full = eta.cpu().numpy().view(np.complex128).reshape((NRHS, -1, 12))
+    lexp = np.indices(DIMS).sum(axis=0).reshape(-1) % 2
+    eta_host = torch.from_numpy(np.ascontiguousarray(full[:, lexp == 0]).view(np.float64)).pin_memory()
+    del full, lexp
     psi_hosts = [torch.empty_like(eta_host).pin_memory() for _ in range(2)]
-    eta_devs = [torch.empty_like(eta) for _ in range(2)]
-    psi_devs = [torch.empty_like(eta) for _ in range(2)]
-    solve_full = lambda e, p: h.cgne(e, p, prm, nrhs=NRHS)  # noqa: E731
-    ser_ms, ser_h2d, ser_solve, ser_d2h = e2e_time(solve_full, eta_host, eta_devs[0], psi_devs[0], psi_hosts[0])
-    e2e_ms = e2e_pipelined(solve_full, eta_host, eta_devs, psi_devs, psi_hosts)
+    eta_devs = [torch.empty(eta_host.shape, dtype=eta_host.dtype, device=eta.device) for _ in range(2)]
+    psi_devs = [torch.empty_like(eta_devs[0]) for _ in range(2)]
+    solve_even = lambda e, p: h.cgne_even(e, p, prm, nrhs=NRHS)  # noqa: E731
+    ser_ms, ser_h2d, ser_solve, ser_d2h = e2e_time(solve_even, eta_host, eta_devs[0], psi_devs[0], psi_hosts[0])
+    e2e_ms = e2e_pipelined(solve_even, eta_host, eta_devs, psi_devs, psi_hosts)
     e2e_value = (stencil_bytes / args.steps) / (e2e_ms * 1e-3) / 1e9
     e2e_bytes = int(eta_host.numel() * 8)
     del eta_devs, psi_devs, psi_hosts, eta_host
-    # the even system's fields hold the even sites only (oq_cgne_solve_even: half the bytes)
-    full = eta.cpu().numpy().view(np.complex128).reshape((NRHS, -1, 12))
-    lexp = np.indices(DIMS).sum(axis=0).reshape(-1) % 2
-    eta_host_e = torch.from_numpy(np.ascontiguousarray(full[:, lexp == 0]).view(np.float64)).pin_memory()
-    del full, lexp
-    psi_host_e = torch.empty_like(eta_host_e).pin_memory()
-    eta_dev_e = torch.empty(eta_host_e.shape, dtype=eta_host_e.dtype, device=eta.device)
-    psi_dev_e = torch.empty_like(eta_dev_e)
-    e2e_even = e2e_time(lambda e, p: h.cgne_even(e, p, prm, nrhs=NRHS), eta_host_e, eta_dev_e, psi_dev_e,
-                        psi_host_e)
-    del eta_host_e, psi_host_e, eta_dev_e, psi_dev_e
+    # full-lattice canonical fields (odd sites zero, oq_cgne_solve), serial, for comparison
+    eta_host_f = eta.cpu().pin_memory()
+    psi_host_f = torch.empty_like(eta_host_f).pin_memory()
+    eta_dev_f = torch.empty_like(eta)
+    psi_dev_f = torch.empty_like(eta)
+    e2e_full = e2e_time(lambda e, p: h.cgne(e, p, prm, nrhs=NRHS), eta_host_f, eta_dev_f, psi_dev_f, psi_host_f)
+    del eta_host_f, psi_host_f, eta_dev_f, psi_dev_f
 
     # time to solution, one rhs: binary64 only vs mixed precision
     tts = None
@@ -573,16 +574,16 @@ def run_ours(args):
             "cpu_baseline": cpu_line,
             "e2e": {"value": e2e_value, "unit": "GB/s",
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes,
-                    "ms_per_step": e2e_ms, "layout": "full-lattice canonical fields (oq_cgne_solve)",
+                    "ms_per_step": e2e_ms, "layout": "even-site canonical fields (oq_cgne_solve_even)",
                     "steps": args.e2e_steps,
                     "pipelining": "the next step's H2D and the previous step's D2H on a second stream, "
                                   "overlapping the current solve",
                     "serial": {"ms_per_step": ser_ms, "h2d_ms": ser_h2d, "solve_ms": ser_solve, "d2h_ms": ser_d2h,
                                "note": "median over steps of H2D, solve and D2H one after the other"},
-                    "serial_even_layout": {"ms_per_step": e2e_even[0], "h2d_ms": e2e_even[1],
-                                           "solve_ms": e2e_even[2], "d2h_ms": e2e_even[3],
-                                           "bytes_each_way": e2e_bytes // 2,
-                                           "note": "oq_cgne_solve_even, even-site canonical fields"}},
+                    "serial_full_layout": {"ms_per_step": e2e_full[0], "h2d_ms": e2e_full[1],
+                                           "solve_ms": e2e_full[2], "d2h_ms": e2e_full[3],
+                                           "bytes_each_way": 2 * e2e_bytes,
+                                           "note": "oq_cgne_solve, full-lattice canonical fields"}},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "solve": {"steps": [s["steps"] for s in st_last], "resets": [s["resets"] for s in st_last],

@@ -12,11 +12,11 @@
 // intermediate recomputations use double-float arithmetic (~48 bits, on the
 // binary32 pipes, 3x faster than binary64 on GB300) unless
 // OQ_OPT_DF64_RESETS is 0, and a residual that meets the target is always
-// confirmed by a binary64 recomputation (a reset whose inner solves stopped on
-// the target is computed in binary64 right away).  The regular steps never wait for the host:
-// alpha, beta and the reset decision are computed on the device by the last
-// CTA of each fused grid reduction; the host looks at the per-rhs state once
-// every CHUNK iterations.
+// confirmed by a binary64 recomputation (a reset whose inner solves stopped
+// on the target is computed in binary64 right away).  The regular steps never
+// wait for the host: alpha, beta and the reset decision are computed on the
+// device by the last CTA of each fused grid reduction; the host looks at the
+// per-rhs state once every CHUNK iterations.
 //
 // Precision ladder (Sec. 2, after Fig. 4): the storage type of the regular
 // steps may change from one inner solve to the next, e.g. binary16 until the
