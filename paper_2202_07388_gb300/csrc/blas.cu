@@ -135,7 +135,7 @@ cudaError_t cg_update_p(int prec, void* p, const void* r, long Vh, long stride, 
 // x_d += scale * x_s   (right-hand sides in MODE_RESET)
 template <int XP>
 __global__ void __launch_bounds__(256) cg_accx_kernel(char* xd, const char* xs, long Vh, long sd, long ss,
-                                                      const CgState* cg) {
+                                                      const CgState* cg, char* xdf) {
   typedef typename PrecTraits<XP>::R RX;
   const int rhs = blockIdx.y;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,15 +153,28 @@ __global__ void __launch_bounds__(256) cg_accx_kernel(char* xd, const char* xs, 
       d.c[s][c].im = fma(sc, (double)v.c[s][c].im, d.c[s][c].im);
     }
   store_spinor<P_F64>(xd + rhs * sd, Vh, i, d);
+  if (xdf) {
+    // the double-float split of the new x_d, in the binary64 layout: one
+    // (re.hi, re.lo, im.hi, im.lo) chunk where x_d holds one double2
+    float4* o = reinterpret_cast<float4*>(xdf + rhs * sd);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const double re = d.c[k / 3][k % 3].re, im = d.c[k / 3][k % 3].im;
+      const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+      o[k * Vh + i] = make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
+    }
+  }
 }
 
 cudaError_t cg_accumulate_x(int xprec, double* xd, const void* xs, long Vh, long stride_xd, long stride_xs,
-                            int nrhs, const CgState* cg, cudaStream_t s) {
+                            int nrhs, const CgState* cg, cudaStream_t s, void* xdf) {
   dim3 grid((unsigned)((Vh + 255) / 256), nrhs), block(256);
   if (xprec == P_F64)
-    cg_accx_kernel<P_F64><<<grid, block, 0, s>>>((char*)xd, (const char*)xs, Vh, stride_xd, stride_xs, cg);
+    cg_accx_kernel<P_F64><<<grid, block, 0, s>>>((char*)xd, (const char*)xs, Vh, stride_xd, stride_xs, cg,
+                                                 (char*)xdf);
   else
-    cg_accx_kernel<P_F32><<<grid, block, 0, s>>>((char*)xd, (const char*)xs, Vh, stride_xd, stride_xs, cg);
+    cg_accx_kernel<P_F32><<<grid, block, 0, s>>>((char*)xd, (const char*)xs, Vh, stride_xd, stride_xs, cg,
+                                                 (char*)xdf);
   return cudaGetLastError();
 }
 

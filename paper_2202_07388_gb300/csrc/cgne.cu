@@ -210,7 +210,6 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
   // double-float (DF64 storage has the size of binary64)
   void *xdf = nullptr, *etadf = nullptr;
   auto reset_step = [&](int rp, bool accumulate) -> int {
-    if (accumulate) KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
     const void* xin = xd;
     const void* eta_in = eta64;
     if (rp == P_DF64) {
@@ -220,9 +219,15 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
         RK(h->workspace(lat, "cg_etadf", h64 * nrhs, &etadf));
         KL(split_f64((const double*)eta64, etadf, h64 * nrhs / sizeof(double), s));
       }
-      KL(split_f64((const double*)xd, xdf, h64 * nrhs / sizeof(double), s));
+      // the accumulation writes the split of x_d as well (for the rhs being reset)
+      if (accumulate)
+        KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s, xdf));
+      else
+        KL(split_f64((const double*)xd, xdf, h64 * nrhs / sizeof(double), s));
       xin = xdf;
       eta_in = etadf;
+    } else if (accumulate) {
+      KL(cg_accumulate_x(XP, (double*)xd, xs, Vh, (long)h64, (long)hX, nrhs, h->cg_dev, s));
     }
     HopArgs a = h->hop_args(lat, rp);
     a.nrhs = nrhs;

@@ -41,8 +41,10 @@ int reduce_grid(long nsites);
 // CGNE vector kernels (gated on CgState::mode)
 cudaError_t cg_update_p(int prec, void* p, const void* r, long Vh, long stride, int nrhs, const CgState* cg,
                         cudaStream_t s);
+// xdf (optional): also write the double-float split of the new x_d (rhs in MODE_RESET)
 cudaError_t cg_accumulate_x(int xprec, double* xd, const void* xs, long Vh, long stride_xd, long stride_xs,
-                            int nrhs, const CgState* cg, cudaStream_t s);
+                            int nrhs, const CgState* cg, cudaStream_t s,
+                            void* xdf = nullptr);
 cudaError_t cg_restart(int prec, const void* rd, int rd_prec, void* rs, void* p, void* xs, int xprec, long Vh,
                        long stride_d, long stride_s, long stride_xs, int nrhs, const RedArgs& ra, cudaStream_t s);
 cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride, int nrhs, const CgState* cg,
