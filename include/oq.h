@@ -389,7 +389,7 @@ int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* p, const void* rh
 /* Instrumentation: while profiling is on, every stencil launch is bracketed
  * by CUDA events on its own stream.  oq_profile_stop() synchronises the
  * device and returns one entry per (mode, epilogue, precision, rhs per
- * thread, link format): mode 0 = full Dw, 1 = Dhat pass 1 (odd sites), 2 =
+ * thread, link format, adjoint): mode 0 = full Dw, 1 = Dhat pass 1 (odd sites), 2 =
  * Dhat pass 2 (even sites); epi 0 = plain store, 1 = store + norm, 2 = fused
  * CG update, 3 = reset residual; link_fmt -1 for binary64 / double-float
  * links; bytes = algorithmic bytes (each operand counted once) of all
@@ -399,6 +399,7 @@ typedef struct {
   double total_ms;
   double bytes;
   int nr, link_fmt;
+  int dag;  /* 1: the adjoint (Dhat^dag / Dw^dag) instantiation */
 } oq_kernel_time;
 int oq_profile_start(oq_handle h);
 /* Number of kernels the library has launched through this handle so far. */

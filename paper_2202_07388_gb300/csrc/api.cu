@@ -349,9 +349,11 @@ extern "C" int oq_profile_stop(oq_handle h, oq_kernel_time* out, int max_entries
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return OQ_ERR_CUDA;
     oq_kernel_time* t = nullptr;
     for (auto& a : agg)
-      if (a.mode == r.mode && a.epi == r.epi && a.prec == r.prec && a.nr == r.nr && a.link_fmt == r.link_fmt) t = &a;
+      if (a.mode == r.mode && a.epi == r.epi && a.prec == r.prec && a.nr == r.nr && a.link_fmt == r.link_fmt &&
+          a.dag == r.dag)
+        t = &a;
     if (!t) {
-      agg.push_back(oq_kernel_time{r.mode, r.epi, r.prec, 0, 0.0, 0.0, r.nr, r.link_fmt});
+      agg.push_back(oq_kernel_time{r.mode, r.epi, r.prec, 0, 0.0, 0.0, r.nr, r.link_fmt, r.dag});
       t = &agg.back();
     }
     t->launches += 1;

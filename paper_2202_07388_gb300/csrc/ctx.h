@@ -44,7 +44,7 @@ struct LatCtx {
 // one timed stencil launch
 struct ProfRec {
   cudaEvent_t e0, e1;
-  int mode, epi, prec, nr, link_fmt;
+  int mode, epi, prec, nr, link_fmt, dag;
   double bytes;
 };
 
@@ -326,6 +326,7 @@ struct oq_ctx {
       rec.epi = l.epi;
       rec.prec = l.prec;
       rec.nr = l.nr;
+      rec.dag = l.dagger;
       rec.link_fmt = (l.prec == oq::P_F64 || l.prec == oq::P_DF64) ? -1 : l.link_fmt;
       rec.bytes = hop_bytes(l, a);
       cudaEventRecord(rec.e0, s);

@@ -55,7 +55,8 @@ class OqStatus(C.Structure):
 
 class OqKernelTime(C.Structure):
     _fields_ = [("mode", C.c_int), ("epi", C.c_int), ("prec", C.c_int), ("launches", C.c_int),
-                ("total_ms", C.c_double), ("bytes", C.c_double), ("nr", C.c_int), ("link_fmt", C.c_int)]
+                ("total_ms", C.c_double), ("bytes", C.c_double), ("nr", C.c_int), ("link_fmt", C.c_int),
+                ("dag", C.c_int)]
 
 
 _lib = None
@@ -383,4 +384,4 @@ class Handle:
         n = C.c_int()
         _check(lib().oq_profile_stop(self.h, buf, 64, C.byref(n)), "oq_profile_stop")
         return [{"mode": b.mode, "epi": b.epi, "prec": b.prec, "launches": b.launches, "total_ms": b.total_ms,
-                 "bytes": b.bytes, "nr": b.nr, "link_fmt": b.link_fmt} for b in buf[: n.value]]
+                 "bytes": b.bytes, "nr": b.nr, "link_fmt": b.link_fmt, "dag": b.dag} for b in buf[: n.value]]

@@ -149,3 +149,24 @@ def test_double_float_kernels_pinned(case, cap):
         for k in range(n):
             ref = dirac.dw_hat_dagger(u, a, ainv, ev[k]) if dagger else dirac.dw_hat(u, a, ainv, ev[k])
             assert rel_err(got[k], ref) < TOL[4]
+
+
+def test_profile_separates_passes_and_adjoints():
+    """oq_profile_start/stop: one entry per (pass, epilogue, type, rhs per
+    thread, link format, adjoint), with its launch count and bytes."""
+    oq = _oq()
+    dims = (4, 4, 4, 4)
+    u, a, ainv = oracle_case(dims, 0.3, 1, 0.13, 1.0)
+    h = make_handle(dims, u, 0.13, 1.0, oq.LINK_12)
+    ev = dirac.even_part(synth.make_source(dims, 5))
+    pin, pout = h.new_packed(oq.F32, oq.EVEN), h.new_packed(oq.F32, oq.EVEN)
+    h.pack(to_dev(ev), pin, oq.F32, oq.EVEN)
+    h.profile_start()
+    for _ in range(3):
+        h.dw_hat(pin, pout, oq.F32)
+    h.dw_hat(pin, pout, oq.F32, dagger=True)
+    prof = h.profile_stop()
+    got = {(p["mode"], p["dag"]): p for p in prof}
+    assert got[(1, 0)]["launches"] == 3 and got[(2, 0)]["launches"] == 3
+    assert got[(1, 1)]["launches"] == 1 and got[(2, 1)]["launches"] == 1
+    assert all(p["bytes"] > 0 and p["total_ms"] > 0 for p in prof)
