@@ -125,6 +125,8 @@ typedef struct {
   double mr_avg;       /* SAP-GCR: mean MR steps per block solve */
   int ladder_steps[4]; /* CGNE: regular steps run in each storage type of the
                           precision ladder (ladder[i]; index 0 = sdtype without one) */
+  int nn_fallback;     /* oq_nn_gcr_solve: 1 if a restart cycle with the network did not halve
+                          the residual and SAP (or no preconditioner) took over */
 } oq_status;
 
 /* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no
@@ -360,7 +362,10 @@ int oq_sap_gcr_solve(oq_handle h, int lat, const oq_solver_params* p, const doub
  *   updating weights_dev in place; loss_host[step] (may be null) gets the
  *   loss before each step.  Synchronises `stream`.
  * oq_nn_gcr_solve: oq_sap_gcr_solve with M as the preconditioner of the
- *   flexible GCR instead of SAP (the network is the only preconditioner). */
+ *   flexible GCR instead of SAP.  SAP-GCR is the fallback: when a restart
+ *   cycle (nkv steps) with the network does not halve the binary64 residual,
+ *   the rest of the solve uses SAP with p->ncy, p->nmr, p->bs (no
+ *   preconditioner if p->ncy = 0) and st->nn_fallback is set. */
 int oq_nnprec_apply(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
                     void* stream);
 int oq_nnprec_grad(oq_handle h, int lat, const float* weights_dev, const void* r_dev, const void* e_dev,

@@ -582,6 +582,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
     st[k].restarts = 0;
     st[k].cycles = 0;
     st[k].mr_avg = 0.0;
+    st[k].nn_fallback = 0;
     for (int i = 0; i < 4; ++i) st[k].ladder_steps[i] = i == 0 ? cs[k].steps : 0;
     st[k].true_rel_res = eta_n[k] > 0.0 ? sqrt(cs[k].rd2) / eta_n[k] : 0.0;
     st[k].converged = (isfinite(cs[k].rd2) && st[k].true_rel_res <= prm->res) ? 1 : 0;

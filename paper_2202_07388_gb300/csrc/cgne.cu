@@ -387,6 +387,7 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
     st[k].restarts = 0;
     st[k].cycles = 0;
     st[k].mr_avg = 0.0;
+    st[k].nn_fallback = 0;
     st[k].true_rel_res = eta_n[k] > 0.0 ? sqrt(cs[k].rd2) / eta_n[k] : 0.0;
     st[k].converged = (isfinite(cs[k].rd2) && st[k].true_rel_res <= prm->res) ? 1 : 0;
     if (!isfinite(cs[k].rd2)) ret = OQ_ERR_NONFINITE;

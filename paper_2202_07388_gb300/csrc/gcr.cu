@@ -351,6 +351,11 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
     int status = 0, restarts = 0, cycles_total = 0, precs = 0;
     CK(cudaMemsetAsync(mrc, 0, sizeof(unsigned), s));
     bool nonfinite = false;
+    // the learned preconditioner, until a restart cycle fails to halve the
+    // binary64 residual: then SAP (ncy > 0) or none takes over for the rest
+    // of the solve
+    bool use_nn = nn_w != nullptr;
+    int fallback = 0;
     while (rn > tol && status < prm->nmx && !nonfinite && eta_n > 0.0) {
       KL((vec_convert_kernel<P_F64, P_F32><<<egrid, eblock, 0, s>>>((char*)rho, (const char*)rho64, Vh, hb64,
                                                                      hb32),
@@ -362,7 +367,7 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
         char* phik = (char*)Phi + (long)k * f32;
         char* chik = (char*)Chi + (long)k * f32;
         // phi_k = M rho
-        if (nn_w) {
+        if (use_nn) {
           if (h->nn_tensor_cores)
             RK(nnprec_forward_tc(h, lat, nn_w, rho, phik, s));
           else
@@ -468,9 +473,14 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
           cudaGetLastError()));
       double r2 = 0.0;
       RK(fetch(1, &r2));
+      const double rn_cycle = rn;
       rn = sqrt(r2);
       if (!isfinite(r2)) nonfinite = true;
       restarts += 1;
+      if (use_nn && !(rn <= 0.5 * rn_cycle)) {
+        use_nn = false;
+        fallback = 1;
+      }
     }
     unsigned mr_total = 0;
     CK(cudaMemcpyAsync(&mr_total, mrc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -483,7 +493,9 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
     st[r].true_rel_res = eta_n > 0.0 ? rn / eta_n : 0.0;
     st[r].converged = (!nonfinite && rn <= tol) ? 1 : 0;
     st[r].cycles = cycles_total;
-    st[r].mr_avg = (precs > 0 && nblk > 0) ? (double)mr_total / ((double)cycles_total * nblk) : 0.0;
+    st[r].nn_fallback = fallback;
+    st[r].mr_avg = (precs > 0 && cycles_total > 0 && nblk > 0) ? (double)mr_total / ((double)cycles_total * nblk)
+                                                              : 0.0;
     for (int i = 0; i < 4; ++i) st[r].ladder_steps[i] = 0;
     if (nonfinite) ret = OQ_ERR_NONFINITE;
     else if (!st[r].converged && ret == OQ_OK) ret = OQ_ERR_NOCONV;

@@ -50,7 +50,7 @@ class OqCloverParams(C.Structure):
 class OqStatus(C.Structure):
     _fields_ = [("steps", C.c_int), ("resets", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("true_rel_res", C.c_double), ("cycles", C.c_int), ("mr_avg", C.c_double),
-                ("ladder_steps", C.c_int * 4)]
+                ("ladder_steps", C.c_int * 4), ("nn_fallback", C.c_int)]
 
 
 class OqKernelTime(C.Structure):
@@ -186,7 +186,7 @@ class SolverParams:
 def status_dict(s: OqStatus) -> dict:
     return {"steps": s.steps, "resets": s.resets, "restarts": s.restarts, "converged": bool(s.converged),
             "true_rel_res": s.true_rel_res, "cycles": s.cycles, "mr_avg": s.mr_avg,
-            "ladder_steps": list(s.ladder_steps)}
+            "ladder_steps": list(s.ladder_steps), "nn_fallback": s.nn_fallback}
 
 
 class Handle:

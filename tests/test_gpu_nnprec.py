@@ -169,3 +169,41 @@ def test_trained_network_cuts_gcr_steps():
     assert rc2 == oq.OK and st2[0]["steps"] < st0[0]["steps"]   # tcgen05 network
     x2 = from_dev(psi2, eta.shape)
     assert np.linalg.norm(eta - dirac.dw(u, a, x2)) / np.linalg.norm(eta) <= 1.2e-10
+
+
+def _direct_path_network(w1, w2):
+    """Weights with only the identity path: M = w2 w1 (4x4 spin matrices)."""
+    w = np.zeros(2 * (NW1 + NW2), np.float32)
+    wc = w[0::2] + 1j * w[1::2]
+    W1 = wc[:NW1].reshape(9, 2, 1, 4, 4)
+    W2 = wc[NW1:].reshape(9, 1, 2, 4, 4)
+    W1[0, 0, 0] = w1
+    W2[0, 0, 0] = w2
+    wc = np.concatenate([W1.reshape(-1), W2.reshape(-1)])
+    w[0::2], w[1::2] = wc.real, wc.imag
+    return _wdev(w)
+
+
+def test_useless_network_falls_back_to_sap():
+    """A network whose output lies in half of the space (M = the projector
+    on the upper chirality): D M spans half the space, so a restart cycle
+    cannot halve the residual of a Gaussian source (the rest keeps ~1/sqrt(2)
+    of it); SAP takes over, the solve reaches 1e-10 and reports the fallback.
+    M = 2 kappa (a scaled identity) keeps the network for the whole solve."""
+    from paper_2202_07388_gb300 import oq
+    dims = (8, 8, 8, 8)
+    kappa = 0.1365
+    u, a, ainv = oracle_case(dims, 0.5, 95, kappa, 1.0)
+    h = make_handle(dims, u, kappa, 1.0, oq.LINK_12)
+    eta = synth.make_source(dims, 96)
+    gprm = oq.SolverParams(res=1e-10, nmx=2000, nkv=8, ncy=2, nmr=4, bs=(4, 4, 4, 4), sdtype=oq.F32)
+    wd = _direct_path_network(np.diag([1.0, 1.0, 0.0, 0.0]), np.eye(4))
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.nn_gcr(wd, to_dev(eta), psi, gprm)
+    assert rc == oq.OK and st[0]["converged"]
+    assert st[0]["nn_fallback"] == 1 and st[0]["cycles"] > 0
+    x = from_dev(psi, eta.shape)
+    assert np.linalg.norm(eta - dirac.dw(u, a, x)) / np.linalg.norm(eta) <= 1.2e-10
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.nn_gcr(_direct_path_network(np.eye(4), np.eye(4) * (2 * kappa)), to_dev(eta), psi, gprm)
+    assert rc == oq.OK and st[0]["nn_fallback"] == 0 and st[0]["cycles"] == 0
