@@ -4,7 +4,6 @@ ranks; the reference arm runs on rank 0 only."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 
