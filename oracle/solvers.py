@@ -81,14 +81,15 @@ class CgneResult:
     reset_at: list = field(default_factory=list)  # value of status at every reset step
 
 
-def precision_ladder(types=("fp16", "fp32", "fp64")):
+def precision_ladder(types=("fp16", "fp32", "fp64"), c=1.0):
     """The precision ladder of Sec. 2 (after Fig. 4): start the small-type CG
     in the first type and move to the next one once the relative residual has
-    fallen below the machine epsilon of the current type (the paper asks for
-    a threshold that scales with epsilon; the factor 1 is the reading used
-    here).  Returns (type, switch_below) pairs; the last type never switches.
+    fallen below c times the machine epsilon of the current type (the paper
+    asks for a threshold that scales with epsilon; c = 1 is the reading used
+    by default).  Returns (type, switch_below) pairs; the last type never
+    switches.
     """
-    return [(t, machine_eps(t) if k + 1 < len(types) else 0.0) for k, t in enumerate(types)]
+    return [(t, c * machine_eps(t) if k + 1 < len(types) else 0.0) for k, t in enumerate(types)]
 
 
 def cgne(apply_a, eta, res, nmx, store="fp64", delta=None, history=False,

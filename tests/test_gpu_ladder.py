@@ -148,3 +148,24 @@ def test_ladder_rejections():
     rc, _ = h.cgne_batch([0], [to_dev(eta)], [psi], oq.SolverParams(res=1e-12, nmx=100, ladder=(oq.F16,)),
                          check=False)
     assert rc == oq.ERR_ARG
+
+
+def test_ladder_switch_constant():
+    """ladder_c scales the switch thresholds (c eps of the current type): with
+    c = 100 binary16 is left after its first reset (residual ~1e-2 < 100 eps);
+    the GPU follows the oracle ladder with the same constant."""
+    oq = _oq()
+    u, a, ainv, eta = _case()
+    h = make_handle(DIMS, u, 0.13, 1.0, oq.LINK_12)
+    rc, st, x = _solve(h, eta, ladder=(oq.F16, oq.F32, oq.F64), ladder_c=100.0)
+    assert rc == oq.OK and st["converged"]
+    assert _normal_residual(u, a, ainv, eta, x) <= 1.05e-12
+    ref = solvers.cgne(lambda v: dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, v)), eta, 1e-12, 3000,
+                       ncomp=1536, ladder=solvers.precision_ladder(("fp16", "fp32", "fp64"), c=100.0))
+    assert ref.phases[0] == "fp16" and ref.phases[1] != "fp16"
+    bounds = [0] + ref.reset_at
+    per = {}
+    for i, t in enumerate(ref.phases):
+        per[t] = per.get(t, 0) + bounds[i + 1] - bounds[i]
+    for i, t in enumerate(("fp16", "fp32", "fp64")):
+        assert abs(st["ladder_steps"][i] - per.get(t, 0)) <= 2, (t, st["ladder_steps"], per)
