@@ -869,7 +869,8 @@ def run_workload_c5(args):
     h.nn_gcr(wd, eta, psi, plain)
     t, (rc, st) = _timed(lambda: h.nn_gcr(wd, eta, psi, plain))
     out["nn_gcr"] = {"s": t, "rc": rc, "steps": st[0]["steps"], "restarts": st[0]["restarts"],
-                     "true_rel_res": st[0]["true_rel_res"], "train_pairs": ntrain, "pair_solve_s": tpairs,
+                     "true_rel_res": st[0]["true_rel_res"], "nn_fallback": st[0]["nn_fallback"],
+                     "train_pairs": ntrain, "pair_solve_s": tpairs,
                      "train_steps": args.nn_steps, "train_s": ttrain, "loss_first": float(losses[0]),
                      "loss_last": float(losses[-1])}
     h.set_option(oq.OPT_NN_TENSOR_CORES, 1)
