@@ -142,3 +142,25 @@ def test_qed_clover_constant_flux_closed_form():
     a = dirac.clover_field_qed(one, au, q, m0, 2.0, cq)
     expect = (4 + m0) * np.eye(12) - 0.5 * cq * np.sin(q * theta) * np.kron(dirac.sigma_munu(mu, nu), np.eye(3))
     assert np.max(np.abs(a - expect)) < 1e-12
+
+
+def test_sf_cgne_matches_dense_solve():
+    """CGNE on the Schroedinger-functional Schur system reaches the dense
+    solution of the normal equations on the active even sites (brute force
+    on 4 x 2^3)."""
+    from oracle import solvers
+    dims = (4, 2, 2, 2)
+    u = synth.make_gauge_sf(dims, 0.4, 51)
+    a = dirac.clover_field_sf(u, dirac.kappa_to_m0(0.13), 1.0, 1.2)
+    ainv = np.linalg.inv(a)
+    eta = dirac.sf_project(dirac.even_part(synth.make_source(dims, 52)))
+    dh = lambda v: dirac.dw_hat_sf(u, a, ainv, v)
+    dhd = lambda v: dirac.dw_hat_sf_dagger(u, a, ainv, v)
+    res = solvers.cgne(lambda v: dhd(dh(v)), eta, 1e-12, 500, "fp64")
+    m = dirac.assemble_dense(dh, dims)
+    ev = _active_idx(dims, even_only=True)
+    n = m[np.ix_(ev, ev)]
+    x = np.linalg.solve(n.conj().T @ n, eta.reshape(-1)[ev])
+    assert res.converged
+    assert np.max(np.abs(res.x.reshape(-1)[ev] - x)) < 1e-9 * np.max(np.abs(x))
+    assert np.max(np.abs(res.x.reshape(-1)[~ev])) == 0.0
