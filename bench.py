@@ -7,10 +7,15 @@ bhat the even part of the source), storage binary16, arithmetic binary32,
 binary64 resets / solution / reductions, stopping at a binary64 relative
 residual of 1e-10 for every right-hand side.
 
-value    = algorithmic bytes of all stencil launches of the timed steps
-           (each operand counted once) / wall time of those steps [GB/s]
-roofline = the dominant stencil kernel: its algorithmic bytes per launch /
-           its mean CUDA-event duration, against the measured HBM copy peak
+value    = algorithmic bytes of the stencil launches of the timed steps
+           (each operand counted once; a launch's links and clover once, its
+           spinors once per right-hand side live in it, as the kernels record;
+           launches whose right-hand sides were all gated off by the solver
+           state move nothing) / wall time of those steps [GB/s]
+roofline = the dominant stencil source kernel (plain and adjoint
+           instantiations summed): its algorithmic bytes per launch / its mean
+           CUDA-event duration over launches that did work, against the
+           measured HBM copy peak
 e2e      = the same bytes / time of the public call with host buffers
            (pinned host -> device copy of eta, solve, device -> host psi;
            even-site canonical fields, oq_cgne_solve_even), the copies of a
@@ -154,6 +159,25 @@ def kernel_key(p):
     fmt = {-1: "u64", 0: "u18", 1: "u12"}[p.get("link_fmt", -1)]
     key = f"{MODE_NAMES[p['mode']]}/{EPI_NAMES[p['epi']]}/{PREC_NAMES[p['prec']]}/nr{p.get('nr', 1)}/{fmt}"
     return key + "/dag" if p.get("dag") else key
+
+
+def merge_source_kernels(prof):
+    """One entry per source kernel: the plain and adjoint instantiations of a
+    pass (the same template, the projector sign a compile-time parameter) are
+    summed; launches / total_ms / bytes / rhs_launches cover the launches with
+    live right-hand sides, gated_* the launches the solver state gated off."""
+    out = {}
+    for p in prof:
+        k = kernel_key(p)
+        k = k[:-len("/dag")] if k.endswith("/dag") else k
+        if k not in out:
+            out[k] = dict(p, dag=0, instantiations=0)
+            for f in ("launches", "total_ms", "bytes", "rhs_launches", "gated_launches", "gated_ms"):
+                out[k][f] = 0
+        for f in ("launches", "total_ms", "bytes", "rhs_launches", "gated_launches", "gated_ms"):
+            out[k][f] += p[f]
+        out[k]["instantiations"] += 1
+    return [v for v in out.values() if v["launches"] > 0]
 
 
 def traffic_for(kernel_key):
@@ -348,7 +372,12 @@ def run_ours(args):
     launches = h.kernel_launches() - n0
     t_ms = ev0.elapsed_time(ev1)
     t_ms = max_over_ranks(t_ms, "cuda", ws)
+    # bytes of launches with live right-hand sides only (links and clover once
+    # per such launch, spinors per live rhs); launches that the solver state
+    # gated off entirely move nothing and are reported apart
     stencil_bytes = sum(p["bytes"] for p in prof)
+    gated_launches = sum(p["gated_launches"] for p in prof)
+    gated_ms = sum(p["gated_ms"] for p in prof)
     value = job_throughput(sum_over_ranks(stencil_bytes, "cuda", ws), t_ms)
 
     # dominant kernel (largest share of the timed region) and the dominant
@@ -359,11 +388,12 @@ def run_ours(args):
     def roofline_of(p):
         key = kernel_key(p)
         avg = p["total_ms"] / p["launches"]
+        live = p["rhs_launches"] / p["launches"]   # mean live right-hand sides per launch
         if p["prec"] == 4:
             # double-float passes: bound by the binary32 pipe.  Binary32 operations
             # per output site and rhs of the double-float formulas (hop loop 8 x 1,200,
             # clover 3,048, scaling 48, + 264 for the sum of pass 2)
-            ops = (12696.0 if p["mode"] == 1 else 12960.0) * vh * (2 if p["mode"] == 0 else 1) * NRHS
+            ops = (12696.0 if p["mode"] == 1 else 12960.0) * vh * (2 if p["mode"] == 0 else 1) * live
             achieved = ops / (avg * 1e-3) / 1e12
             tr = traffic_for(key)
             return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS, "unit": "Top/s",
@@ -373,7 +403,7 @@ def run_ours(args):
         if p["prec"] == 0:
             # binary64 passes: bound by the FP64 pipe of GB300.  Flops per output
             # site and rhs: 1320 hopping + 504 clover (+24 for the sum of pass 2)
-            flops = (1824.0 if p["mode"] == 1 else 1848.0) * vh * (2 if p["mode"] == 0 else 1) * NRHS
+            flops = (1824.0 if p["mode"] == 1 else 1848.0) * vh * (2 if p["mode"] == 0 else 1) * live
             achieved = flops / (avg * 1e-3) / 1e12
             return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": key,
@@ -384,17 +414,21 @@ def run_ours(args):
         traffic = tr["dram_bytes_per_site"] * vh if tr else None
         # binary32 arithmetic of the same launch (stencil flops only): with many
         # right-hand sides the pass sits near the binary32 ridge
-        flops = (1824.0 if p["mode"] == 1 else 1848.0) * vh * (2 if p["mode"] == 0 else 1) * NRHS
+        flops = (1824.0 if p["mode"] == 1 else 1848.0) * vh * (2 if p["mode"] == 0 else 1) * live
         alu = flops / (avg * 1e-3) / 1e12
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": key, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                "avg_launch_ms": avg, "launches": p["launches"],
+                "avg_launch_ms": avg, "launches": p["launches"], "mean_live_rhs": live,
+                "gated_launches": p["gated_launches"],
                 "alu": {"achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu / FP32_PEAK_TFLOPS,
                         "peak_kind": "binary32 FMA rate from unit counts and the 2.07 GHz clock"}}
 
-    dom = max(prof, key=lambda p: p["total_ms"])
+    # the dominant source kernel (adjoint and plain instantiations summed), over
+    # launches that did work
+    merged = merge_source_kernels(prof)
+    dom = max(merged, key=lambda p: p["total_ms"])
     roof = roofline_of(dom)
-    small = [p for p in prof if p["prec"] not in (0, 4)]
+    small = [p for p in merged if p["prec"] not in (0, 4)]
     roof_hbm = roofline_of(max(small, key=lambda p: p["total_ms"])) if small else None
 
     # end to end through the public call with host buffers (even-site
@@ -591,9 +625,14 @@ def run_ours(args):
             "clocks": clk.summary(),
             "solve": {"steps": [s["steps"] for s in st_last], "resets": [s["resets"] for s in st_last],
                       "max_true_rel_res": max(s["true_rel_res"] for s in st_last)},
+            "stencil_bytes_per_step": stencil_bytes / args.steps,
+            "gated_launches_per_step": gated_launches / args.steps,
+            "gated_ms_per_step": gated_ms / args.steps,
             "kernels": [{"kernel": kernel_key(p),
                          "launches": p["launches"], "ms": p["total_ms"],
-                         "gbs": p["bytes"] / (p["total_ms"] * 1e-3) / 1e9} for p in prof],
+                         "gbs": p["bytes"] / (p["total_ms"] * 1e-3) / 1e9 if p["total_ms"] > 0 else None,
+                         "rhs_launches": p["rhs_launches"], "gated_launches": p["gated_launches"],
+                         "gated_ms": p["gated_ms"]} for p in prof],
             "tts": tts, "setup_s": setup_s, "tuned_shapes": tuned,
         }
         print(json.dumps(line), flush=True)

@@ -221,9 +221,17 @@ int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_dev, void* ou
  * holds until the process exits.  The caller still passes the input and
  * output fields (packed even half fields, as for oq_dw_hat_apply) and the
  * handle must already hold the gauge field and clover term.
+ *  - prec is OQ_F64, OQ_F32, OQ_BF16 or OQ_F16.  OQ_DF64 is rejected
+ *    (OQ_ERR_ARG, nothing enqueued): its kernels read double-float splits of
+ *    the links and clover that the handle allocates on their first use.
+ *  - The device that is current at the call must be the handle's device,
+ *    else OQ_ERR_STATE and nothing is enqueued (the array is per device).
  *  - nrhs * oq_spinor_bytes(h, lat, prec, OQ_EVEN) must not exceed
  *    OQ_NOALLOC_SCRATCH_BYTES, else the call returns OQ_ERR_ARG and enqueues
  *    nothing (binary32: up to 174,762 even sites for one right-hand side).
+ *  - Its two stencil launches are timed by oq_profile_start/stop like those
+ *    of oq_dw_hat_apply (the profile's records live on the host and in a
+ *    buffer that oq_profile_start allocates).
  *  - The first call made while a given device is current looks up the
  *    array's device address on that device (cudaGetSymbolAddress); make that
  *    first call before any stream capture.
@@ -392,19 +400,31 @@ int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* p, const void* rh
                  double mr_tol, void* stream);
 
 /* Instrumentation: while profiling is on, every stencil launch is bracketed
- * by CUDA events on its own stream.  oq_profile_stop() synchronises the
- * device and returns one entry per (mode, epilogue, precision, rhs per
- * thread, link format, adjoint): mode 0 = full Dw, 1 = Dhat pass 1 (odd sites), 2 =
- * Dhat pass 2 (even sites); epi 0 = plain store, 1 = store + norm, 2 = fused
- * CG update, 3 = reset residual; link_fmt -1 for binary64 / double-float
- * links; bytes = algorithmic bytes (each operand counted once) of all
- * launches. */
+ * by CUDA events on its own stream, and the kernel records how many
+ * right-hand sides were live in it (a solver launches its regular steps in
+ * chunks and gates off, on the device, every right-hand side whose state has
+ * left the step's mode).  oq_profile_stop() synchronises the device and
+ * returns one entry per (mode, epilogue, precision, rhs per thread, link
+ * format, adjoint): mode 0 = full Dw, 1 = Dhat pass 1 (odd sites), 2 = Dhat
+ * pass 2 (even sites); epi 0 = plain store, 1 = store + norm, 2 = fused CG
+ * update, 3 = reset residual; link_fmt -1 for binary64 / double-float links.
+ * launches, total_ms and bytes cover the launches with at least one live
+ * right-hand side: bytes = algorithmic bytes (each operand counted once:
+ * links and clover once per launch, spinor and epilogue vectors per live
+ * right-hand side); rhs_launches = the sum of live right-hand sides over
+ * those launches.  Launches with no live right-hand side move no operand:
+ * they are counted in gated_launches / gated_ms only.  The first 262,144
+ * launches of a profile are recorded this way, later ones count as fully
+ * live. */
 typedef struct {
   int mode, epi, prec, launches;
   double total_ms;
   double bytes;
   int nr, link_fmt;
   int dag;  /* 1: the adjoint (Dhat^dag / Dw^dag) instantiation */
+  int gated_launches;
+  double gated_ms;
+  long long rhs_launches;
 } oq_kernel_time;
 int oq_profile_start(oq_handle h);
 /* Number of kernels the library has launched through this handle so far. */

@@ -335,6 +335,13 @@ extern "C" int oq_profile_start(oq_handle h) {
     h->event_pool.push_back(r.e1);
   }
   h->prof.clear();
+  // one live-count slot per launch (1 MiB: 262,144 launches; later launches
+  // of the same profile are counted as all right-hand sides live)
+  if (!h->prof_live) {
+    const size_t n = (size_t)1 << 18;
+    if (cudaMalloc(&h->prof_live, n * sizeof(unsigned)) != cudaSuccess) return OQ_ERR_NOMEM;
+    h->prof_live_n = n;
+  }
   h->prof_on = true;
   return OQ_OK;
 }
@@ -343,6 +350,10 @@ extern "C" int oq_profile_stop(oq_handle h, oq_kernel_time* out, int max_entries
   if (!h || !n_entries || (max_entries > 0 && !out)) return OQ_ERR_ARG;
   h->prof_on = false;
   if (cudaDeviceSynchronize() != cudaSuccess) return OQ_ERR_CUDA;
+  std::vector<unsigned> live(h->prof.size() < h->prof_live_n ? h->prof.size() : h->prof_live_n);
+  if (!live.empty() &&
+      cudaMemcpy(live.data(), h->prof_live, live.size() * sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OQ_ERR_CUDA;
   std::vector<oq_kernel_time> agg;
   for (auto& r : h->prof) {
     float ms = 0.f;
@@ -353,12 +364,20 @@ extern "C" int oq_profile_stop(oq_handle h, oq_kernel_time* out, int max_entries
           a.dag == r.dag)
         t = &a;
     if (!t) {
-      agg.push_back(oq_kernel_time{r.mode, r.epi, r.prec, 0, 0.0, 0.0, r.nr, r.link_fmt, r.dag});
+      agg.push_back(oq_kernel_time{r.mode, r.epi, r.prec, 0, 0.0, 0.0, r.nr, r.link_fmt, r.dag, 0, 0.0, 0});
       t = &agg.back();
     }
-    t->launches += 1;
-    t->total_ms += ms;
-    t->bytes += r.bytes;
+    const unsigned nl = r.slot >= 0 ? live[r.slot] : (unsigned)r.nrhs;
+    if (nl == 0) {
+      // every right-hand side gated off: the launch moved no operand
+      t->gated_launches += 1;
+      t->gated_ms += ms;
+    } else {
+      t->launches += 1;
+      t->total_ms += ms;
+      t->bytes += r.fixed + r.per_rhs * nl;
+      t->rhs_launches += nl;
+    }
     h->event_pool.push_back(r.e0);
     h->event_pool.push_back(r.e1);
   }

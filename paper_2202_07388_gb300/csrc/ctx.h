@@ -41,11 +41,15 @@ struct LatCtx {
   std::map<std::string, DevBuf> ws;
 };
 
-// one timed stencil launch
+// one timed stencil launch: its algorithmic bytes are fixed (links, clover:
+// read once if any right-hand side is live) + per_rhs x (live right-hand
+// sides), the live count read back from slot `slot` of the device record
 struct ProfRec {
   cudaEvent_t e0, e1;
   int mode, epi, prec, nr, link_fmt, dag;
-  double bytes;
+  double fixed, per_rhs;
+  int nrhs;
+  long slot;  // -1: no record slot (counted as all right-hand sides live)
 };
 
 // tuned CTA shape of one stencil variant; epi = EPI_NONE is the entry for
@@ -106,6 +110,9 @@ struct oq_ctx {
   bool prof_on = false;
   std::vector<oq::ProfRec> prof;
   std::vector<cudaEvent_t> event_pool;
+  // per profiled launch: right-hand sides live in it (written by the kernel)
+  unsigned* prof_live = nullptr;
+  size_t prof_live_n = 0;
 
   int alloc(oq::DevBuf* b, size_t n) {
     if (b->n >= n && b->p) return OQ_OK;
@@ -276,8 +283,10 @@ struct oq_ctx {
     return l;
   }
 
-  // algorithmic bytes of one stencil launch (each operand counted once)
-  double hop_bytes(const oq::HopLaunch& l, const oq::HopArgs& a) {
+  // algorithmic bytes of one stencil launch (each operand counted once), as
+  // the part read once per launch (links, clover) and the part per live
+  // right-hand side (spinors and epilogue vectors)
+  void hop_bytes_parts(const oq::HopLaunch& l, const oq::HopArgs& a, double* fixed, double* per_rhs) {
     const double sp = oq::prec_bytes(l.prec);
     const bool wide = l.prec == oq::P_F64 || l.prec == oq::P_DF64;  // binary64 links and clover
     const double su = wide ? 8.0 : 4.0;
@@ -295,7 +304,15 @@ struct oq_ctx {
     if (l.epi == oq::EPI_CG) spin += (24.0 + 24.0 + 48.0 - 24.0) * sp + 48.0 * (l.prec == oq::P_F64 ? 8.0 : 4.0);
     if (l.epi == oq::EPI_RESID64) spin += 24.0 * sp;
     const double clov = 72.0 * su;
-    return sites * (spin * a.nrhs + links + clov);
+    *fixed = sites * (links + clov);
+    *per_rhs = sites * spin;
+  }
+
+  // all right-hand sides live
+  double hop_bytes(const oq::HopLaunch& l, const oq::HopArgs& a) {
+    double f = 0.0, r = 0.0;
+    hop_bytes_parts(l, a, &f, &r);
+    return f + r * a.nrhs;
   }
 
   // the binary32 link copy that matches the launch's link format
@@ -310,6 +327,7 @@ struct oq_ctx {
 
   int run_hop(const oq::HopLaunch& l, const oq::HopArgs& a, cudaStream_t s) {
     oq::ProfRec rec;
+    rec.slot = -1;
     if (prof_on) {
       if (event_pool.size() < 2) {
         for (int k = 0; k < 64; ++k) {
@@ -328,10 +346,14 @@ struct oq_ctx {
       rec.nr = l.nr;
       rec.dag = l.dagger;
       rec.link_fmt = (l.prec == oq::P_F64 || l.prec == oq::P_DF64) ? -1 : l.link_fmt;
-      rec.bytes = hop_bytes(l, a);
+      hop_bytes_parts(l, a, &rec.fixed, &rec.per_rhs);
+      rec.nrhs = a.nrhs;
+      rec.slot = prof.size() < prof_live_n ? (long)prof.size() : -1;
       cudaEventRecord(rec.e0, s);
     }
-    cudaError_t e = oq::launch_hop(l, with_links(l, a), s);
+    oq::HopArgs b = with_links(l, a);
+    b.live_rec = (prof_on && rec.slot >= 0) ? prof_live + rec.slot : nullptr;
+    cudaError_t e = oq::launch_hop(l, b, s);
     launches += 1;
     if (prof_on) {
       cudaEventRecord(rec.e1, s);
@@ -346,6 +368,7 @@ struct oq_ctx {
       for (auto* b : bs) cudaFree(b->p);
       for (auto& kv : L.ws) cudaFree(kv.second.p);
     }
+    cudaFree(prof_live);
     cudaFree(partials);
     cudaFree(counters);
     cudaFree(results);

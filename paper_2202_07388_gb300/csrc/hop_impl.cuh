@@ -291,12 +291,13 @@ __device__ __forceinline__ void hop_kernel_body(const HopArgs& a, double* red_sm
   const long i = blk * blockDim.x + threadIdx.x;
   const int rhs = tile * blockDim.y + threadIdx.y;
   const int p = (MODE == HOP_DW) ? (int)(rest & 1) : a.p;
-  bool live = (i < a.g.Vh) && (rhs < a.nrhs);
-  if (live && a.cg) live = (a.cg[rhs].mode == a.gate);
+  record_live(a);
+  const bool off = a.cg && rhs < a.nrhs && a.cg[rhs].mode != a.gate;  // gated off by the solver state
+  const bool live = (i < a.g.Vh) && (rhs < a.nrhs) && !off;
   double red = 0.0;
   if (live) red = hop_site<P, FMT, MODE, DAG, EPI>(a, i, rhs, p);
   if constexpr (EPI != EPI_NONE) {
-    grid_reduce(red, a.red, rhs, a.nrhs, red_smem, (unsigned)blk, gridDim.x / ntile);
+    grid_reduce(red, a.red, rhs, a.nrhs, red_smem, (unsigned)blk, gridDim.x / ntile, off);
   }
 }
 
@@ -335,13 +336,13 @@ __global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs* __restric
     const long blk = (MODE == HOP_DW) ? (long)(tl.y >> 1) : (long)tl.y;
     const int p = (MODE == HOP_DW) ? (tl.y & 1) : a.p;
     const long i = blk * blockDim.x + threadIdx.x;
-    bool live = i < a.g.Vh;
-    if (live && a.cg) live = (a.cg[0].mode == a.gate);
+    const bool off = a.cg && a.cg[0].mode != a.gate;  // the system is gated off by its solver state
+    const bool live = i < a.g.Vh && !off;
     double red = 0.0;
     if (live) red = hop_site<P, FMT, MODE, DAG, EPI>(a, i, 0, p);
     if constexpr (EPI != EPI_NONE) {
       const unsigned nblk = (unsigned)((a.g.Vh + blockDim.x - 1) / blockDim.x);
-      grid_reduce(red, a.red, 0, 1, red_smem, (unsigned)blk, nblk);
+      grid_reduce(red, a.red, 0, 1, red_smem, (unsigned)blk, nblk, off);
     }
   }
 }

@@ -490,9 +490,10 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
 
 // grid_reduce for NR values per thread (right-hand sides rhs0 .. rhs0+NR-1
 // of the thread's row): smem needs (blockDim.x / 32) * blockDim.y * NR doubles
+// off[k]: rhs0 + k is gated off in this launch (skipped by every CTA, see grid_reduce)
 template <int NR>
 __device__ __forceinline__ void grid_reduce_nr(const double (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
-                                               double* smem, unsigned cta, unsigned ncta) {
+                                               double* smem, unsigned cta, unsigned ncta, const bool (&off)[NR]) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nw = blockDim.x >> 5;
 #pragma unroll
@@ -505,6 +506,7 @@ __device__ __forceinline__ void grid_reduce_nr(const double (&v)[NR], const RedA
   for (int k = 0; k < NR; ++k) {
     const int rhs = rhs0 + k;
     if (rhs >= nrhs) break;
+    if (off[k]) continue;
     bool last = false;
     if (tx == 0) {
       double s = 0.0;
@@ -551,12 +553,13 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
   const uint32_t i = blk * blockDim.x + threadIdx.x;
   const int rhs0 = (int)(tile * blockDim.y + threadIdx.y) * NR;
   const int p = (MODE == HOP_DW) ? (int)(rest & 1) : a.p;
-  bool live[NR];
+  record_live(a);
+  bool live[NR], off[NR];
   bool any = false;
 #pragma unroll
   for (int k = 0; k < NR; ++k) {
-    live[k] = (i < (uint32_t)a.g.Vh) && (rhs0 + k < a.nrhs);
-    if (live[k] && a.cg) live[k] = (a.cg[rhs0 + k].mode == a.gate);
+    off[k] = a.cg && rhs0 + k < a.nrhs && a.cg[rhs0 + k].mode != a.gate;  // gated off by the solver state
+    live[k] = (i < (uint32_t)a.g.Vh) && (rhs0 + k < a.nrhs) && !off[k];
     any |= live[k];
   }
   double red[NR];
@@ -567,7 +570,7 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
 #pragma unroll
     for (int k = 0; k < NR; ++k)
       if (!live[k]) red[k] = 0.0;
-    mr::grid_reduce_nr<NR>(red, a.red, rhs0, a.nrhs, red_smem, blk, gridDim.x / ntile);
+    mr::grid_reduce_nr<NR>(red, a.red, rhs0, a.nrhs, red_smem, blk, gridDim.x / ntile, off);
   }
 }
 

@@ -46,6 +46,10 @@ extern "C" int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const voi
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
   if (!L.has_clover) return OQ_ERR_STATE;
+  // the scratch address is per device: only the handle's device may be current
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return OQ_ERR_CUDA;
+  if (cur != h->device) return OQ_ERR_STATE;
   const size_t half = (size_t)spinor_half_bytes(L.g.Vh, prec);
   if (half * (size_t)nrhs > (size_t)OQ_NOALLOC_SCRATCH_BYTES) return OQ_ERR_ARG;  // does not fit the fixed scratch
   const char* a0 = (const char*)in_dev;
@@ -63,15 +67,12 @@ extern "C" int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const voi
   a.in = in_dev;
   a.out = t;
   a.p = 1;
-  HopLaunch l1 = h->hop_launch(lat, prec, HOP_P1, dagger ? 1 : 0, EPI_NONE, nrhs);
-  if (launch_hop(l1, h->with_links(l1, a), s) != cudaSuccess) return OQ_ERR_CUDA;
+  rc = h->run_hop(h->hop_launch(lat, prec, HOP_P1, dagger ? 1 : 0, EPI_NONE, nrhs), a, s);
+  if (rc) return rc;
   // pass 2: out_e = A_ee in_e + 1/2 H_eo t_o
   a.in = t;
   a.in2 = in_dev;
   a.out = out_dev;
   a.p = 0;
-  HopLaunch l2 = h->hop_launch(lat, prec, HOP_P2, dagger ? 1 : 0, EPI_NONE, nrhs);
-  if (launch_hop(l2, h->with_links(l2, a), s) != cudaSuccess) return OQ_ERR_CUDA;
-  h->launches += 2;
-  return OQ_OK;
+  return h->run_hop(h->hop_launch(lat, prec, HOP_P2, dagger ? 1 : 0, EPI_NONE, nrhs), a, s);
 }

@@ -69,7 +69,20 @@ struct HopArgs {
   RedArgs red;
   CgState* cg;
   int lat;             // host side: lattice of the handle these arguments belong to
+  // instrumentation (nullable): CTA 0 writes the number of right-hand sides
+  // live in this launch (not gated off by their solver state)
+  unsigned* live_rec;
 };
+
+// the number of right-hand sides a launch acts on, written by one thread of CTA 0
+// before the CTA contributes to any reduction (so before any finisher runs)
+__device__ __forceinline__ void record_live(const HopArgs& a) {
+  if (a.live_rec && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    unsigned n = 0;
+    for (int r = 0; r < a.nrhs; ++r) n += (!a.cg || a.cg[r].mode == a.gate) ? 1u : 0u;
+    *a.live_rec = n;
+  }
+}
 
 struct HopLaunch {
   int prec;      // Prec of in/in2/out

@@ -70,8 +70,12 @@ __device__ __forceinline__ void run_finisher(const RedArgs& ra, int rhs, double 
 // Called by all threads of a CTA of shape (bx, by): thread (tx, ty) holds v
 // for right-hand side `rhs` (one rhs per row).  `cta` numbers this CTA among
 // the `ncta` CTAs that contribute to the same rhs.  smem needs bx*by/32 doubles.
+// off: the rhs is gated off in this launch (its solver state is not in the
+// launch's mode).  Every CTA of the launch sees the same state (it changes
+// only in the finisher of the last CTA), so all of them skip the rhs: no
+// partial, no ticket, no finisher.
 __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs, int nrhs,
-                                            double* smem, unsigned cta, unsigned ncta) {
+                                            double* smem, unsigned cta, unsigned ncta, bool off = false) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nw = blockDim.x >> 5;  // warps per rhs row (blockDim.x % 32 == 0)
   v = warp_sum(v);
@@ -80,7 +84,7 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs
   if (tx < 32) {
     bool last = false;
     double s = 0.0;
-    if (rhs < nrhs) {
+    if (rhs < nrhs && !off) {
       if (tx == 0) {
         for (int w = 0; w < nw; ++w) s += smem[ty * nw + w];
         ra.partials[(long)rhs * ncta + cta] = s;

@@ -56,7 +56,8 @@ class OqStatus(C.Structure):
 class OqKernelTime(C.Structure):
     _fields_ = [("mode", C.c_int), ("epi", C.c_int), ("prec", C.c_int), ("launches", C.c_int),
                 ("total_ms", C.c_double), ("bytes", C.c_double), ("nr", C.c_int), ("link_fmt", C.c_int),
-                ("dag", C.c_int)]
+                ("dag", C.c_int), ("gated_launches", C.c_int), ("gated_ms", C.c_double),
+                ("rhs_launches", C.c_longlong)]
 
 
 _lib = None
@@ -384,4 +385,6 @@ class Handle:
         n = C.c_int()
         _check(lib().oq_profile_stop(self.h, buf, 64, C.byref(n)), "oq_profile_stop")
         return [{"mode": b.mode, "epi": b.epi, "prec": b.prec, "launches": b.launches, "total_ms": b.total_ms,
-                 "bytes": b.bytes, "nr": b.nr, "link_fmt": b.link_fmt, "dag": b.dag} for b in buf[: n.value]]
+                 "bytes": b.bytes, "nr": b.nr, "link_fmt": b.link_fmt, "dag": b.dag,
+                 "gated_launches": b.gated_launches, "gated_ms": b.gated_ms, "rhs_launches": b.rhs_launches}
+                for b in buf[: n.value]]

@@ -73,3 +73,40 @@ def test_noalloc_rejects_requests_beyond_the_static_scratch():
     assert _call_noalloc(oq, h, oq.F64, pin, pout, nrhs, False) == oq.ERR_ARG
     assert int(pout.abs().sum()) == 0   # nothing was enqueued
     h.close()
+
+
+def test_noalloc_rejects_double_float_and_writes_nothing():
+    """OQ_DF64 needs handle-allocated double-float splits of links and clover,
+    so the entry point that must not allocate refuses it before enqueuing."""
+    import torch
+    from paper_2202_07388_gb300 import oq
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.1365, 1.3)
+    h = make_handle(dims, u, 0.1365, 1.3, oq.LINK_12)
+    half = h.spinor_bytes(oq.DF64, oq.EVEN)
+    pin = torch.ones(half, dtype=torch.uint8, device="cuda")
+    pout = torch.zeros_like(pin)
+    assert _call_noalloc(oq, h, oq.DF64, pin, pout, 1, False) == oq.ERR_ARG
+    torch.cuda.synchronize()
+    assert int(pout.abs().sum()) == 0
+    h.close()
+
+
+def test_noalloc_launches_are_profiled_like_the_allocating_ones():
+    """Both stencil passes show in the profile and in the launch count."""
+    import torch
+    from paper_2202_07388_gb300 import oq
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.1365, 1.3)
+    h = make_handle(dims, u, 0.1365, 1.3, oq.LINK_12)
+    psi = dirac.even_part(synth.make_source(dims, 600))
+    pin, pout = h.new_packed(oq.F32, oq.EVEN), h.new_packed(oq.F32, oq.EVEN)
+    h.pack(to_dev(psi), pin, oq.F32, oq.EVEN)
+    n0 = h.kernel_launches()
+    h.profile_start()
+    assert _call_noalloc(oq, h, oq.F32, pin, pout, 1, False) == oq.OK
+    prof = h.profile_stop()
+    assert h.kernel_launches() - n0 == 2
+    assert sorted(p["mode"] for p in prof) == [1, 2]
+    assert all(p["launches"] == 1 and p["bytes"] > 0 for p in prof)
+    h.close()
