@@ -82,8 +82,15 @@ typedef struct {
   int L[4];  /* L[0] = T, all extents even and >= 2 */
   int bc_t;  /* time boundary: -1 antiperiodic, +1 periodic (the fermion factor of a hop
                 across x0 = T-1 <-> 0), or 0 = Schroedinger functional (openQCD boundary
-                type 1, Sec. 2 footnote): quark fields vanish at x0 = 0 and x0 = T */
+                type 1, Sec. 2 footnote): quark fields vanish at x0 = 0 and x0 = T,
+                or OQ_BC_HALO: a time-split sub-domain (see oq_face_pack) */
 } oq_lattice;
+
+/* bc_t of a sub-domain of a lattice split along time (Sec. 3: the lattice is
+ * divided into local lattices, one per process).  Its hops across x0 = 0 and
+ * x0 = T-1 read faces received from the neighbouring sub-domains; the whole-
+ * lattice operators and solvers reject it (OQ_ERR_STATE). */
+#define OQ_BC_HALO 2
 
 /* Solver settings, after Table 2 of the paper (res, nmx, nkv, ncy, nmr, bs)
  * plus the storage type of the "small" vectors (sdtype; the "large" type and
@@ -131,7 +138,7 @@ typedef struct {
 
 /* Create a handle for nlat lattices (nlat > 1: an uneven batch).  Selects no
  * device: the current CUDA device at creation is used for every call.
- * Every extent must be even and >= 2, bc_t +1, -1 or 0, and the volume at most
+ * Every extent must be even and >= 2, bc_t +1, -1, 0 or OQ_BC_HALO, and the volume at most
  * 2^29 sites (half volume <= 2^28, so site offsets fit 32-bit arithmetic);
  * otherwise OQ_ERR_ARG. */
 int oq_create(oq_handle* h, const oq_lattice* lats, int nlat);
@@ -253,7 +260,10 @@ int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, 
  * clover blocks and indices of a site are loaded once for nr right-hand sides
  * and the arithmetic runs on packed pairs of them; bx*by <= 128), a register
  * cap (regcap 0/1) of the nr > 1 kernels and of the OQ_DF64 kernel (bx*by <=
- * 128; regcap 1: at most 128 registers per thread, 2: at most 168), and for
+ * 128; regcap 1: at most 128 registers per thread, 2: at most 168), for the
+ * nr > 1 kernels regcap 2: the cap of 1 with each hop's neighbour spinors and
+ * link copied ahead into shared memory while the previous hop is computed
+ * (12-real links only), and for
  * binary32-arithmetic kernels
  * on 12-real links the 18-real copy the handle keeps (fewer instructions,
  * more bytes).  oq_tune_get reports the chosen launch and its time
@@ -302,6 +312,83 @@ int oq_norm2(oq_handle h, int lat, int prec, int subset, const void* x_dev, int 
              double* out_host, void* stream);
 int oq_dot(oq_handle h, int lat, int prec, int subset, const void* x_dev, const void* y_dev,
            int nrhs, double* out_host, void* stream);
+
+/* ---- Time-split sub-domains (Sec. 3: one local lattice per process) ----
+ *
+ * A lattice of global extent T x L1 x L2 x L3 split along time into R parts
+ * of T_loc = T / R slices (T_loc even) is handled as R sub-domain lattices
+ * (bc_t = OQ_BC_HALO, extents T_loc x L1 x L2 x L3; even-odd parities of the
+ * sub-domain are the global ones since T_loc is even).  Every application of
+ * the operator exchanges two faces per sub-domain and output parity, 12 reals
+ * per boundary site (the spin projection halves the spinor):
+ *   to_prev: (1 -/+ g0) psi on the sub-domain's x0 = 0 slice, which the
+ *            previous sub-domain's forward time hops from its last slice read;
+ *   to_next: U_0(x)^dag (1 +/- g0) psi(x) on the x0 = T_loc-1 slice, which the
+ *            next sub-domain's backward time hops from its first slice read
+ *            (the link lives on the sender, so the sender applies it);
+ * (upper signs for Dw, lower for the adjoint).  A face of one parity and one
+ * right-hand side is oq_face_bytes(): L1 L2 L3 / 2 sites of 6 complex numbers
+ * in the arithmetic type (binary64 for OQ_F64, binary32 for OQ_F32 / BF16 /
+ * F16), 16-byte chunks stored chunk-major.  Moving the faces between
+ * sub-domains (device copies, NCCL or any transport) is the caller's; the
+ * library packs and consumes them.  OQ_DF64 has no sub-domain form. */
+
+/* Links of a sub-domain: U_ext_dev holds the canonical binary64 links of
+ * T_loc + 2 time slices (global slices t0 - 1, t0, ..., t0 + T_loc, periodic
+ * in the global lattice), so that the clover term of every interior site
+ * has all its plaquette leaves.  The hopping term uses the interior slices;
+ * oq_clover_build then builds the clover on the extended lattice and keeps
+ * the interior (plain c_sw; cF and the QED split are rejected).  OQ_ERR_STATE
+ * unless the lattice was created with bc_t = OQ_BC_HALO. */
+int oq_gauge_upload_halo(oq_handle h, int lat, const double* U_ext_dev, int link_fmt, void* stream);
+
+/* Bytes of one face (one output parity, one right-hand side); 0 for an
+ * invalid lattice or precision (OQ_DF64 included). */
+size_t oq_face_bytes(oq_handle h, int lat, int prec);
+
+/* Pack the two faces of packed input fields for their neighbours (see above).
+ * subset OQ_EVEN / OQ_ODD: in_dev holds nrhs half fields of that parity and
+ * the faces serve the output parity 1 - subset: face k of to_prev_dev /
+ * to_next_dev at k * oq_face_bytes().  subset OQ_FULL: in_dev holds full
+ * fields and the faces of output parity p are at (p * nrhs + k) *
+ * oq_face_bytes().  dagger selects the adjoint's projectors.  Asynchronous. */
+int oq_face_pack(oq_handle h, int lat, int prec, int subset, const void* in_dev, int nrhs, int dagger,
+                 void* to_prev_dev, void* to_next_dev, void* stream);
+
+/* The faces a sub-domain received: from_next = the next sub-domain's to_prev,
+ * from_prev = the previous one's to_next (device pointers, the layout of
+ * oq_face_pack), and the boundary factor of the hops across each face (+1, or
+ * -1 on the global antiperiodic time boundary: the hop from x0 = T-1 of the
+ * last sub-domain to x0 = 0 of the first, and back). */
+typedef struct {
+  const void* from_next;
+  const void* from_prev;
+  double sign_next, sign_prev;
+} oq_halo;
+
+/* out = D in (or D^dag) on a sub-domain: oq_dw_apply with the time hops that
+ * leave the sub-domain taken from the faces (packed from the full input
+ * fields by the neighbours with subset OQ_FULL).  OQ_F64 / F32 / BF16 / F16. */
+int oq_dw_apply_halo(oq_handle h, int lat, int prec, const void* in_dev, void* out_dev, int nrhs, int dagger,
+                     const oq_halo* halo, void* stream);
+
+/* One pass of Dhat = D_ee - D_eo D_oo^-1 D_oe (the two passes of
+ * oq_dw_hat_apply, Sec. 3 even-odd ordering):
+ *   pass 1: out_o = A_oo^-1 (-1/2 H_oe in_e)          (in: even half fields)
+ *   pass 2: out_e = A_ee in2_e + 1/2 H_eo in_o         (in: odd, in2: even)
+ * so that Dhat in_e = pass2(pass1(in_e), in_e).  halo: the faces of the input
+ * field of the pass (packed with subset OQ_EVEN for pass 1, OQ_ODD for pass
+ * 2); required on a sub-domain, NULL on a whole lattice (periodic or
+ * antiperiodic wrap as for oq_dw_hat_apply).  in and out must not overlap. */
+int oq_dhat_pass(oq_handle h, int lat, int prec, int pass, const void* in_dev, const void* in2_dev, void* out_dev,
+                 int nrhs, int dagger, const oq_halo* halo, void* stream);
+
+/* y_k = a_host[k] x_k + b_host[k] y_k for right-hand side k < nrhs (<= 64),
+ * on packed OQ_F64 or OQ_F32 fields of the subset: the vector step of a
+ * solver driven from the host (the distributed CGNE over sub-domains).
+ * Asynchronous. */
+int oq_axpby(oq_handle h, int lat, int prec, int subset, const double* a_host, const void* x_dev,
+             const double* b_host, void* y_dev, int nrhs, void* stream);
 
 /* CGNE with reset steps (Sec. 2, Fig. 4): solves Dhat^dag Dhat psi = eta on
  * the even sites.  eta_dev / psi_dev: canonical binary64 full-lattice fields

@@ -56,7 +56,8 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
   for (int k = 0; k < nlat; ++k) {
     for (int mu = 0; mu < 4; ++mu)
       if (lats[k].L[mu] < 2 || (lats[k].L[mu] & 1)) return OQ_ERR_ARG;
-    if (lats[k].bc_t != 1 && lats[k].bc_t != -1 && lats[k].bc_t != 0) return OQ_ERR_ARG;
+    if (lats[k].bc_t != 1 && lats[k].bc_t != -1 && lats[k].bc_t != 0 && lats[k].bc_t != OQ_BC_HALO)
+      return OQ_ERR_ARG;
     const double v = (double)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3];
     if (v > (double)(1L << 29)) return OQ_ERR_ARG;  // Vh <= 2^28: 32-bit site offsets
   }
@@ -72,7 +73,8 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
     for (int mu = 0; mu < 4; ++mu) L.g.L[mu] = lats[k].L[mu];
     L.g.Lh3 = lats[k].L[3] / 2;
     L.g.Vh = (long)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3] / 2;
-    L.g.bc_t = (float)lats[k].bc_t;
+    L.halo_t = lats[k].bc_t == OQ_BC_HALO;
+    L.g.bc_t = L.halo_t ? 1.0f : (float)lats[k].bc_t;  // a sub-domain's boundary factors come with its faces
     geom_init_div(L.g);
   }
   *out = h;
@@ -136,6 +138,7 @@ static int gauge_upload(oq_handle h, int lat, const double* U_dev, const double*
   L.has_gauge = true;
   L.has_clover = false;
   L.df_ready = false;
+  L.has_uext = false;
   return OQ_OK;
 }
 
@@ -147,6 +150,41 @@ extern "C" int oq_gauge_upload_qed(oq_handle h, int lat, const double* U_dev, co
                                    void* stream) {
   if (!A_dev) return OQ_ERR_ARG;
   return gauge_upload(h, lat, U_dev, A_dev, q, OQ_LINK_18, stream);
+}
+
+// Clover term of a sub-domain: built on the extended lattice (T_loc + 2
+// slices) into scratch, then slice s + 1 of the extended parity 1 - q is
+// slice s of parity q (one slice shifts the parity; the eo index shifts by
+// the Fs = Vh / T_loc sites of a slice).  Blocks of A and A^{-1}: 36 (binary64)
+// or 18 (binary32) chunks of 16 bytes per parity.
+static int clover_build_halo(oq_handle h, int lat, double kappa, double csw, cudaStream_t s) {
+  LatCtx& L = h->lats[lat];
+  const Geom ge = halo_ext_geom(L.g);
+  const long Fs = L.g.Vh / L.g.L[0];
+  void *a64, *a32, *i64, *i32;
+  const size_t n64 = sizeof(double) * 2 * 72 * ge.Vh, n32 = sizeof(float) * 2 * 72 * ge.Vh;
+  int rc = h->workspace(lat, "clov_ext_a64", n64, &a64);
+  if (!rc) rc = h->workspace(lat, "clov_ext_a32", n32, &a32);
+  if (!rc) rc = h->workspace(lat, "clov_ext_i64", n64, &i64);
+  if (!rc) rc = h->workspace(lat, "clov_ext_i32", n32, &i32);
+  if (rc) return rc;
+  if (build_clover(ge, (const double*)L.uext.p, nullptr, 0.0, 0, kappa, csw, 0.0, 1.0, (double*)a64, (float*)a32,
+                   (double*)i64, (float*)i32, h->status_dev, s) != cudaSuccess)
+    return OQ_ERR_CUDA;
+  struct Part {
+    void* dst;
+    const void* src;
+    int nch;
+  } parts[] = {{L.a64.p, a64, 36}, {L.i64.p, i64, 36}, {L.a32.p, a32, 18}, {L.i32.p, i32, 18}};
+  for (const Part& pt : parts)
+    for (int q = 0; q < 2; ++q) {
+      char* d = (char*)pt.dst + (size_t)q * pt.nch * L.g.Vh * 16;
+      const char* src = (const char*)pt.src + ((size_t)(1 - q) * pt.nch * ge.Vh + Fs) * 16;
+      if (cudaMemcpy2DAsync(d, (size_t)L.g.Vh * 16, src, (size_t)ge.Vh * 16, (size_t)L.g.Vh * 16, pt.nch,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return OQ_ERR_CUDA;
+    }
+  return OQ_OK;
 }
 
 extern "C" int oq_clover_build(oq_handle h, int lat, double kappa, double csw, void* stream) {
@@ -177,11 +215,20 @@ extern "C" int oq_clover_build_ex(oq_handle h, int lat, const oq_clover_params* 
   if (!rc) rc = h->ensure_scratch();
   if (rc) return rc;
   if (cudaMemsetAsync(h->status_dev, 0, sizeof(int), s) != cudaSuccess) return OQ_ERR_CUDA;
-  const double* links = L.uclov_valid ? (const double*)L.uclov.p : (const double*)L.u64.p;
-  if (build_clover(L.g, links, L.has_u1 ? (const double*)L.au1.p : nullptr, L.qcharge, prm->qed_split, kappa, csw,
-                   prm->csw_qed, prm->cF, (double*)L.a64.p, (float*)L.a32.p, (double*)L.i64.p, (float*)L.i32.p,
-                   h->status_dev, s) != cudaSuccess)
-    return OQ_ERR_CUDA;
+  if (L.halo_t) {
+    // sub-domain: build on the lattice extended by one slice on each side
+    // (every plaquette leaf of an interior site is there), keep the interior
+    if (!L.has_uext) return OQ_ERR_STATE;
+    if (prm->qed_split || prm->cF != 1.0) return OQ_ERR_ARG;
+    rc = clover_build_halo(h, lat, kappa, csw, s);
+    if (rc) return rc;
+  } else {
+    const double* links = L.uclov_valid ? (const double*)L.uclov.p : (const double*)L.u64.p;
+    if (build_clover(L.g, links, L.has_u1 ? (const double*)L.au1.p : nullptr, L.qcharge, prm->qed_split, kappa, csw,
+                     prm->csw_qed, prm->cF, (double*)L.a64.p, (float*)L.a32.p, (double*)L.i64.p, (float*)L.i32.p,
+                     h->status_dev, s) != cudaSuccess)
+      return OQ_ERR_CUDA;
+  }
   int st = 0;
   if (cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return OQ_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return OQ_ERR_CUDA;
@@ -235,7 +282,7 @@ extern "C" int oq_dw_apply(oq_handle h, int lat, int prec, const void* in_dev, v
                            void* stream) {
   if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 4 || nrhs < 1) return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // a sub-domain needs oq_dw_apply_halo
   const size_t full = oq_spinor_bytes(h, lat, prec, OQ_FULL);
   if (overlap(in_dev, out_dev, full * nrhs)) return OQ_ERR_ARG;
   if (prec == P_DF64) {
@@ -257,7 +304,7 @@ extern "C" int oq_dw_hat_apply(oq_handle h, int lat, int prec, const void* in_de
                                void* stream) {
   if (!valid_lat(h, lat) || !in_dev || !out_dev || prec < 0 || prec > 4 || nrhs < 1) return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // a sub-domain needs oq_dhat_pass with faces
   const size_t half = oq_spinor_bytes(h, lat, prec, OQ_EVEN);
   if (overlap(in_dev, out_dev, half * nrhs)) return OQ_ERR_ARG;
   void* t = nullptr;

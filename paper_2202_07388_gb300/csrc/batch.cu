@@ -171,7 +171,7 @@ extern "C" int oq_cgne_solve_batch(oq_handle h, int nsys, const int* lats, const
   for (int s = 0; s < nsys; ++s) {
     if (lats[s] < 0 || lats[s] >= (int)h->lats.size() || !eta_dev[s] || !psi_dev[s]) return OQ_ERR_ARG;
     const LatCtx& L = h->lats[lats[s]];
-    if (!L.has_clover) return OQ_ERR_STATE;
+    if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
     if (fmt < 0) fmt = L.link_fmt;
     if (L.link_fmt != fmt) return OQ_ERR_ARG;  // one link format per batch (one kernel instantiation)
   }

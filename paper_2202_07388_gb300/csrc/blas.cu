@@ -277,4 +277,38 @@ cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride1
   return cudaGetLastError();
 }
 
+// y = a_k x + b_k y for right-hand side k (real coefficients), on the reals
+// of packed binary64 or binary32 fields (the layout is irrelevant: every
+// real is scaled the same way); n reals per right-hand side
+struct AxpbyCoef {
+  double a[64], b[64];
+};
+template <typename R>
+__global__ void __launch_bounds__(256) axpby_kernel(const R* x, R* y, long n, const AxpbyCoef c) {
+  const int rhs = blockIdx.y;
+  const R a = (R)c.a[rhs], b = (R)c.b[rhs];
+  const R* xr = x + rhs * n;
+  R* yr = y + rhs * n;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+    yr[k] = fma(a, xr[k], b * yr[k]);
+}
+
+cudaError_t axpby(int prec, const double* a, const void* x, const double* b, void* y, long n, int nrhs,
+                  cudaStream_t s) {
+  if (nrhs < 1 || nrhs > 64) return cudaErrorInvalidValue;
+  AxpbyCoef c;
+  for (int k = 0; k < nrhs; ++k) {
+    c.a[k] = a[k];
+    c.b[k] = b[k];
+  }
+  dim3 grid(reduce_grid(n / 24 + 1), nrhs), block(256);
+  if (prec == P_F64)
+    axpby_kernel<double><<<grid, block, 0, s>>>((const double*)x, (double*)y, n, c);
+  else if (prec == P_F32)
+    axpby_kernel<float><<<grid, block, 0, s>>>((const float*)x, (float*)y, n, c);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 }  // namespace oq

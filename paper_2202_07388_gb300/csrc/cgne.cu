@@ -16,7 +16,12 @@
 // on the target is computed in binary64 right away).  The regular steps never
 // wait for the host: alpha, beta and the reset decision are computed on the
 // device by the last CTA of each fused grid reduction; the host looks at the
-// per-rhs state once every CHUNK iterations.
+// per-rhs state after a chunk of iterations.  The chunk is the number of
+// steps left until the earliest predicted end of an inner solve (its length
+// predicted as one less than the previous inner solve of that rhs; at most
+// CHUNK, at least 1): an iteration launched after every rhs has stopped is
+// gated off on the device and does nothing, but still costs the launch of
+// every CTA, while a look at the state costs one small copy.
 //
 // Precision ladder (Sec. 2, after Fig. 4): the storage type of the regular
 // steps may change from one inner solve to the next, e.g. binary16 until the
@@ -44,7 +49,7 @@ using namespace oq;
 
 namespace {
 
-const int CHUNK = 8;
+const int CHUNK = 8;   // chunk length before a rhs has a previous inner solve, and the maximum
 
 // unit of least precision at 1 of a storage type (0 for binary64 storage)
 double type_eps(int prec) {
@@ -74,7 +79,7 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
   const int nphase = (int)phase_prec.size();
   int phase = 0;
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
   cudaStream_t s = (cudaStream_t)stream;
   const long Vh = L.g.Vh;
   // small type of the current phase (P), its solution type (XP) and sizes;
@@ -289,7 +294,15 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
   // A binary64 phase resets in binary64 (its inner solve reaches the target).
   bool df_ok = h->df64_resets;
   auto reset_prec_of = [&]() { return (P != P_F64 && df_ok) ? P_DF64 : P_F64; };
+  // steps of each rhs at the start of its current inner solve, and the
+  // length of its previous inner solve (0: none yet)
+  std::vector<int> inner_start(nrhs, 0), inner_len(nrhs, 0);
+  auto mark_starts = [&]() {
+    for (int k = 0; k < nrhs; ++k)
+      if (cs[k].mode == MODE_RESET) inner_start[k] = cs[k].steps;
+  };
   int pending = decide(false);
+  mark_starts();
   RK(upload());
   if (pending) RK(restart());
   for (;;) {
@@ -329,11 +342,14 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
         RK(download());
       }
       pending = decide(false);
+      mark_starts();
       RK(upload());
       if (pending) RK(restart());
       continue;
     }
     if (rst) {
+      for (int k = 0; k < nrhs; ++k)
+        if (cs[k].mode == MODE_RESET) inner_len[k] = cs[k].steps - inner_start[k];
       int reset_prec = reset_prec_of();
       // a reset whose inner solves all stopped on the target (their recursive
       // residual claims convergence) is the one expected to end the solve: it
@@ -366,12 +382,20 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
         }
       }
       pending = decide(true);
+      mark_starts();
       RK(upload());
       if (pending) RK(restart());
       continue;
     }
     if (!run) break;
-    for (int k = 0; k < CHUNK; ++k) RK(iteration());
+    int chunk = CHUNK;
+    for (int k = 0; k < nrhs; ++k) {
+      if (cs[k].mode != MODE_RUN || inner_len[k] == 0) continue;
+      int left = inner_len[k] - 1 - (cs[k].steps - inner_start[k]);
+      left = left < 1 ? 1 : left;
+      chunk = left < chunk ? left : chunk;
+    }
+    for (int k = 0; k < chunk; ++k) RK(iteration());
   }
 
   // psi = x_d on the even sites, zero on the odd sites

@@ -37,6 +37,11 @@ struct LatCtx {
   // and the packed U(1) angles with their charge
   DevBuf uclov, au1;
   bool uclov_valid = false, has_u1 = false;
+  // time-split sub-domain (OQ_BC_HALO): its time hops across x0 = 0 / T-1
+  // read faces of the neighbouring sub-domains; uext holds the packed binary64
+  // links of the sub-domain extended by one slice on each side (clover build)
+  bool halo_t = false, has_uext = false;
+  DevBuf uext;
   double qcharge = 0.0, cF = 1.0, csw_qed = 0.0;
   std::map<std::string, DevBuf> ws;
 };
@@ -364,7 +369,8 @@ struct oq_ctx {
 
   void release() {
     for (auto& L : lats) {
-      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18, &L.udf, &L.adf, &L.idf, &L.uclov, &L.au1};
+      oq::DevBuf* bs[] = {&L.u64, &L.u32, &L.a64, &L.a32, &L.i64, &L.i32, &L.u32_18, &L.udf, &L.adf, &L.idf, &L.uclov, &L.au1,
+                          &L.uext};
       for (auto* b : bs) cudaFree(b->p);
       for (auto& kv : L.ws) cudaFree(kv.second.p);
     }

@@ -212,7 +212,7 @@ extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, c
       (prm->sap_eo != 0 && prm->sap_eo != 1) || (prm->sap_eo && prm->bs[3] % 2))
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
   int bvol = 1;
   for (int mu = 0; mu < 4; ++mu) {
     const int b = prm->bs[mu];
@@ -256,7 +256,7 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
     return OQ_ERR_ARG;
   if (prm->sdtype != OQ_F32) return OQ_ERR_ARG;  // SAP and the Krylov vectors run in binary32
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
   int nblk = 1, bvol = 1;
   if (prm->ncy > 0) {
     for (int mu = 0; mu < 4; ++mu) {

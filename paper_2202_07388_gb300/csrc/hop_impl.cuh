@@ -40,36 +40,55 @@ __device__ __forceinline__ void hop_accum(Spinor<R>& acc, HalfSpinor<R>& t, R w,
   }
 }
 
+// fnext / fprev (sub-domain launches, this rhs and output parity): the time
+// faces that replace the hops leaving the sub-domain (HopArgs::halo_next)
 template <int P, int FMT, int MU, bool DAG>
 __device__ __forceinline__ void hop_dir(const HopArgs& a, const char* in, int p, long i, const int x[4],
                                         Spinor<typename PrecTraits<P>::R>& acc,
-                                        typename PrecTraits<P>::R w) {
+                                        typename PrecTraits<P>::R w, const char* fnext = nullptr,
+                                        const char* fprev = nullptr) {
   typedef typename PrecTraits<P>::R R;
   constexpr int SF = DAG ? +1 : -1;  // projector sign of the forward hop
   bool cr;
   // forward: U_mu(x) (1 -/+ g) psi(x + mu)
   {
     long j = eo_neighbour(a.g, x, MU, +1, &cr);
-    Spinor<R> nb;
-    load_spinor<P>(in, a.g.Vh, j, nb);
     HalfSpinor<R> h, t;
-    project<MU, SF>(nb, h);
+    float sg = a.g.bc_t;
+    if (MU == 0 && cr && fnext) {
+      // x0 = T-1: the projected neighbour comes from the next sub-domain
+      const long Fs = a.g.Vh / a.g.L[0];
+      load_half<R>(fnext, Fs, i - (long)x[0] * Fs, h);
+      sg = a.halo_sign_next;
+    } else {
+      Spinor<R> nb;
+      load_spinor<P>(in, a.g.Vh, j, nb);
+      project<MU, SF>(nb, h);
+    }
     Su3<R> u;
     load_link<R, FMT>(a.links, a.g.Vh, p, MU, i, u);
     su3_mul(u, h, t);
-    hop_accum<MU, SF>(acc, t, w, cr, a.g.bc_t);
+    hop_accum<MU, SF>(acc, t, w, cr, sg);
   }
   // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
   {
     long j = eo_neighbour(a.g, x, MU, -1, &cr);
-    Spinor<R> nb;
-    load_spinor<P>(in, a.g.Vh, j, nb);
-    HalfSpinor<R> h, t;
-    project<MU, -SF>(nb, h);
-    Su3<R> u;
-    load_link<R, FMT>(a.links, a.g.Vh, 1 - p, MU, j, u);
-    su3_dag_mul(u, h, t);
-    hop_accum<MU, -SF>(acc, t, w, cr, a.g.bc_t);
+    HalfSpinor<R> t;
+    float sg = a.g.bc_t;
+    if (MU == 0 && cr && fprev) {
+      // x0 = 0: link and projection were applied by the previous sub-domain
+      load_half<R>(fprev, a.g.Vh / a.g.L[0], i, t);
+      sg = a.halo_sign_prev;
+    } else {
+      Spinor<R> nb;
+      load_spinor<P>(in, a.g.Vh, j, nb);
+      HalfSpinor<R> h;
+      project<MU, -SF>(nb, h);
+      Su3<R> u;
+      load_link<R, FMT>(a.links, a.g.Vh, 1 - p, MU, j, u);
+      su3_dag_mul(u, h, t);
+    }
+    hop_accum<MU, -SF>(acc, t, w, cr, sg);
   }
 }
 
@@ -189,7 +208,14 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
     if constexpr (DF) {
       hop_loop_df<P, FMT, DAG>(a, in, p, i, x, acc);
     } else {
-      hop_dir<P, FMT, 0, DAG>(a, in, p, i, x, acc, w);
+      const char* fn = nullptr;
+      const char* fp = nullptr;
+      if (a.halo_next) {  // sub-domain launch: faces of this rhs and output parity
+        const long po = (MODE == HOP_DW) ? (long)p * a.halo_pstride : 0;
+        fn = (const char*)a.halo_next + rhs * a.halo_stride + po;
+        fp = (const char*)a.halo_prev + rhs * a.halo_stride + po;
+      }
+      hop_dir<P, FMT, 0, DAG>(a, in, p, i, x, acc, w, fn, fp);
       hop_dir<P, FMT, 1, DAG>(a, in, p, i, x, acc, w);
       hop_dir<P, FMT, 2, DAG>(a, in, p, i, x, acc, w);
       hop_dir<P, FMT, 3, DAG>(a, in, p, i, x, acc, w);

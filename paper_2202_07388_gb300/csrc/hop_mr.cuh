@@ -126,6 +126,28 @@ struct RawSp {
   }
 };
 
+// Per-thread staging of the next hop's operands in shared memory: 16-byte
+// asynchronous copies (cp.async) that hold no register while in flight.  A
+// thread reads back only the slots it filled itself, so waiting for its own
+// copy groups suffices (no barrier).  Slot k of stage st of thread tid is
+// stg[(st * nslot + k) * nthr + tid]: a warp reads 512 contiguous bytes.
+__device__ __forceinline__ void cp16(uint4* smem, const void* gmem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+struct Stage {
+  uint4* base;
+  uint32_t nthr, tid;
+  __device__ __forceinline__ uint4* at(int st, int k, int nslot) const {
+    return base + (size_t)((uint32_t)(st * nslot + k) * nthr + tid);
+  }
+};
+
 __device__ __forceinline__ void join(const Spinor<float>& a, const Spinor<float>& b, Sp2& s) {
 #pragma unroll
   for (int k = 0; k < 4; ++k)
@@ -169,6 +191,19 @@ __device__ __forceinline__ void load_u(const void* base, uint32_t Vh, int p, int
     u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
     u.m[2][2] = conj(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
   }
+}
+
+// 12-real link from its three 16-byte chunks (rows 0, 1 stored, row 2 rebuilt)
+__device__ __forceinline__ void link12_from(const float4 a0, const float4 a1, const float4 a2, Su3<float>& u) {
+  u.m[0][0] = {a0.x, a0.y};
+  u.m[0][1] = {a0.z, a0.w};
+  u.m[0][2] = {a1.x, a1.y};
+  u.m[1][0] = {a1.z, a1.w};
+  u.m[1][1] = {a2.x, a2.y};
+  u.m[1][2] = {a2.z, a2.w};
+  u.m[2][0] = conj(u.m[0][1] * u.m[1][2] - u.m[0][2] * u.m[1][1]);
+  u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
+  u.m[2][2] = conj(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
 }
 
 // acc[.][a] += wt * reconstruction (projector 1 -/+ g_mu, S = -1 / +1) of
@@ -282,6 +317,21 @@ __device__ __forceinline__ void load_blk(const void* base, uint32_t Vh, int p, i
   for (int c = 0; c < 15; ++c) k.off[c] = cx<float>{r[6 + 2 * c], r[7 + 2 * c]};
 }
 
+__device__ __forceinline__ void blk_from(const float4 (&w)[9], Blk& k) {
+  float r[36];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    r[4 * c] = w[c].x;
+    r[4 * c + 1] = w[c].y;
+    r[4 * c + 2] = w[c].z;
+    r[4 * c + 3] = w[c].w;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) k.d[c] = r[c];
+#pragma unroll
+  for (int c = 0; c < 15; ++c) k.off[c] = cx<float>{r[6 + 2 * c], r[7 + 2 * c]};
+}
+
 // y = K x for one block (x, y: the 6 components 3*spin_local + colour)
 __device__ __forceinline__ void blk_apply(const Blk& k, const C2* x, C2* y) {
 #pragma unroll
@@ -316,9 +366,14 @@ __device__ __forceinline__ void coords(const Geom& g, int p, uint32_t i, int x[4
 }
 
 // Per-thread work of hop_mr_kernel: the NR/2 lane pairs of one output site.
-template <int P, int FMT, int MODE, bool DAG, int EPI, int NR>
+// PF: the operands of hop k + 1 (neighbour spinors of the NR right-hand
+// sides and the 12-real link) are copied into the thread's shared-memory
+// stage (k + 1) % 2 while hop k is computed, and pass 1 stages its inverse
+// clover blocks the same way (stg: 2 stages of NR * chunks + 3 slots).
+template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, bool PF>
 __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int p, const bool (&live)[NR],
-                                     double (&red)[NR]) {
+                                     double (&red)[NR], const Stage& stg) {
+  static_assert(!PF || FMT == LINK_12, "staged hops read 12-real links");
   constexpr int NP = NR / 2;
   constexpr int SF = DAG ? +1 : -1;  // projector sign of the forward hop
   const Geom& g = a.g;
@@ -355,6 +410,34 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
     const int r = rhs0 + k < a.nrhs ? rhs0 + k : a.nrhs - 1;  // clamp: lanes past nrhs are not stored
     in[k] = (const char*)a.in + (long)r * a.in_stride + par_in;
   }
+
+  // staged operands of hop H (mu = H / 2, forward for even H)
+  constexpr int SC = RawSp<P>::NC;
+  constexpr int NSLOT = NR * SC + 3;
+  auto prefetch = [&](auto h_c, int st) {
+    constexpr int H = decltype(h_c)::value;
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    const uint32_t j = FWD ? jf[MU] : jb[MU];
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+      for (int c = 0; c < SC; ++c)
+        cp16(stg.at(st, k * SC + c, NSLOT), reinterpret_cast<const uint4*>(in[k]) + (c * Vh + j));
+    const float4* b = reinterpret_cast<const float4*>(a.links) + (size_t)(((FWD ? p : 1 - p) * 4 + MU) * 3) * Vh;
+    const uint32_t li = FWD ? i : j;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cp16(stg.at(st, NR * SC + c, NSLOT), b + (c * Vh + li));
+    cp_commit();
+  };
+  // clover block b of this site (9 chunks) into stage st
+  auto prefetch_blk = [&](const void* base, int b, int st) {
+    const float4* q = reinterpret_cast<const float4*>(base) + (size_t)(p * 18) * Vh;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) cp16(stg.at(st, c, NSLOT), q + ((9 * b + c) * Vh + i));
+    cp_commit();
+  };
+  if constexpr (PF) prefetch(std::integral_constant<int, 0>{}, 0);
 
   // The weighted hops accumulate onto acc: for pass 2 and Dw onto A in2,
   // formed first while few registers are live (the site-local spinors stay
@@ -418,13 +501,80 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       hop_pair<P, MU, -SF, true>(u, n0, n1, acc[q], MU == 0 ? wb : w);
     }
   };
-  hop(std::integral_constant<int, 0>{});
-  hop(std::integral_constant<int, 1>{});
-  hop(std::integral_constant<int, 2>{});
-  hop(std::integral_constant<int, 3>{});
+  // staged form: wait for hop H's copies while hop H + 1's are in flight
+  auto step = [&](auto h_c) {
+    constexpr int H = decltype(h_c)::value;
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    constexpr int st = H & 1;
+    if constexpr (H < 7) {
+      prefetch(std::integral_constant<int, H + 1>{}, (H + 1) & 1);
+      cp_wait<1>();
+    } else if constexpr (MODE == HOP_P1) {
+      prefetch_blk(a.cinv, 0, 0);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    Su3<float> u;
+    link12_from(*reinterpret_cast<const float4*>(stg.at(st, NR * SC, NSLOT)),
+                *reinterpret_cast<const float4*>(stg.at(st, NR * SC + 1, NSLOT)),
+                *reinterpret_cast<const float4*>(stg.at(st, NR * SC + 2, NSLOT)), u);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      RawSp<P> n0, n1;
+#pragma unroll
+      for (int c = 0; c < SC; ++c) {
+        n0.ch[c] = *stg.at(st, (2 * q) * SC + c, NSLOT);
+        n1.ch[c] = *stg.at(st, (2 * q + 1) * SC + c, NSLOT);
+      }
+      hop_pair<P, MU, FWD ? SF : -SF, !FWD>(u, n0, n1, acc[q], MU == 0 ? (FWD ? wf : wb) : w);
+    }
+  };
+  if constexpr (PF) {
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
+    step(std::integral_constant<int, 2>{});
+    step(std::integral_constant<int, 3>{});
+    step(std::integral_constant<int, 4>{});
+    step(std::integral_constant<int, 5>{});
+    step(std::integral_constant<int, 6>{});
+    step(std::integral_constant<int, 7>{});
+  } else {
+    hop(std::integral_constant<int, 0>{});
+    hop(std::integral_constant<int, 1>{});
+    hop(std::integral_constant<int, 2>{});
+    hop(std::integral_constant<int, 3>{});
+  }
 
   Sp2 (&res)[NP] = acc;
-  if constexpr (MODE == HOP_P1) {
+  if constexpr (MODE == HOP_P1 && PF) {
+    // res = A^{-1} (w H in): block 0 was staged with the last hop, block 1
+    // is staged while block 0 is applied
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (b == 0) {
+        prefetch_blk(a.cinv, 1, 1);
+        cp_wait<1>();
+      } else {
+        cp_wait<0>();
+      }
+      float4 w9[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) w9[c] = *reinterpret_cast<const float4*>(stg.at(b, c, NSLOT));
+      Blk k;
+      blk_from(w9, k);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        C2 xv[6], yv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) xv[r] = acc[q].c[2 * b + r / 3][r % 3];
+        blk_apply(k, xv, yv);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) res[q].c[2 * b + r / 3][r % 3] = yv[r];
+      }
+    }
+  } else if constexpr (MODE == HOP_P1) {
     // res = A^{-1} (w H in), in place one clover block at a time
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -538,13 +688,25 @@ __device__ __forceinline__ void grid_reduce_nr(const double (&v)[NR], const RedA
 // site block adjacent).  CAP = 1 caps the registers (128 for NR = 2, 168 for
 // NR = 4: at least 16 / 12 warps per SM, with some spilling); CAP = 0 lets
 // the compiler keep all neighbour loads of a site in flight.
+// CAP = 2: the register cap of CAP = 1 and the hop operands staged in
+// shared memory (site<..., PF = true>; 12-real links only).
 template <int NR, int CAP>
 struct MrBounds {
   static constexpr int min_blocks = CAP == 0 ? 1 : NR == 2 ? 4 : 3;
 };
+// dynamic shared memory of a staged launch: 2 stages of NR * chunks + 3 slots of 16 bytes per thread
+template <int P, int NR>
+constexpr size_t mr_stage_bytes(int nthr) {
+  return (size_t)2 * (NR * (P == P_F32 ? 6 : 3) + 3) * 16 * nthr;
+}
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, int CAP>
 __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_kernel(const HopArgs a) {
-  extern __shared__ double red_smem[];
+  extern __shared__ double dyn_smem[];
+  constexpr bool PF = CAP == 2;
+  const uint32_t nthr = blockDim.x * blockDim.y;
+  // staged launches: the stages first, then the reduction scratch
+  double* red_smem = PF ? dyn_smem + mr_stage_bytes<P, NR>(nthr) / sizeof(double) : dyn_smem;
+  mr::Stage stg{reinterpret_cast<uint4*>(dyn_smem), nthr, threadIdx.y * blockDim.x + threadIdx.x};
   const unsigned per_cta = blockDim.y * NR;
   const unsigned ntile = (a.nrhs + per_cta - 1) / per_cta;
   const unsigned tile = blockIdx.x % ntile;
@@ -565,7 +727,7 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
   double red[NR];
 #pragma unroll
   for (int k = 0; k < NR; ++k) red[k] = 0.0;
-  if (any) mr::site<P, FMT, MODE, DAG, EPI, NR>(a, i, rhs0, p, live, red);
+  if (any) mr::site<P, FMT, MODE, DAG, EPI, NR, PF>(a, i, rhs0, p, live, red, stg);
   if constexpr (EPI != EPI_NONE) {
 #pragma unroll
     for (int k = 0; k < NR; ++k)
@@ -582,6 +744,21 @@ static cudaError_t launch_mr_one(const HopLaunch& L, const HopArgs& a, cudaStrea
   const unsigned ntile = (unsigned)((a.nrhs + L.by * NR - 1) / (L.by * NR));
   dim3 grid((MODE == HOP_DW ? 2u * nb : nb) * ntile, 1u, 1u);
   const size_t smem = (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32) * L.by * NR;
+  if (L.regcap == 2) {
+    if constexpr (FMT == LINK_12) {
+      const size_t bytes = smem + mr_stage_bytes<P, NR>(L.bx * L.by);
+      static bool attr = false;  // per instantiation: allow more than 48 KiB once
+      if (!attr && bytes > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 2>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 2><<<grid, block, bytes, s>>>(a);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
   if (L.regcap)
     hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 1><<<grid, block, smem, s>>>(a);
   else

@@ -45,7 +45,7 @@ extern "C" int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const voi
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !in_dev || !out_dev || prec < 0 || prec > 3 || nrhs < 1)
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
   // the scratch address is per device: only the handle's device may be current
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return OQ_ERR_CUDA;

@@ -651,6 +651,44 @@ __device__ __forceinline__ void project(const Spinor<R>& p, HalfSpinor<R>& h) {
 
 // acc += w * (1 -/+ g_mu)-reconstruction of the transported half spinor h
 // (SCALE = false: w = 1, no multiplication)
+// A time face of a sub-domain: one half spinor (2 spins x 3 colours) per
+// site of one parity of one time slice, Fs = Vh / L0 sites, 16-byte chunks
+// stored chunk-major ([chunk][Fs]): binary64 6 chunks (one complex each),
+// binary32 3 chunks (two complex each); component k = 3 spin + colour.
+template <typename R>
+__device__ __forceinline__ void load_half(const void* base, long Fs, long f, HalfSpinor<R>& h) {
+  cx<R>* c = &h.c[0][0];
+  if constexpr (sizeof(R) == 8) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 v = b[k * Fs + f];
+      c[k] = cx<R>{v.x, v.y};
+    }
+  } else {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 v = b[k * Fs + f];
+      c[2 * k] = cx<R>{v.x, v.y};
+      c[2 * k + 1] = cx<R>{v.z, v.w};
+    }
+  }
+}
+template <typename R>
+__device__ __forceinline__ void store_half(void* base, long Fs, long f, const HalfSpinor<R>& h) {
+  const cx<R>* c = &h.c[0][0];
+  if constexpr (sizeof(R) == 8) {
+    double2* b = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) b[k * Fs + f] = make_double2(c[k].re, c[k].im);
+  } else {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[k * Fs + f] = make_float4(c[2 * k].re, c[2 * k].im, c[2 * k + 1].re, c[2 * k + 1].im);
+  }
+}
+
 template <int MU, int S, typename R, bool SCALE = true>
 __device__ __forceinline__ void accum_reconstruct(Spinor<R>& acc, const HalfSpinor<R>& h, R w) {
 #pragma unroll

@@ -72,6 +72,17 @@ struct HopArgs {
   // instrumentation (nullable): CTA 0 writes the number of right-hand sides
   // live in this launch (not gated off by their solver state)
   unsigned* live_rec;
+  // sub-domain launches (halo_next != null): the time hops that leave the
+  // sub-domain read faces (load_half layout) received from the neighbouring
+  // sub-domains instead of the periodic wrap: halo_next the projected half
+  // spinors (1 -/+ g0) psi of the next one's x0 = 0 slice, halo_prev the
+  // transported U_0^dag (1 +/- g0) psi of the previous one's last slice;
+  // halo_sign_* the boundary factor of those hops
+  const void* halo_next;
+  const void* halo_prev;
+  long halo_stride;    // bytes between right-hand sides of a face
+  long halo_pstride;   // HOP_DW: bytes between the faces of the two output parities
+  float halo_sign_next, halo_sign_prev;
 };
 
 // the number of right-hand sides a launch acts on, written by one thread of CTA 0
@@ -114,6 +125,16 @@ cudaError_t launch_hop_mr2_bf16(const HopLaunch& L, const HopArgs& a, cudaStream
 cudaError_t launch_hop_mr4_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_mr2_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_mr4_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+
+// geometry of a sub-domain extended by one time slice on each side
+inline Geom halo_ext_geom(const Geom& g) {
+  Geom e = g;
+  const long Fs = g.Vh / g.L[0];
+  e.L[0] = g.L[0] + 2;
+  e.Vh = g.Vh + 2 * Fs;
+  geom_init_div(e);
+  return e;
+}
 
 __host__ __device__ inline int prec_bytes(int prec) {
   return (prec == P_F64 || prec == P_DF64) ? 8 : prec == P_F32 ? 4 : 2;

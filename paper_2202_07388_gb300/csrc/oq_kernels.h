@@ -47,6 +47,9 @@ cudaError_t cg_accumulate_x(int xprec, double* xd, const void* xs, long Vh, long
                             void* xdf = nullptr);
 cudaError_t cg_restart(int prec, const void* rd, int rd_prec, void* rs, void* p, void* xs, int xprec, long Vh,
                        long stride_d, long stride_s, long stride_xs, int nrhs, const RedArgs& ra, cudaStream_t s);
+// y = a_k x + b_k y per right-hand side (binary64 or binary32 fields of n reals each)
+cudaError_t axpby(int prec, const double* a, const void* x, const double* b, void* y, long n, int nrhs,
+                  cudaStream_t s);
 cudaError_t cg_copy_gated(double* dst, const double* src, long n16, long stride, int nrhs, const CgState* cg,
                           int gate, cudaStream_t s);
 

@@ -45,6 +45,7 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, dou
   double2* d64 = u64 + ((long)(p * 4 + mu) * 9) * g.Vh;
 #pragma unroll
   for (int k = 0; k < 9; ++k) d64[k * g.Vh + i] = m[k];
+  if (!u32) return;  // binary64 links only
   if (fmt == LINK_18) {
     float2* d = reinterpret_cast<float2*>(u32) + ((long)(p * 4 + mu) * 9) * g.Vh;
 #pragma unroll

@@ -354,7 +354,7 @@ int nnprec_forward(oq_handle h, int lat, const void* r, void* y, cudaStream_t s)
 extern "C" int oq_nnprec_apply(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
                                void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !weights_dev || !in_dev || !out_dev) return OQ_ERR_ARG;
-  if (!h->lats[lat].has_gauge) return OQ_ERR_STATE;
+  if (!h->lats[lat].has_gauge || h->lats[lat].halo_t) return OQ_ERR_STATE;  // whole lattices only
   cudaStream_t s = (cudaStream_t)stream;
   int rc = nnprec_prepare(h, lat, weights_dev, s);
   if (rc) return rc;
@@ -399,7 +399,7 @@ extern "C" int oq_nnprec_grad(oq_handle h, int lat, const float* weights_dev, co
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !weights_dev || !r_dev || !e_dev || n < 1 || !grad_dev)
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
-  if (!L.has_gauge) return OQ_ERR_STATE;
+  if (!L.has_gauge || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
   cudaStream_t s = (cudaStream_t)stream;
   NnBufs b;
   int rc = nn_bufs(h, lat, &b);

@@ -329,7 +329,7 @@ using namespace oq;
 extern "C" int oq_nnprec_apply_tc(oq_handle h, int lat, const float* weights_dev, const void* in_dev, void* out_dev,
                                   void* stream) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !weights_dev || !in_dev || !out_dev) return OQ_ERR_ARG;
-  if (!h->lats[lat].has_gauge) return OQ_ERR_STATE;
+  if (!h->lats[lat].has_gauge || h->lats[lat].halo_t) return OQ_ERR_STATE;  // whole lattices only
   return nnprec_forward_tc(h, lat, weights_dev, in_dev, out_dev, (cudaStream_t)stream);
 }
 

@@ -48,7 +48,7 @@ std::vector<TuneVal> candidates(int prec, int nrhs) {
     const int nrs[] = {2, 4};
     for (int nr : nrs) {
       if (nr > nrhs) continue;
-      for (int cap = 0; cap < 2; ++cap)
+      for (int cap = 0; cap < 3; ++cap)
         for (int bx : bxs)
           for (int by = 1; by <= 2; ++by) {
             if (bx * by > 128 || by * nr > nrhs) continue;
@@ -72,7 +72,9 @@ bool valid_shape(const LatCtx& L, int prec, int nrhs, const TuneVal& v) {
       return false;
   } else if (v.nr == 2 || v.nr == 4) {
     if (prec != P_F32 && prec != P_BF16 && prec != P_F16) return false;
-    if (v.bx * v.by > 128 || (v.regcap != 0 && v.regcap != 1)) return false;
+    if (v.bx * v.by > 128 || v.regcap < 0 || v.regcap > 2) return false;
+    // staged hops (regcap 2) read 12-real links
+    if (v.regcap == 2 && (v.link_fmt == LINK_18 || (v.link_fmt == -1 && L.link_fmt != LINK_12))) return false;
   } else {
     return false;
   }
@@ -91,7 +93,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
   if (!h || lat < 0 || lat >= (int)h->lats.size() || prec < 0 || prec > 4 || nrhs < 1 || nrhs > 64)
     return OQ_ERR_ARG;
   LatCtx& L = h->lats[lat];
-  if (!L.has_clover) return OQ_ERR_STATE;
+  if (!L.has_clover || L.halo_t) return OQ_ERR_STATE;  // whole lattices only
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == P_DF64) {
     const int rc = h->ensure_df(lat, s);
@@ -175,6 +177,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
     const bool two_fmts = prec != P_F64 && prec != P_DF64 && L.link_fmt == LINK_12 && L.u32_18.p;
     for (int fmt = L.link_fmt; fmt >= 0; fmt = (two_fmts && fmt == LINK_12) ? LINK_18 : -1) {
       for (TuneVal c : candidates(prec, nrhs)) {
+        if (c.regcap == 2 && c.nr > 1 && fmt != LINK_12) continue;  // staged hops read 12-real links
         HopLaunch l = h->hop_launch(lat, prec, mode, 0, var.epi, nrhs);
         l.bx = c.bx;
         l.by = c.by;

@@ -25,6 +25,8 @@ EVEN, ODD, FULL = 0, 1, 2
 PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16, "df64": DF64}
 OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA, OPT_NN_TENSOR_CORES, OPT_SAP_KERNEL = 1, 2, 3, 4
 
+BC_HALO = 2   # bc_t of a time-split sub-domain
+
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_NOCONV, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
 
@@ -51,6 +53,11 @@ class OqStatus(C.Structure):
     _fields_ = [("steps", C.c_int), ("resets", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("true_rel_res", C.c_double), ("cycles", C.c_int), ("mr_avg", C.c_double),
                 ("ladder_steps", C.c_int * 4), ("nn_fallback", C.c_int)]
+
+
+class OqHalo(C.Structure):
+    _fields_ = [("from_next", C.c_void_p), ("from_prev", C.c_void_p), ("sign_next", C.c_double),
+                ("sign_prev", C.c_double)]
 
 
 class OqKernelTime(C.Structure):
@@ -103,6 +110,13 @@ _SIGS = {
                               C.POINTER(C.c_int)]),
     "oq_tune_set": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                               C.c_int]),
+    "oq_gauge_upload_halo": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),
+    "oq_face_bytes": (C.c_size_t, [_P, C.c_int, C.c_int]),
+    "oq_face_pack": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P, _P, _P]),
+    "oq_dw_apply_halo": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, C.POINTER(OqHalo), _P]),
+    "oq_dhat_pass": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, C.POINTER(OqHalo), _P]),
+    "oq_axpby": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), _P, C.POINTER(C.c_double), _P,
+                           C.c_int, _P]),
     "oq_profile_start": (C.c_int, [_P]),
     "oq_kernel_launches": (C.c_longlong, [_P]),
     "oq_profile_stop": (C.c_int, [_P, C.POINTER(OqKernelTime), C.c_int, C.POINTER(C.c_int)]),
@@ -275,6 +289,47 @@ class Handle:
                "oq_dot")
         v = np.array(out[:])
         return v[0::2] + 1j * v[1::2]
+
+    # time-split sub-domains ------------------------------------------
+    def gauge_upload_halo(self, u_ext_dev, link_fmt=LINK_12, lat=0, stream=None):
+        """Links of T_loc + 2 slices (one beyond each face) of a sub-domain lattice."""
+        _check(lib().oq_gauge_upload_halo(self.h, lat, _ptr(u_ext_dev), link_fmt, _stream(stream)),
+               "oq_gauge_upload_halo")
+
+    def face_bytes(self, prec, lat=0):
+        return int(lib().oq_face_bytes(self.h, lat, prec))
+
+    def new_faces(self, prec, nrhs=1, parities=1, lat=0):
+        import torch
+        return torch.empty(self.face_bytes(prec, lat) * nrhs * parities, dtype=torch.uint8, device="cuda")
+
+    def face_pack(self, in_dev, to_prev, to_next, prec, subset, nrhs=1, dagger=False, lat=0, stream=None):
+        _check(lib().oq_face_pack(self.h, lat, prec, subset, _ptr(in_dev), nrhs, int(dagger), _ptr(to_prev),
+                                  _ptr(to_next), _stream(stream)), "oq_face_pack")
+
+    @staticmethod
+    def halo(from_next, from_prev, sign_next=1.0, sign_prev=1.0):
+        return OqHalo(_ptr(from_next).value, _ptr(from_prev).value, float(sign_next), float(sign_prev))
+
+    def dw_halo(self, in_dev, out_dev, prec, halo: OqHalo, nrhs=1, dagger=False, lat=0, stream=None):
+        _check(lib().oq_dw_apply_halo(self.h, lat, prec, _ptr(in_dev), _ptr(out_dev), nrhs, int(dagger),
+                                      C.byref(halo), _stream(stream)), "oq_dw_apply_halo")
+
+    def dhat_pass(self, pass_, in_dev, in2_dev, out_dev, prec, halo=None, nrhs=1, dagger=False, lat=0,
+                  stream=None, check=True):
+        rc = lib().oq_dhat_pass(self.h, lat, prec, pass_, _ptr(in_dev), _ptr(in2_dev) if in2_dev is not None
+                                else None, _ptr(out_dev), nrhs, int(dagger),
+                                C.byref(halo) if halo is not None else None, _stream(stream))
+        if check:
+            _check(rc, "oq_dhat_pass")
+        return rc
+
+    def axpby(self, a, x_dev, b, y_dev, prec, subset=FULL, nrhs=1, lat=0, stream=None):
+        """y = a x + b y per right-hand side (a, b: sequences of nrhs reals)."""
+        av = (C.c_double * nrhs)(*[float(v) for v in a])
+        bv = (C.c_double * nrhs)(*[float(v) for v in b])
+        _check(lib().oq_axpby(self.h, lat, prec, subset, av, _ptr(x_dev), bv, _ptr(y_dev), nrhs, _stream(stream)),
+               "oq_axpby")
 
     # solvers -----------------------------------------------------------
     def cgne(self, eta_dev, psi_dev, params: SolverParams, nrhs=1, lat=0, stream=None, check=True):

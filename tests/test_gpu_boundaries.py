@@ -180,7 +180,7 @@ def test_boundary_rejections():
     oq = _oq()
     dims = (4, 4, 4, 4)
     with pytest.raises(oq.OqError):
-        oq.Handle(dims, bc_t=2)
+        oq.Handle(dims, bc_t=3)                      # 2 is a time-split sub-domain (OQ_BC_HALO)
     h = oq.Handle(dims, bc_t=0)
     h.gauge_upload(to_dev(synth.make_gauge_sf(dims, 0.3, 1)), oq.LINK_12)
     with pytest.raises(oq.OqError):

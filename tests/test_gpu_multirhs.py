@@ -1,6 +1,7 @@
 """GPU parity of the multi-right-hand-side stencil (2 or 4 right-hand sides
 per thread, packed two-lane binary32 arithmetic, with and without the
-register cap) against the FP64 oracle, pinned with oq_tune_set: full Dw,
+register cap, and with the hop operands staged in shared memory) against
+the FP64 oracle, pinned with oq_tune_set: full Dw,
 Dhat and their adjoints for every binary32-arithmetic storage type and both
 link formats, on ragged site counts and right-hand-side counts that are not
 multiples of the per-thread count; the fused CG epilogue through a batched
@@ -31,8 +32,7 @@ def _pin(h, prec, nrhs, bx, by, nr, cap, fmt):
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("prec", [1, 2, 3])
 @pytest.mark.parametrize("nr,nrhs,bx,by", [(2, 5, 64, 2), (4, 5, 32, 1), (4, 8, 128, 1), (2, 2, 32, 1)])
-@pytest.mark.parametrize("cap", [0, 1])
-@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("cap,fmt", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 1)])
 def test_multi_rhs_dw_and_dw_hat(case, prec, nr, nrhs, bx, by, cap, fmt):
     oq = _oq()
     dims, eps, seed, kappa, csw = case
@@ -63,7 +63,7 @@ def test_multi_rhs_dw_and_dw_hat(case, prec, nr, nrhs, bx, by, cap, fmt):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
-@pytest.mark.parametrize("nr,cap", [(2, 0), (4, 1)])
+@pytest.mark.parametrize("nr,cap", [(2, 0), (4, 1), (2, 2), (4, 2)])
 def test_multi_rhs_cgne_epilogues(prec, nr, cap):
     """The norm and CG-update epilogues of the multi-rhs kernel inside the
     batched CGNE: 5 right-hand sides (a ragged group), every one to a binary64
@@ -103,16 +103,20 @@ def test_tune_set_rejects_inadmissible_launches():
     assert h.tune_set(oq.F16, 1, 4, 128, 2, nr=2, check=False) == oq.ERR_ARG     # 256 threads with nr > 1
     assert h.tune_set(oq.F64, 1, 4, 64, 1, nr=2, check=False) == oq.ERR_ARG      # binary64: one rhs per thread
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=3, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, link_fmt=0, check=False) == oq.ERR_ARG  # staged: 12-real
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, link_fmt=1) == oq.OK
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=3, check=False) == oq.ERR_ARG
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=1, regcap=1, check=False) == oq.ERR_ARG   # cap: nr > 1 or DF64
     assert h.tune_set(oq.DF64, 1, 4, 128, 2, nr=1, regcap=1, check=False) == oq.ERR_ARG  # capped: <= 128 threads
     assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=1) == oq.OK
     assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=2) == oq.OK
     assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=3, check=False) == oq.ERR_ARG
-    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2) == oq.OK      # staged on the uploaded 12-real links
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=4, regcap=1) == oq.OK
     assert h.tune_get(oq.F16, 1, 4)[4:] == (4, 1)
     h2 = make_handle(dims, u, 0.13, 1.0, oq.LINK_18)
     assert h2.tune_set(oq.F32, 1, 1, 64, 1, link_fmt=oq.LINK_12, check=False) == oq.ERR_ARG
+    assert h2.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, check=False) == oq.ERR_ARG  # staged: 12-real links
 
 
 @pytest.mark.parametrize("case", CASES)
