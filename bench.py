@@ -227,18 +227,70 @@ def algo_bytes_normal_op(ve_sites, prec_bytes, link_reals, nrhs):
     return 2 * (per_pass_p1 + per_pass_p2) * ve_sites
 
 
-def cpu_time_oracle(reps):
-    """Wall and CPU time of `reps` oracle Dhat^dag Dhat applications on the slab."""
-    case = oracle_sample_setup()
-    oracle_step(case)  # warm-up
-    t0, c0 = time.perf_counter(), time.process_time()
+C2_CASE = ((32, 16, 16, 16), 0.5, 0.135, 2)     # 32x16^3 workload: dims, eps, kappa, seed
+
+
+def _oracle_normal_seconds(dims, eps, kappa, seed, reps):
+    """Seconds of one oracle Dhat^dag Dhat application (the work of one CG
+    iteration on the even-odd system) on one core, mean of reps after one
+    warm-up."""
+    from oracle import dirac
+    from paper_2202_07388_gb300 import synth
+    u = synth.make_gauge(dims, eps, seed)
+    a = dirac.clover_field(u, dirac.kappa_to_m0(kappa), CSW)
+    ainv = np.linalg.inv(a)
+    psi = dirac.even_part(synth.make_source(dims, seed + 1))
+    normal = lambda v: dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, v))  # noqa: E731
+    normal(psi)
+    t0 = time.perf_counter()
     for _ in range(reps):
-        oracle_step(case)
-    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
-    ve = int(np.prod(SLAB)) // 2
-    # bytes the same work would move in the GPU step's storage (f16 spinors, 12-real f32 links)
-    byts = algo_bytes_normal_op(ve, 2, 12, 1) * reps
-    return wall, cpu, byts
+        normal(psi)
+    return (time.perf_counter() - t0) / reps
+
+
+def _pool_normal(_):
+    return _oracle_normal_seconds(*C2_CASE, reps=1)
+
+
+def cpu_baseline_tts():
+    """The oracle's binary64 CGNE on the host cores: the 4^4 workload solved to
+    1e-10 outright; the 32x16^3 and 64x32^3 workloads by their time per CG
+    iteration (one normal-operator application, the 64x32^3 one scaled from
+    the 32x16^3 one by the volume, 16x), to be multiplied by the step count of
+    the binary64 CGNE (the GPU's, same algorithm and inputs); and all cores at
+    once on independent 32x16^3 applications (a spawned process pool, the
+    oracle being single-threaded NumPy)."""
+    import multiprocessing as mp
+    import platform
+    from oracle import dirac, solvers
+    from paper_2202_07388_gb300 import synth
+    out = {"cpu_model": platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+    dims = (4, 4, 4, 4)
+    u = synth.make_gauge(dims, 0.3, 1)
+    a = dirac.clover_field(u, dirac.kappa_to_m0(0.13), CSW)
+    ainv = np.linalg.inv(a)
+    eta = dirac.even_part(synth.make_source(dims, 2))
+    normal = lambda v: dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, v))  # noqa: E731
+    t0 = time.perf_counter()
+    r = solvers.cgne(normal, eta, RES, 5000, "fp64")
+    out["c1_4x4x4x4_cgne_fp64_s"] = time.perf_counter() - t0
+    out["c1_steps"] = int(r.status)
+    out["c2_32x16c_s_per_iter_1core"] = _oracle_normal_seconds(*C2_CASE, reps=2)
+    out["c3_64x32c_s_per_iter_1core"] = 16.0 * out["c2_32x16c_s_per_iter_1core"]
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    workers = max(1, min(cores, 16))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        per = pool.map(_pool_normal, range(workers))
+    wall = time.perf_counter() - t0
+    out["all_cores"] = {"workers": workers, "cores": cores, "wall_s": wall,
+                        "c2_s_per_iter_per_worker": float(np.mean(per)),
+                        "c2_iters_per_s": workers / float(np.mean(per))}
+    return out
 
 
 def run_reference(args):
@@ -304,13 +356,16 @@ def run_ours(args):
         dist.init_process_group("nccl")
     # cpu baseline first (no CUDA work in flight, rank 0 at N=1 only)
     cpu_line = None
+    cpu_tts = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        wall, cpu, byts = cpu_time_oracle(args.cpu_reps)
-        cpu_line = {"value": byts / wall / 1e9, "unit": "GB/s", "cores": max(1, round(cpu / wall)),
-                    "kind": "oracle",
-                    "sample": f"{args.cpu_reps} oracle (NumPy FP64) Dhat^dag Dhat on one rhs of a "
-                              f"{SLAB[0]}x{SLAB[1]}^3 slab ({wall:.1f} s), bytes counted as the GPU step's "
-                              f"f16 workload"}
+        cpu_tts = cpu_baseline_tts()
+        per = cpu_tts["c2_32x16c_s_per_iter_1core"]
+        ve = int(np.prod(C2_CASE[0])) // 2
+        byts = algo_bytes_normal_op(ve, 2, 12, 1)
+        cpu_line = {"value": byts / per / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                    "sample": f"oracle (NumPy FP64) Dhat^dag Dhat on one rhs of the 32x16^3 workload "
+                              f"({per:.2f} s per application, the same per-site work as the 64x32^3 step), "
+                              f"bytes counted as the GPU step's f16 workload; time-to-solution rows in tts"}
 
     t_setup = time.perf_counter()
     u = synth.make_gauge(DIMS, EPS, SEED + 1000 * rank)
@@ -599,6 +654,56 @@ def run_ours(args):
              "launches": p["launches"], "ms": p["total_ms"]} for p in h.profile_stop()]
         h.set_option(oq.OPT_DF64_RESETS, 1)
 
+    # time to solution on the 4^4 and 32x16^3 workloads (one Gaussian source,
+    # even part): binary64 CGNE and the F16 mixed-precision CGNE, next to the
+    # oracle's binary64 CGNE on the host cores
+    small_tts = None
+    if rank == 0 and ws == 1 and not args.no_tts:
+        small_tts = {}
+        for name, (dims, eps, kappa, seed) in (("c1_4x4x4x4", ((4, 4, 4, 4), 0.3, 0.13, 1)), ("c2_32x16c", C2_CASE)):
+            hs = oq.Handle(dims)
+            hs.gauge_upload(to_dev(synth.make_gauge(dims, eps, seed)), oq.LINK_12)
+            hs.clover_build(kappa, CSW)
+            src = synth.make_source(dims, seed + 1)
+            src[np.indices(dims).sum(axis=0) % 2 == 1] = 0.0
+            e_d = to_dev(src)
+            p_d = torch.zeros_like(e_d)
+            row = {}
+            for pname, pc in (("fp64", oq.F64), ("fp16", oq.F16)):
+                p1 = oq.SolverParams(res=RES, nmx=50000, sdtype=pc)
+                hs.cgne(e_d, p_d, p1)
+                torch.cuda.synchronize()
+                s0 = time.perf_counter()
+                rc, st1 = hs.cgne(e_d, p_d, p1)
+                torch.cuda.synchronize()
+                row[pname] = {"s": time.perf_counter() - s0, "steps": st1[0]["steps"], "resets": st1[0]["resets"],
+                              "true_rel_res": st1[0]["true_rel_res"]}
+            small_tts[name] = row
+            hs.close()
+    if cpu_tts is not None and small_tts is not None and tts is not None:
+        # oracle binary64 CGNE time to solution: measured on 4^4, per-iteration
+        # time x the binary64 step count on the larger workloads
+        cpu_tts["c2_32x16c_cgne_fp64_s_extrapolated"] = (cpu_tts["c2_32x16c_s_per_iter_1core"]
+                                                         * small_tts["c2_32x16c"]["fp64"]["steps"])
+        cpu_tts["c3_64x32c_1rhs_cgne_fp64_s_extrapolated"] = (cpu_tts["c3_64x32c_s_per_iter_1core"]
+                                                              * tts["fp64"]["steps"])
+        cpu_tts["gpu_speedup_fp64_c2"] = (cpu_tts["c2_32x16c_cgne_fp64_s_extrapolated"]
+                                          / small_tts["c2_32x16c"]["fp64"]["s"])
+        cpu_tts["note"] = ("4^4 solved by the oracle; 32x16^3 and 64x32^3 (one point-source rhs): seconds per CG "
+                           "iteration (one Dhat^dag Dhat) x the binary64 CGNE step count on the GPU; 1 core unless "
+                           "all_cores")
+    if cpu_line is not None:
+        cpu_line["tts"] = cpu_tts
+
+    # the uneven QCD+QED batch and the learned preconditioner against SAP-GCR,
+    # compact forms of --workload c4 / c5 (rank 0, N = 1)
+    extra = {}
+    if rank == 0 and ws == 1 and not args.no_extra:
+        t_x = time.perf_counter()
+        extra["c4_uneven_batch"] = run_workload_c4(args, compact=True)
+        extra["c5_learned_vs_sap"] = run_workload_c5(args, compact=True)
+        extra["extra_s"] = time.perf_counter() - t_x
+
     st_last = statuses[-1]
     if rank == 0:
         line = {
@@ -633,7 +738,7 @@ def run_ours(args):
                          "gbs": p["bytes"] / (p["total_ms"] * 1e-3) / 1e9 if p["total_ms"] > 0 else None,
                          "rhs_launches": p["rhs_launches"], "gated_launches": p["gated_launches"],
                          "gated_ms": p["gated_ms"]} for p in prof],
-            "tts": tts, "setup_s": setup_s, "tuned_shapes": tuned,
+            "tts": tts, "tts_small": small_tts, "setup_s": setup_s, "tuned_shapes": tuned, **extra,
         }
         print(json.dumps(line), flush=True)
     h.close()
@@ -730,15 +835,17 @@ def _timed(fn):
     return time.perf_counter() - t0, out
 
 
-def run_workload_c4(args):
+def run_workload_c4(args, compact=False):
     """Uneven batch (QCD+QED): U(3) links with charges 2/3 and -1/3 on 8^4,
     32x16^3 and 48x24^3 lattices; batched CGNE (tile-list launches, graph
     replay) against the same systems solved one after the other; then the
-    batch again with the clover of separate SU(3) and U(1) coefficients."""
+    batch again with the clover of separate SU(3) and U(1) coefficients.
+    compact: F16 storage only, returned as a dict (the default bench line)."""
     import torch
     from paper_2202_07388_gb300 import oq, synth
     from paper_2202_07388_gb300 import build as _build
-    _build.build()
+    if not compact:
+        _build.build()
     lats = [(8, 8, 8, 8), (32, 16, 16, 16), (48, 24, 24, 24)]
     charges = [2.0 / 3.0, -1.0 / 3.0]
     dims_all, fields = [], []
@@ -761,7 +868,7 @@ def run_workload_c4(args):
         psis.append(torch.zeros_like(etas[-1]))
     del fields
     out = {"workload": "uneven batch 8^4 + 32x16^3 + 48x24^3, U(3) links, q = 2/3, -1/3 (6 systems)"}
-    for pname, pc in (("f32", oq.F32), ("f16", oq.F16)):
+    for pname, pc in ((("f16", oq.F16),) if compact else (("f32", oq.F32), ("f16", oq.F16))):
         prm = oq.SolverParams(res=RES, nmx=20000, sdtype=pc)
         h.cgne_batch(list(range(len(dims_all))), etas, psis, prm)  # warm-up
         tb, (rc, st) = _timed(lambda: h.cgne_batch(list(range(len(dims_all))), etas, psis, prm))
@@ -774,6 +881,9 @@ def run_workload_c4(args):
         out[pname] = {"batched_s": tb, "sequential_s": ts, "speedup": ts / tb, "rc": rc,
                       "steps": [s["steps"] for s in st], "resets": [s["resets"] for s in st],
                       "max_true_rel_res": max(s["true_rel_res"] for s in st)}
+    if compact:
+        h.close()
+        return out
     # openQ*D's clover with separate SU(3) and U(1) coefficients (both c_sw)
     tc, _ = _timed(lambda: [h.clover_build(KAPPA, CSW, lat=lat, csw_qed=CSW) for lat in range(len(dims_all))])
     prm = oq.SolverParams(res=RES, nmx=20000, sdtype=oq.F16)
@@ -839,16 +949,19 @@ def run_workload_sf(args):
     return 0
 
 
-def run_workload_c5(args):
+def run_workload_c5(args, compact=False):
     """48x24^3 at kappa = 0.1365: SAP-GCR (4^4 blocks, 5 MR steps, 4 cycles,
     16 Krylov vectors), its adaptive variant, GCR without preconditioner, and
     the learned PTC preconditioner trained on the GPU on (r, D^-1 r) pairs
     from the binary64 solver, each to a binary64 residual of 1e-10; plus the
-    plain binary64 and the mixed-precision CGNE on the even-odd system."""
+    plain binary64 and the mixed-precision CGNE on the even-odd system.
+    compact: static and adaptive SAP-GCR, plain GCR, the trained network,
+    binary64 and F16 CGNE, returned as a dict (the default bench line)."""
     import torch
     from paper_2202_07388_gb300 import oq, synth
     from paper_2202_07388_gb300 import build as _build
-    _build.build()
+    if not compact:
+        _build.build()
     dims = (48, 24, 24, 24)
     kappa = 0.1365
     u = synth.make_gauge(dims, 0.5, 5)
@@ -873,10 +986,13 @@ def run_workload_c5(args):
     sap_eo3 = dataclasses.replace(sap, sap_eo=1, nmr=3)
     ada_eo = dataclasses.replace(ada, sap_eo=1)
     # SAP block kernels: operands in shared memory (default), global operands one / two blocks per SM
-    for name, prm, kern in (("sap_gcr", sap, 0), ("sap_gcr_global_operands", sap, 1),
-                            ("sap_gcr_global_operands_two_ctas", sap, 2), ("sap_gcr_adaptive", ada, 0),
-                            ("sap_gcr_eo_blocks", sap_eo, 0), ("sap_gcr_eo_blocks_nmr3", sap_eo3, 0),
-                            ("sap_gcr_adaptive_eo_blocks", ada_eo, 0), ("gcr", plain, 0)):
+    variants = (("sap_gcr", sap, 0), ("sap_gcr_global_operands", sap, 1),
+                ("sap_gcr_global_operands_two_ctas", sap, 2), ("sap_gcr_adaptive", ada, 0),
+                ("sap_gcr_eo_blocks", sap_eo, 0), ("sap_gcr_eo_blocks_nmr3", sap_eo3, 0),
+                ("sap_gcr_adaptive_eo_blocks", ada_eo, 0), ("gcr", plain, 0))
+    if compact:
+        variants = tuple(v for v in variants if v[0] in ("sap_gcr", "sap_gcr_adaptive", "gcr"))
+    for name, prm, kern in variants:
         h.set_option(oq.OPT_SAP_KERNEL, kern)
         h.sap_gcr(eta, psi, prm)
         t, (rc, st) = _timed(lambda: h.sap_gcr(eta, psi, prm))
@@ -912,6 +1028,18 @@ def run_workload_c5(args):
                      "train_pairs": ntrain, "pair_solve_s": tpairs,
                      "train_steps": args.nn_steps, "train_s": ttrain, "loss_first": float(losses[0]),
                      "loss_last": float(losses[-1])}
+    out["nn_gcr_speedup_vs_sap_gcr"] = out["sap_gcr"]["s"] / out["nn_gcr"]["s"]
+    if compact:
+        for name, pc in (("cgne_f64", oq.F64), ("cgne_f16", oq.F16)):
+            ee = eta.clone().view(dims + (4, 6))
+            ee[torch.from_numpy(np.indices(dims).sum(axis=0) % 2 == 1).cuda()] = 0.0
+            prm = oq.SolverParams(res=RES, nmx=50000, sdtype=pc)
+            h.cgne(ee, psi, prm)
+            t, (rc, st) = _timed(lambda: h.cgne(ee, psi, prm))
+            out[name] = {"s": t, "rc": rc, "steps": st[0]["steps"], "resets": st[0]["resets"],
+                         "true_rel_res": st[0]["true_rel_res"]}
+        h.close()
+        return out
     h.set_option(oq.OPT_NN_TENSOR_CORES, 1)
     h.nn_gcr(wd, eta, psi, plain)
     t, (rc, st) = _timed(lambda: h.nn_gcr(wd, eta, psi, plain))
@@ -957,9 +1085,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-reps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tts", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the compact c4 / c5 workloads")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

@@ -44,3 +44,10 @@ def make_handle(dims, u, kappa, csw, link_fmt):
 
 def rel_err(got, ref):
     return float(np.linalg.norm((got - ref).reshape(-1)) / np.linalg.norm(ref.reshape(-1)))
+
+
+def check_residual(oracle_res, reported, target=1e-10, rel=1e-3):
+    """The binary64 relative residual recomputed by the oracle meets the
+    target, and the solver's own report of it agrees to `rel` (relative)."""
+    assert oracle_res <= target * (1 + rel), (oracle_res, target)
+    assert abs(oracle_res - reported) <= rel * oracle_res, (oracle_res, reported)

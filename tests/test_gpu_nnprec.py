@@ -1,14 +1,15 @@
 """The learned preconditioner on the GPU: forward layers and gradients
 against the FP64 oracle (with the same bfloat16-rounded weights), and the
-gain test: a network trained on the GPU (own forward/backward kernels, Adam)
-on (residual, error) pairs from the binary64 solver lowers its loss and cuts
-the flexible-GCR step count relative to GCR without it."""
+gain tests: a network trained on the GPU (own forward/backward kernels, Adam)
+on (residual, error) pairs from the binary64 solver lowers its loss, cuts
+the flexible-GCR step count relative to GCR without it, and reaches the
+target residual in less time than SAP-GCR, its fallback and judge."""
 import numpy as np
 import pytest
 
 from oracle import dirac, ptc
 from paper_2202_07388_gb300 import synth
-from tests.gpu_cases import oracle_case, make_handle, to_dev, from_dev, rel_err
+from tests.gpu_cases import oracle_case, make_handle, to_dev, from_dev, rel_err, check_residual
 
 pytestmark = pytest.mark.gpu
 
@@ -161,14 +162,82 @@ def test_trained_network_cuts_gcr_steps():
     assert rc0 == oq.OK and rc1 == oq.OK
     x = from_dev(psi1, eta.shape)
     res = np.linalg.norm(eta - dirac.dw(u, a, x)) / np.linalg.norm(eta)
-    assert res <= 1.2e-10
+    check_residual(res, st1[0]["true_rel_res"])
     assert st1[0]["steps"] < st0[0]["steps"]     # binary32 CUDA-core network (default)
     h.set_option(oq.OPT_NN_TENSOR_CORES, 1)
     psi2 = to_dev(np.zeros_like(eta))
     rc2, st2 = h.nn_gcr(wd, to_dev(eta), psi2, gprm)
     assert rc2 == oq.OK and st2[0]["steps"] < st0[0]["steps"]   # tcgen05 network
     x2 = from_dev(psi2, eta.shape)
-    assert np.linalg.norm(eta - dirac.dw(u, a, x2)) / np.linalg.norm(eta) <= 1.2e-10
+    check_residual(np.linalg.norm(eta - dirac.dw(u, a, x2)) / np.linalg.norm(eta), st2[0]["true_rel_res"])
+
+
+def _timed_min(fn, reps=3):
+    """Best of reps CUDA-event timings of fn() on the current stream (ms) and its last result."""
+    import torch
+    best, out = None, None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best, out
+
+
+def test_trained_network_against_sap_gcr():
+    """The comparison the learned preconditioner is judged by: on a 16^4
+    lattice at kappa = 0.1365 a network trained on the GPU (12 pairs from the
+    binary64 SAP-GCR solver, 150 Adam steps) preconditions flexible GCR, and
+    SAP-GCR with the Table 2 style settings (4^4 blocks, 5 MR steps, 4
+    cycles, 16 Krylov vectors) solves the same held-out source.  Both reach a
+    binary64 residual of 1e-10 (recomputed by the oracle and equal to the
+    reported one within 1e-3 relative); the network keeps the whole solve (no
+    fallback to SAP) and reaches the target in less time than SAP-GCR."""
+    from paper_2202_07388_gb300 import oq
+    dims = (16, 16, 16, 16)
+    kappa = 0.1365
+    u, a, ainv = oracle_case(dims, 0.5, 191, kappa, 1.0)
+    h = make_handle(dims, u, kappa, 1.0, oq.LINK_12)
+    for p in (oq.F32, oq.F64):
+        h.autotune(p, nrhs=1)
+    sap = oq.SolverParams(res=1e-10, nmx=2000, nkv=16, ncy=4, nmr=5, bs=(4, 4, 4, 4), sdtype=oq.F32)
+    ntrain = 12
+    r = synth.make_source(dims, 192, nrhs=ntrain)
+    e = np.zeros_like(r)
+    for k in range(ntrain):
+        psi = to_dev(np.zeros_like(r[k]))
+        rc, _ = h.sap_gcr(to_dev(r[k]), psi, sap)
+        assert rc == oq.OK
+        e[k] = from_dev(psi, r[k].shape)
+    wc = np.zeros(NW1 + NW2, complex)
+    W1 = wc[:NW1].reshape(9, 2, 1, 4, 4)
+    W2 = wc[NW1:].reshape(9, 1, 2, 4, 4)
+    W1[0, 0, 0] = np.eye(4)
+    W2[0, 0, 0] = np.eye(4) * (2 * kappa)
+    w = np.empty(2 * wc.size, np.float32)
+    w[0::2], w[1::2] = wc.real, wc.imag
+    wd = _wdev(w)
+    losses = h.nnprec_train(wd, _packed(h, oq, r), _packed(h, oq, e), ntrain, 0.01, 150)
+    assert losses[-1] < 0.8 * losses[0]
+    eta = synth.make_source(dims, 199)
+    plain = oq.SolverParams(res=1e-10, nmx=2000, nkv=16, ncy=0, sdtype=oq.F32)
+    results = {}
+    for name, run in (("nn_gcr", lambda x: h.nn_gcr(wd, to_dev(eta), x, plain)),
+                      ("sap_gcr", lambda x: h.sap_gcr(to_dev(eta), x, sap))):
+        x = to_dev(np.zeros_like(eta))
+        ms, (rc, st) = _timed_min(lambda: run(x))
+        assert rc == oq.OK and st[0]["converged"], name
+        xs = from_dev(x, eta.shape)
+        res = np.linalg.norm(eta - dirac.dw(u, a, xs)) / np.linalg.norm(eta)
+        assert res <= 1e-10 * (1 + 1e-3) and abs(res - st[0]["true_rel_res"]) <= 1e-3 * res, name
+        results[name] = (ms, st[0])
+    assert results["nn_gcr"][1]["nn_fallback"] == 0
+    assert results["nn_gcr"][0] < results["sap_gcr"][0], results
+    h.close()
 
 
 def _direct_path_network(w1, w2):
@@ -203,7 +272,7 @@ def test_useless_network_falls_back_to_sap():
     assert rc == oq.OK and st[0]["converged"]
     assert st[0]["nn_fallback"] == 1 and st[0]["cycles"] > 0
     x = from_dev(psi, eta.shape)
-    assert np.linalg.norm(eta - dirac.dw(u, a, x)) / np.linalg.norm(eta) <= 1.2e-10
+    check_residual(np.linalg.norm(eta - dirac.dw(u, a, x)) / np.linalg.norm(eta), st[0]["true_rel_res"])
     psi = to_dev(np.zeros_like(eta))
     rc, st = h.nn_gcr(_direct_path_network(np.eye(4), np.eye(4) * (2 * kappa)), to_dev(eta), psi, gprm)
     assert rc == oq.OK and st[0]["nn_fallback"] == 0 and st[0]["cycles"] == 0

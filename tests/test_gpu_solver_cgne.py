@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dirac, solvers
 from paper_2202_07388_gb300 import synth
-from tests.gpu_cases import oracle_case, make_handle, to_dev, from_dev
+from tests.gpu_cases import oracle_case, make_handle, to_dev, from_dev, check_residual
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,7 @@ def test_cgne_true_residual(dims, eps, seed, kappa, prec):
     assert rc == oq.OK and st[0]["converged"]
     x = from_dev(psi, eta.shape)
     assert np.max(np.abs(dirac.odd_part(x))) == 0.0
-    assert _normal_residual(u, a, ainv, eta, x) <= 1.2e-10
+    check_residual(_normal_residual(u, a, ainv, eta, x), st[0]["true_rel_res"])
     assert st[0]["true_rel_res"] <= 1e-10
     if prec == oq.F64:
         ref = solvers.cgne(lambda v: dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, v)),
@@ -58,7 +58,7 @@ def test_cgne_multi_rhs_and_reset_ordering():
         assert rc == oq.OK
         x = from_dev(psi, eta.shape)
         for k in range(n):
-            assert _normal_residual(u, a, ainv, eta[k], x[k]) <= 1.2e-10
+            check_residual(_normal_residual(u, a, ainv, eta[k], x[k]), st[k]["true_rel_res"])
         resets[prec] = np.mean([s["resets"] for s in st])
     assert resets[2] > resets[3] > resets[1]   # bf16 > fp16 > fp32 (Sec. 2)
 
@@ -81,7 +81,7 @@ def test_cgne_double_float_resets(prec):
         psi = to_dev(np.zeros_like(eta))
         rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5000, sdtype=prec))
         assert rc == oq.OK and st[0]["converged"]
-        assert _normal_residual(u, a, ainv, eta, from_dev(psi, eta.shape)) <= 1.2e-10
+        check_residual(_normal_residual(u, a, ainv, eta, from_dev(psi, eta.shape)), st[0]["true_rel_res"])
         assert st[0]["true_rel_res"] <= 1e-10
         out[df] = st[0]
     assert abs(out[1]["resets"] - out[0]["resets"]) <= 1
@@ -123,4 +123,37 @@ def test_cgne_even_site_layout(dims):
     assert np.array_equal(full[:, ev], half)
     assert [s["steps"] for s in st] == [s["steps"] for s in st2]
     for k in range(n):
-        assert _normal_residual(u, a, ainv, eta[k], from_dev(psi, eta.shape)[k]) <= 1.2e-10
+        check_residual(_normal_residual(u, a, ainv, eta[k], from_dev(psi, eta.shape)[k]), st[k]["true_rel_res"])
+
+
+@pytest.mark.parametrize("launch", ["tuned", "bench_shapes"])
+def test_bench_configuration_end_to_end(launch):
+    """The configuration bench.py times, on a 16 x 8^3 lattice the oracle
+    checks in seconds: the 12 spin-colour point sources at the origin,
+    eta = Dhat^dag bhat, one batched call with binary16 storage, binary32
+    arithmetic, double-float intermediate resets and a binary64 final reset.
+    Launches as the autotuner picks them, or pinned to the bench's tuned
+    shapes on the 64 x 32^3 lattice (pass 1: 32 x 2 threads, 2 rhs per thread,
+    hop operands staged in shared memory; pass 2: 128 threads, 2 rhs per
+    thread, register cap).  Every right-hand side reaches 1e-10 with the
+    oracle's Dhat^dag Dhat and the reported residual agrees with it."""
+    oq = _oq()
+    dims = (16, 8, 8, 8)
+    u, a, ainv = oracle_case(dims, 0.6, 3, 0.135, 1.0)
+    b = synth.make_point_sources(dims)
+    eta = np.stack([dirac.dw_hat_dagger(u, a, ainv, dirac.even_part(b[k])) for k in range(12)])
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+    if launch == "tuned":
+        for p in (oq.F16, oq.F64, oq.DF64):
+            h.autotune(p, nrhs=12)
+    else:
+        h.tune_set(oq.F16, 1, 12, 32, 2, nr=2, regcap=2, link_fmt=oq.LINK_12)
+        h.tune_set(oq.F16, 2, 12, 128, 1, nr=2, regcap=1, link_fmt=oq.LINK_12)
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=20000, sdtype=oq.F16), nrhs=12)
+    assert rc == oq.OK
+    x = from_dev(psi, eta.shape)
+    for k in range(12):
+        assert st[k]["converged"] and st[k]["resets"] >= 2
+        check_residual(_normal_residual(u, a, ainv, eta[k], x[k]), st[k]["true_rel_res"])
+    h.close()
