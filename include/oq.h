@@ -84,6 +84,14 @@ typedef struct {
                 across x0 = T-1 <-> 0), or 0 = Schroedinger functional (openQCD boundary
                 type 1, Sec. 2 footnote): quark fields vanish at x0 = 0 and x0 = T,
                 or OQ_BC_HALO: a time-split sub-domain (see oq_face_pack) */
+  int cstar; /* C* boundary conditions in this many spatial directions (0 = periodic; 1: x1;
+                2: x1, x2; 3: x1, x2, x3), in the orbifold form of openQ*D (Sec. 1): the
+                library's lattice is doubled in x1 (extent 2 L[1]; its fields, canonical
+                or packed, have that extent), the second half carrying the
+                charge-conjugate copy of the gauge field (oq_gauge_upload takes the
+                physical links, of extent L[1], and stores their complex conjugates
+                there, U(1) angles negated); a hop across the x2 or x3 boundary of a
+                C* direction also moves x1 by L[1].  L[1] must be even. */
 } oq_lattice;
 
 /* bc_t of a sub-domain of a lattice split along time (Sec. 3: the lattice is

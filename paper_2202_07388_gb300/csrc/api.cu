@@ -58,7 +58,8 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
       if (lats[k].L[mu] < 2 || (lats[k].L[mu] & 1)) return OQ_ERR_ARG;
     if (lats[k].bc_t != 1 && lats[k].bc_t != -1 && lats[k].bc_t != 0 && lats[k].bc_t != OQ_BC_HALO)
       return OQ_ERR_ARG;
-    const double v = (double)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3];
+    if (lats[k].cstar < 0 || lats[k].cstar > 3) return OQ_ERR_ARG;
+    const double v = (double)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3] * (lats[k].cstar ? 2 : 1);
     if (v > (double)(1L << 29)) return OQ_ERR_ARG;  // Vh <= 2^28: 32-bit site offsets
   }
   oq_ctx* h = new (std::nothrow) oq_ctx();
@@ -71,8 +72,12 @@ extern "C" int oq_create(oq_handle* out, const oq_lattice* lats, int nlat) {
   for (int k = 0; k < nlat; ++k) {
     LatCtx& L = h->lats[k];
     for (int mu = 0; mu < 4; ++mu) L.g.L[mu] = lats[k].L[mu];
+    // C* boundaries: the orbifold lattice doubled in x1, x2 / x3 wraps shifted
+    L.cstar = lats[k].cstar;
+    if (L.cstar) L.g.L[1] *= 2;
+    L.g.cs_shift = (L.cstar >= 2 ? 4 : 0) | (L.cstar >= 3 ? 8 : 0);
     L.g.Lh3 = lats[k].L[3] / 2;
-    L.g.Vh = (long)lats[k].L[0] * lats[k].L[1] * lats[k].L[2] * lats[k].L[3] / 2;
+    L.g.Vh = (long)L.g.L[0] * L.g.L[1] * L.g.L[2] * L.g.L[3] / 2;
     L.halo_t = lats[k].bc_t == OQ_BC_HALO;
     L.g.bc_t = L.halo_t ? 1.0f : (float)lats[k].bc_t;  // a sub-domain's boundary factors come with its faces
     geom_init_div(L.g);
@@ -129,7 +134,7 @@ static int gauge_upload(oq_handle h, int lat, const double* U_dev, const double*
   void* u18 = link_fmt == OQ_LINK_12 ? L.u32_18.p : nullptr;
   if (pack_links(L.g, U_dev, (double*)L.u64.p, L.u32.p, link_fmt, u18, A_dev, q,
                  (sf || A_dev) ? (double*)L.uclov.p : nullptr, A_dev ? (double*)L.au1.p : nullptr,
-                 s) != cudaSuccess)
+                 s, L.cstar ? L.g.L[1] / 2 : 0) != cudaSuccess)
     return OQ_ERR_CUDA;
   if (sf && sf_mask_links(L.g, (double*)L.u64.p, L.u32.p, link_fmt, u18, s) != cudaSuccess) return OQ_ERR_CUDA;
   L.uclov_valid = sf || A_dev;

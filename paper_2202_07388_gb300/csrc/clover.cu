@@ -65,12 +65,22 @@ __device__ __forceinline__ M3 dmul(const M3& a, const M3& b) {
   return c;
 }
 
+// y += d mu (d = -1, 0, +1) on the periodic lattice, with the x1 shift of a
+// C* boundary when the step wraps
+__device__ __forceinline__ void displace(const Geom& g, int y[4], int mu, int d) {
+  if (!d) return;
+  int v = y[mu] + d;
+  const bool wrap = v < 0 || v >= g.L[mu];
+  y[mu] = (v + g.L[mu]) % g.L[mu];
+  if (wrap) y[1] = cs_x1(g, mu, y[1]);
+}
+
 // the link U_mu(y), y = x + d1 mu1 + d2 mu2; with au1 times exp(i q A_mu(y))
 __device__ __forceinline__ M3 link_at(const Geom& g, const double2* u64, const int x[4], int mu, int d1, int mu1,
                                       int d2, int mu2, const double* au1 = nullptr, double q = 0.0) {
   int y[4] = {x[0], x[1], x[2], x[3]};
-  if (d1) y[mu1] = (y[mu1] + d1 + g.L[mu1]) % g.L[mu1];
-  if (d2) y[mu2] = (y[mu2] + d2 + g.L[mu2]) % g.L[mu2];
+  displace(g, y, mu1, d1);
+  displace(g, y, mu2, d2);
   const int p = (y[0] + y[1] + y[2] + y[3]) & 1;
   const long j = eo_index(g, y);
   Su3<double> u;
@@ -128,8 +138,8 @@ __device__ M3 field_strength(const Geom& g, const double2* u64, const int x[4], 
 __device__ __forceinline__ double angle_at(const Geom& g, const double* au1, const int x[4], int mu, int d1,
                                            int mu1, int d2, int mu2) {
   int y[4] = {x[0], x[1], x[2], x[3]};
-  if (d1) y[mu1] = (y[mu1] + d1 + g.L[mu1]) % g.L[mu1];
-  if (d2) y[mu2] = (y[mu2] + d2 + g.L[mu2]) % g.L[mu2];
+  displace(g, y, mu1, d1);
+  displace(g, y, mu2, d2);
   const int p = (y[0] + y[1] + y[2] + y[3]) & 1;
   return au1[(long)(p * 4 + mu) * g.Vh + eo_index(g, y)];
 }

@@ -41,6 +41,9 @@ struct LatCtx {
   // read faces of the neighbouring sub-domains; uext holds the packed binary64
   // links of the sub-domain extended by one slice on each side (clover build)
   bool halo_t = false, has_uext = false;
+  // C* boundaries in this many spatial directions (x1 first): the lattice is
+  // doubled in x1 (g.L[1] = 2 L1); 0 = none
+  int cstar = 0;
   DevBuf uext;
   double qcharge = 0.0, cF = 1.0, csw_qed = 0.0;
   std::map<std::string, DevBuf> ws;

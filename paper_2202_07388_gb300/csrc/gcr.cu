@@ -220,6 +220,8 @@ extern "C" int oq_sap_apply(oq_handle h, int lat, const oq_solver_params* prm, c
     bvol *= b;
   }
   if (bvol > 256) return OQ_ERR_ARG;
+  // shifted (C*) wraps keep the block colouring only if the x1 shift is an even number of blocks
+  if (L.g.cs_shift && ((L.g.L[1] / 2) / prm->bs[1]) % 2) return OQ_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const long f32 = 2 * spinor_half_bytes(L.g.Vh, P_F32);
   if (cudaMemsetAsync(phi_dev, 0, f32, s) != cudaSuccess) return OQ_ERR_CUDA;
@@ -266,6 +268,8 @@ static int gcr_impl(oq_handle h, int lat, const oq_solver_params* prm, const flo
       bvol *= b;
     }
     if (bvol > 256) return OQ_ERR_ARG;
+    // shifted (C*) wraps keep the block colouring only if the x1 shift is an even number of blocks
+    if (L.g.cs_shift && ((L.g.L[1] / 2) / prm->bs[1]) % 2) return OQ_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   const long Vh = L.g.Vh;

@@ -233,14 +233,15 @@ extern "C" int oq_gauge_upload_halo(oq_handle h, int lat, const double* U_ext_de
   const long Fs = L.g.Vh / L.g.L[0];
   // the hopping links: slices 0 .. T_loc-1 of the extended field (canonical
   // site x0 = 0 of the sub-domain starts one slice, 2 Fs sites of 72 reals, in)
-  int rc = oq_gauge_upload(h, lat, U_ext_dev + (size_t)2 * Fs * 72, link_fmt, stream);
+  const long Fs_in = L.cstar ? Fs / 2 : Fs;  // C*: the uploaded links are the physical (undoubled) ones
+  int rc = oq_gauge_upload(h, lat, U_ext_dev + (size_t)2 * Fs_in * 72, link_fmt, stream);
   if (rc) return rc;
   // the extended links for the clover build
   Geom ge = halo_ext_geom(L.g);
   rc = h->alloc(&L.uext, sizeof(double) * 2 * 4 * 18 * ge.Vh);
   if (rc) return rc;
-  if (pack_links(ge, U_ext_dev, (double*)L.uext.p, nullptr, LINK_18, nullptr, nullptr, 0.0, nullptr, nullptr, s) !=
-      cudaSuccess)
+  if (pack_links(ge, U_ext_dev, (double*)L.uext.p, nullptr, LINK_18, nullptr, nullptr, 0.0, nullptr, nullptr, s,
+                 L.cstar ? L.g.L[1] / 2 : 0) != cudaSuccess)
     return OQ_ERR_CUDA;
   L.has_uext = true;
   return OQ_OK;

@@ -392,12 +392,20 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
     jf[mu] = x[mu] == g.L[mu] - 1 ? i - wrap : i + st[mu];
     jb[mu] = x[mu] == 0 ? i + wrap : i - st[mu];
   }
+  // C* boundaries: a wrapped hop along x2 or x3 also moves x1 by half its extent
+  const uint32_t h1 = (uint32_t)(g.L[1] >> 1) * s1;
+  const uint32_t dcs = x[1] < (g.L[1] >> 1) ? h1 : (uint32_t)0 - h1;
+  if (g.cs_shift & 4) {
+    if (x[2] == g.L[2] - 1) jf[2] += dcs;
+    if (x[2] == 0) jb[2] += dcs;
+  }
   {
     const uint32_t row = i - (uint32_t)(x[3] >> 1);
     const int xf = x[3] + 1 == g.L[3] ? 0 : x[3] + 1;
     const int xb = x[3] == 0 ? g.L[3] - 1 : x[3] - 1;
-    jf[3] = row + (uint32_t)(xf >> 1);
-    jb[3] = row + (uint32_t)(xb >> 1);
+    const uint32_t s3 = (g.cs_shift & 8) ? dcs : 0u;
+    jf[3] = row + (uint32_t)(xf >> 1) + (x[3] + 1 == g.L[3] ? s3 : 0u);
+    jb[3] = row + (uint32_t)(xb >> 1) + (x[3] == 0 ? s3 : 0u);
   }
   const F2 sf = bc(x[0] == g.L[0] - 1 ? g.bc_t : 1.f);  // forward time hop crosses the boundary
   const F2 sb = bc(x[0] == 0 ? g.bc_t : 1.f);

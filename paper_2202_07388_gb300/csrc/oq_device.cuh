@@ -206,7 +206,18 @@ struct Geom {
   // (n * dm) >> ds, exact for n < 2^31 (geom_init_div)
   uint32_t dm[3];
   int ds[3];
+  // C* boundaries (orbifold form): bit mu (2 or 3) set = a hop across the
+  // x_mu boundary also moves x1 by L[1] / 2 (the lattice is doubled in x1,
+  // its second half holding the charge-conjugate copy)
+  int cs_shift;
 };
+
+// x1 after a hop along mu that wrapped (C* boundaries shift it by half the doubled extent)
+__host__ __device__ __forceinline__ int cs_x1(const Geom& g, int mu, int x1) {
+  if (!((g.cs_shift >> mu) & 1)) return x1;
+  const int h = g.L[1] >> 1;
+  return x1 < h ? x1 + h : x1 - h;
+}
 
 // Multipliers for geom's 32-bit divisions: for d >= 1 let l be the smallest
 // integer with 2^l >= d, m = ceil(2^(31+l) / d) (< 2^32) and s = 31 + l.
@@ -252,6 +263,7 @@ __device__ __forceinline__ long eo_neighbour(const Geom& g, const int x[4], int 
   if (v == g.L[mu]) { v = 0; c = true; }
   if (v < 0) { v = g.L[mu] - 1; c = true; }
   y[mu] = v;
+  if (c) y[1] = cs_x1(g, mu, y[1]);
   *crossed = c && (mu == 0);
   return eo_index(g, y);
 }
@@ -265,7 +277,8 @@ __device__ __forceinline__ long eo_neighbour_rt(const Geom& g, const int x[4], i
   if (v == L) { v = 0; c = true; }
   if (v < 0) { v = L - 1; c = true; }
   *crossed = c && (mu == 0);
-  const int y0 = mu == 0 ? v : x[0], y1 = mu == 1 ? v : x[1], y2 = mu == 2 ? v : x[2], y3 = mu == 3 ? v : x[3];
+  const int y0 = mu == 0 ? v : x[0], y2 = mu == 2 ? v : x[2], y3 = mu == 3 ? v : x[3];
+  const int y1 = mu == 1 ? v : (c ? cs_x1(g, mu, x[1]) : x[1]);
   const long lex = (((long)y0 * g.L[1] + y1) * g.L[2] + y2) * g.L[3] + y3;
   return lex >> 1;
 }

@@ -9,8 +9,10 @@ namespace oq {
 // A (optional): canonical U(1) angles A_mu(x) multiplied into the links as
 // exp(i q A); uclov (optional): the packed binary64 links before the phase;
 // au1 (optional): the packed angles
+// cs_l1 > 0: C* lattice doubled in x1; canon holds the physical links (x1 < cs_l1)
+// and the second half gets their complex conjugates (U(1) angles negated)
 cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, void* u18,
-                       const double* A, double q, double* uclov, double* au1, cudaStream_t s);
+                       const double* A, double q, double* uclov, double* au1, cudaStream_t s, int cs_l1 = 0);
 // Schroedinger-functional boundaries: zero the time-like links of slices
 // x0 = 0 and x0 = T-1 in every hopping copy
 cudaError_t sf_mask_links(const Geom& g, double* u64, void* u32, int fmt, void* u18, cudaStream_t s);

@@ -15,27 +15,38 @@ __device__ __forceinline__ long lex_of(const Geom& g, const int x[4]) {
 // binary32 copy next to a 12-real one; A (optional) multiplies the link by
 // exp(i q A_mu(x)) (QCD+QED), uclov / au1 (optional) keep the link before
 // the phase and the angle
+// cs_l1 > 0 (C* boundaries): canon holds the physical links of L1 = cs_l1
+// (half the doubled extent g.L[1]); the sites x1 >= cs_l1 of the doubled
+// lattice get the charge-conjugate copy: the complex conjugate link (and the
+// U(1) angle negated)
 __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, double2* __restrict__ u64,
                                   void* __restrict__ u32, int fmt, float2* __restrict__ u18,
                                   const double* __restrict__ A, double q, double2* __restrict__ uclov,
-                                  double* __restrict__ au1) {
+                                  double* __restrict__ au1, int cs_l1) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   const int mu = blockIdx.z;
   if (i >= g.Vh) return;
   int x[4];
   eo_coords(g, p, i, x);
-  const double2* src = canon + (lex_of(g, x) * 4 + mu) * 9;
+  bool mirror = false;
+  long lex = lex_of(g, x);
+  if (cs_l1 > 0) {
+    mirror = x[1] >= cs_l1;
+    const int x1 = mirror ? x[1] - cs_l1 : x[1];
+    lex = (((long)x[0] * cs_l1 + x1) * g.L[2] + x[2]) * g.L[3] + x[3];
+  }
+  const double2* src = canon + (lex * 4 + mu) * 9;
   double2 m[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) m[k] = src[k];
+  for (int k = 0; k < 9; ++k) m[k] = mirror ? make_double2(src[k].x, -src[k].y) : src[k];
   if (uclov) {
     double2* d = uclov + ((long)(p * 4 + mu) * 9) * g.Vh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) d[k * g.Vh + i] = m[k];
   }
   if (A) {
-    const double a = A[lex_of(g, x) * 4 + mu];
+    const double a = mirror ? -A[lex * 4 + mu] : A[lex * 4 + mu];
     double sn, cs;
     sincos(q * a, &sn, &cs);
 #pragma unroll
@@ -64,12 +75,12 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, dou
 }
 
 cudaError_t pack_links(const Geom& g, const double* canon, double* u64, void* u32, int fmt, void* u18,
-                       const double* A, double q, double* uclov, double* au1, cudaStream_t s) {
+                       const double* A, double q, double* uclov, double* au1, cudaStream_t s, int cs_l1) {
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), 2, 4);
   pack_links_kernel<<<grid, block, 0, s>>>(g, reinterpret_cast<const double2*>(canon),
                                            reinterpret_cast<double2*>(u64), u32, fmt,
                                            reinterpret_cast<float2*>(u18), A, q,
-                                           reinterpret_cast<double2*>(uclov), au1);
+                                           reinterpret_cast<double2*>(uclov), au1, cs_l1);
   return cudaGetLastError();
 }
 

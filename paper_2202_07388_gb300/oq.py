@@ -32,7 +32,7 @@ ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_NOCONV, ERR_STATE 
 
 
 class OqLattice(C.Structure):
-    _fields_ = [("L", C.c_int * 4), ("bc_t", C.c_int)]
+    _fields_ = [("L", C.c_int * 4), ("bc_t", C.c_int), ("cstar", C.c_int)]
 
 
 class OqSolverParams(C.Structure):
@@ -207,7 +207,9 @@ def status_dict(s: OqStatus) -> dict:
 class Handle:
     """One library handle over one or more lattices (``dims`` tuples)."""
 
-    def __init__(self, lattices, bc_t=-1):
+    def __init__(self, lattices, bc_t=-1, cstar=0):
+        """cstar: C* boundaries in that many spatial directions; the handle's
+        fields then live on the lattice doubled in x1 (self.dims holds it)."""
         if isinstance(lattices[0], int):
             lattices = [lattices]
         n = len(lattices)
@@ -216,10 +218,11 @@ class Handle:
             for mu in range(4):
                 arr[k].L[mu] = int(d[mu])
             arr[k].bc_t = bc_t
+            arr[k].cstar = cstar
         h = C.c_void_p()
         _check(lib().oq_create(C.byref(h), arr, n), "oq_create")
         self.h = h
-        self.dims = [tuple(int(v) for v in d) for d in lattices]
+        self.dims = [tuple(int(v) * (2 if (cstar and mu == 1) else 1) for mu, v in enumerate(d)) for d in lattices]
 
     def close(self):
         if self.h:

@@ -157,7 +157,8 @@ def test_autotuner_picks_valid_shapes_and_keeps_results():
         shapes = h.autotune(prec, nrhs=4)
         for mode, (bx, by, ms, fmt, nr, cap) in shapes.items():
             assert bx % 32 == 0 and bx * by <= (256 if nr == 1 else 128) and ms > 0
-            assert fmt in ("12-real", "18-real") and nr in (1, 2, 4) and cap in (0, 1)
+            assert fmt in ("12-real", "18-real") and nr in (1, 2, 4) and cap in (0, 1, 2)
+            assert cap != 2 or (nr > 1 and fmt == "12-real")      # staged hops: multi-rhs, 12-real links
         pin, pout = h.new_packed(prec, nrhs=4), h.new_packed(prec, nrhs=4)
         h.pack(to_dev(psi), pin, prec, nrhs=4)
         h.dw(pin, pout, prec, nrhs=4)
