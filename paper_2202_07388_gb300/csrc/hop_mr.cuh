@@ -235,15 +235,76 @@ __device__ __forceinline__ void accum_col(Sp2& acc, int a, const C2& h0, const C
   }
 }
 
+// Binary16 spin projection from the stored halves: a +/- b of two binary16
+// parts as one exact conversion and one mixed-precision add (binary16 operand,
+// binary32 result, one rounding) -- the same value as converting both parts
+// and adding in binary32, with one conversion instead of two.
+// hi: the imaginary part (upper half of the packed word).
+__device__ __forceinline__ unsigned short half_of(uint32_t w, bool hi) {
+  return (unsigned short)(hi ? (w >> 16) : (w & 0xffffu));
+}
+template <bool AHI, bool BHI, bool PLUS>
+__device__ __forceinline__ float mix_f16(uint32_t wa, uint32_t wb) {
+  const unsigned short a = half_of(wa, AHI), b = half_of(wb, BHI);
+  float d, t;
+  if constexpr (PLUS) {
+    asm("cvt.f32.f16 %0, %1;" : "=f"(t) : "h"(a));
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(b), "f"(t));
+  } else {
+    asm("cvt.f32.f16 %0, %1;" : "=f"(t) : "h"(b));
+    asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(t));
+  }
+  return d;
+}
+__device__ __forceinline__ uint32_t word_of(const RawSp<P_F16>& n, int k) {
+  const uint4 v = n.ch[k / 4];
+  return (k % 4 == 0) ? v.x : (k % 4 == 1) ? v.y : (k % 4 == 2) ? v.z : v.w;
+}
+// h = upper (spin U) + or - the partner (spin L), straight (re with re) or
+// crossed (re with im: the factor i of the projector); SRE / SIM the signs
+template <int U, int L, bool CROSS, int SRE, int SIM>
+__device__ __forceinline__ C2 proj_f16(const RawSp<P_F16>& n0, const RawSp<P_F16>& n1, int a) {
+  const uint32_t u0 = word_of(n0, 3 * U + a), l0 = word_of(n0, 3 * L + a);
+  const uint32_t u1 = word_of(n1, 3 * U + a), l1 = word_of(n1, 3 * L + a);
+  C2 h;
+  h.re = make_float2(mix_f16<false, CROSS, (SRE > 0)>(u0, l0), mix_f16<false, CROSS, (SRE > 0)>(u1, l1));
+  h.im = make_float2(mix_f16<true, !CROSS, (SIM > 0)>(u0, l0), mix_f16<true, !CROSS, (SIM > 0)>(u1, l1));
+  return h;
+}
+
 // One hop for a pair of right-hand sides, with little live state: the
 // projection reads the loaded chunks (n0, n1) directly, and each colour row
 // of U h (or U^dag h) is accumulated into acc as soon as it is formed, so
 // neither the converted neighbour spinor nor the transported half spinor is
 // held whole.  Same linear maps as project, su3 and accum_col.
-template <int P, int MU, int S, bool UD>
+// MIX (binary16 only): the projection by mixed-precision adds (proj_f16);
+// the kernels with the CG-update epilogue keep the converting form, which
+// needs fewer registers there
+template <int P, int MU, int S, bool UD, bool MIX = true>
 __device__ __forceinline__ void hop_pair(const Su3<float>& u, const RawSp<P>& n0, const RawSp<P>& n1, Sp2& acc,
                                          F2 wt) {
   Hs2 h;
+  if constexpr (P == P_F16 && MIX) {
+    // the projectors' tables (as for the binary32 forms below): partner spin,
+    // crossing by the factor i, signs of the real and imaginary parts
+    constexpr int SP = S < 0 ? +1 : -1, SM = -SP;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if constexpr (MU == 0) {
+        h.c[0][a] = proj_f16<0, 2, false, SP, SP>(n0, n1, a);
+        h.c[1][a] = proj_f16<1, 3, false, SP, SP>(n0, n1, a);
+      } else if constexpr (MU == 1) {
+        h.c[0][a] = proj_f16<0, 3, true, SM, SP>(n0, n1, a);
+        h.c[1][a] = proj_f16<1, 2, true, SM, SP>(n0, n1, a);
+      } else if constexpr (MU == 2) {
+        h.c[0][a] = proj_f16<0, 3, false, SP, SP>(n0, n1, a);
+        h.c[1][a] = proj_f16<1, 2, false, SM, SM>(n0, n1, a);
+      } else {
+        h.c[0][a] = proj_f16<0, 2, true, SM, SP>(n0, n1, a);
+        h.c[1][a] = proj_f16<1, 3, true, SP, SM>(n0, n1, a);
+      }
+    }
+  } else {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     C2 pc[4];
@@ -265,6 +326,7 @@ __device__ __forceinline__ void hop_pair(const Su3<float>& u, const RawSp<P>& n0
       if constexpr (S < 0) { h.c[0][a] = cadd_i(pc[0], pc[2]); h.c[1][a] = csub_i(pc[1], pc[3]); }
       else                 { h.c[0][a] = csub_i(pc[0], pc[2]); h.c[1][a] = cadd_i(pc[1], pc[3]); }
     }
+  }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -497,7 +559,7 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       RawSp<P> n0, n1;
       n0.load(in[2 * q], Vh, jf[MU]);
       n1.load(in[2 * q + 1], Vh, jf[MU]);
-      hop_pair<P, MU, SF, false>(u, n0, n1, acc[q], MU == 0 ? wf : w);
+      hop_pair<P, MU, SF, false, EPI != EPI_CG>(u, n0, n1, acc[q], MU == 0 ? wf : w);
     }
     // backward: U_mu(x - mu)^dag (1 +/- g) psi(x - mu)
     load_u<FMT>(a.links, Vh, 1 - p, MU, jb[MU], u);
@@ -506,7 +568,7 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       RawSp<P> n0, n1;
       n0.load(in[2 * q], Vh, jb[MU]);
       n1.load(in[2 * q + 1], Vh, jb[MU]);
-      hop_pair<P, MU, -SF, true>(u, n0, n1, acc[q], MU == 0 ? wb : w);
+      hop_pair<P, MU, -SF, true, EPI != EPI_CG>(u, n0, n1, acc[q], MU == 0 ? wb : w);
     }
   };
   // staged form: wait for hop H's copies while hop H + 1's are in flight
@@ -536,7 +598,7 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
         n0.ch[c] = *stg.at(st, (2 * q) * SC + c, NSLOT);
         n1.ch[c] = *stg.at(st, (2 * q + 1) * SC + c, NSLOT);
       }
-      hop_pair<P, MU, FWD ? SF : -SF, !FWD>(u, n0, n1, acc[q], MU == 0 ? (FWD ? wf : wb) : w);
+      hop_pair<P, MU, FWD ? SF : -SF, !FWD, EPI != EPI_CG>(u, n0, n1, acc[q], MU == 0 ? (FWD ? wf : wb) : w);
     }
   };
   if constexpr (PF) {
