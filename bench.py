@@ -17,11 +17,11 @@ roofline = the dominant stencil source kernel (plain and adjoint
            CUDA-event duration over launches that did work, against the
            measured HBM copy peak
 e2e      = the same bytes / time of the public call with host buffers
-           (pinned host -> device copy of eta, solve, device -> host psi;
-           even-site canonical fields, oq_cgne_solve_even), the copies of a
-           stream of steps overlapped with the solves; the serial timing of
-           each phase, and that of full-lattice fields (oq_cgne_solve), are
-           reported next to it
+           (even-site canonical fields, oq_cgne_solve_even): the pinned host
+           buffers go to the solver, whose packing kernel reads the sources
+           and unpacking kernel writes the solutions over the host-device
+           link; copy-engine variants (pipelined on a second stream, serial,
+           full-lattice fields) are reported next to it
 tts      = time to solution of one right-hand side: binary64-only CGNE vs
            the mixed-precision solves (the "vs plain FP64 GPU" comparison),
            and the precision ladders (one and 12 right-hand sides)
@@ -562,11 +562,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / args.e2e_steps
 
-    # the buffers are made right before they are used (pinned buffers made at
-    # set-up, before the tuning and the timed solves, copied at 20-60 GB/s
-    # instead of ~200 GB/s on the GPU machine).  The source of the even system
-    # lives on the even sites, so the headline stream uses even-site canonical
-    # fields (oq_cgne_solve_even, half the bytes of full fields).
+    def e2e_zero_copy(solve, e_host, p_host):
+        """Each step hands the solver the pinned host buffers themselves: its
+        packing kernel reads the 12 sources from host memory and its unpacking
+        kernel writes the 12 solutions back over the host-device link (the
+        copy engine's first transfer through a pinned buffer after other
+        device work ran at 6-40 GB/s on the GPU machine; the kernels' many parallel
+        requests do not wait on it).  Returns ms per step (CUDA events)."""
+        solve(e_host, p_host)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.e2e_steps):
+            rc_, _ = solve(e_host, p_host)
+            assert rc_ == oq.OK
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / args.e2e_steps
+
+    # The source of the even system lives on the even sites, so the headline
+    # uses even-site canonical fields (oq_cgne_solve_even, half the bytes of
+    # full fields).
     full = eta.cpu().numpy().view(np.complex128).reshape((NRHS, -1, 12))
     lexp = np.indices(DIMS).sum(axis=0).reshape(-1) % 2
     eta_host = torch.from_numpy(np.ascontiguousarray(full[:, lexp == 0]).view(np.float64)).pin_memory()
@@ -575,9 +591,17 @@ def run_ours(args):
     eta_devs = [torch.empty(eta_host.shape, dtype=eta_host.dtype, device=eta.device) for _ in range(2)]
     psi_devs = [torch.empty_like(eta_devs[0]) for _ in range(2)]
     solve_even = lambda e, p: h.cgne_even(e, p, prm, nrhs=NRHS)  # noqa: E731
+    e2e_ms = e2e_zero_copy(solve_even, eta_host, psi_hosts[0])
     ser_ms, ser_h2d, ser_solve, ser_d2h = e2e_time(solve_even, eta_host, eta_devs[0], psi_devs[0], psi_hosts[0])
-    e2e_ms = e2e_pipelined(solve_even, eta_host, eta_devs, psi_devs, psi_hosts)
+    dma_ms = e2e_pipelined(solve_even, eta_host, eta_devs, psi_devs, psi_hosts)
     e2e_value = (stencil_bytes / args.steps) / (e2e_ms * 1e-3) / 1e9
+    # the solution written to host memory is the device solve's
+    psi_check = torch.empty_like(eta_devs[0])
+    solve_even(eta_host.to(psi_check.device), psi_check)
+    solve_even(eta_host, psi_hosts[1])
+    torch.cuda.synchronize()
+    e2e_same = bool(torch.equal(psi_hosts[1], psi_check.cpu()))
+    del psi_check
     e2e_bytes = int(eta_host.numel() * 8)
     del eta_devs, psi_devs, psi_hosts, eta_host
     # full-lattice canonical fields (odd sites zero, oq_cgne_solve), serial, for comparison
@@ -718,10 +742,14 @@ def run_ours(args):
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes,
                     "ms_per_step": e2e_ms, "layout": "even-site canonical fields (oq_cgne_solve_even)",
                     "steps": args.e2e_steps,
-                    "pipelining": "the next step's H2D and the previous step's D2H on a second stream, "
-                                  "overlapping the current solve",
+                    "method": "pinned host buffers passed to the solver: its packing kernel reads the sources "
+                              "and its unpacking kernel writes the solutions over the host-device link",
+                    "same_as_device_buffers": e2e_same,
+                    "dma_pipelined": {"ms_per_step": dma_ms,
+                                      "note": "copy-engine H2D / D2H into device buffers on a second stream, "
+                                              "overlapping the previous / next solve"},
                     "serial": {"ms_per_step": ser_ms, "h2d_ms": ser_h2d, "solve_ms": ser_solve, "d2h_ms": ser_d2h,
-                               "note": "median over steps of H2D, solve and D2H one after the other"},
+                               "note": "median over steps of copy-engine H2D, solve and D2H one after the other"},
                     "serial_full_layout": {"ms_per_step": e2e_full[0], "h2d_ms": e2e_full[1],
                                            "solve_ms": e2e_full[2], "d2h_ms": e2e_full[3],
                                            "bytes_each_way": 2 * e2e_bytes,

@@ -405,7 +405,12 @@ int oq_axpby(oq_handle h, int lat, int prec, int subset, const double* a_host, c
  * arithmetic; reductions, the solution and reset-step residuals are
  * binary64.  Stops when the binary64 residual ||eta - Dhat^dag Dhat psi|| <=
  * res ||eta||, or after nmx regular steps (OQ_ERR_NOCONV).  st: host array
- * of nrhs entries. */
+ * of nrhs entries.  eta_dev and psi_dev may also be page-locked host memory
+ * (cudaHostAlloc or cudaHostRegister; CUDA maps it into the device's address
+ * space at the same address): the solver's packing kernel then reads the
+ * sources and its unpacking kernel writes the solutions over the host-device
+ * link, with no separate copy.  Any other pointer (pageable host memory)
+ * gives OQ_ERR_ARG. */
 int oq_cgne_solve(oq_handle h, int lat, const oq_solver_params* p, const double* eta_dev,
                   double* psi_dev, int nrhs, oq_status* st, void* stream);
 

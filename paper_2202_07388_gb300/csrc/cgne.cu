@@ -64,11 +64,25 @@ double default_delta(int prec) {
 
 }  // namespace
 
+// eta / psi of the solvers: device memory, or page-locked host memory that
+// CUDA maps into the device's address space at the same address (the pack
+// and unpack kernels then read and write it over the host link themselves)
+static bool kernel_addressable(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeHost && at.devicePointer == p;
+}
+
 // half: eta / psi hold the even sites only (lexicographic index / 2)
 static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const double* eta_dev, double* psi_dev,
                      int nrhs, oq_status* st, void* stream, int half) {
   if (!h || lat < 0 || lat >= (int)h->lats.size() || !prm || !eta_dev || !psi_dev || nrhs < 1 || !st) return OQ_ERR_ARG;
   if (!(prm->res > 0.0) || prm->nmx < 1 || prm->nladder < 0 || prm->nladder > 4) return OQ_ERR_ARG;
+  if (!kernel_addressable(eta_dev) || !kernel_addressable(psi_dev)) return OQ_ERR_ARG;
   // the storage types of the phases: sdtype alone, or the ladder
   std::vector<int> phase_prec;
   if (prm->nladder == 0) phase_prec.push_back(prm->sdtype);
@@ -398,8 +412,9 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
     for (int k = 0; k < chunk; ++k) RK(iteration());
   }
 
-  // psi = x_d on the even sites, zero on the odd sites
-  CK(cudaMemsetAsync(psi_dev, 0, canon_field * nrhs, s));
+  // psi = x_d on the even sites, zero on the odd sites (the even-site layout
+  // has no odd sites: every entry is written by the unpacking)
+  if (!half) CK(cudaMemsetAsync(psi_dev, 0, canon_field * nrhs, s));
   KL(unpack_spinor(L.g, P_F64, OQ_EVEN, xd, psi_dev, 1.0, nrhs, (long)h64, canon_stride, s, half));
   CK(cudaStreamSynchronize(s));
   int ret = OQ_OK;

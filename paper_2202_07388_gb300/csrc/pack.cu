@@ -191,9 +191,106 @@ __global__ void unpack_spinor_kernel(Geom g, const char* __restrict__ in, double
     dst[k] = make_double2((double)s.c[k / 3][k % 3].re * inv_scale, (double)s.c[k / 3][k % 3].im * inv_scale);
 }
 
+// Even-site (or odd-site) canonical fields: the site of eo index i sits at
+// position i (lex / 2), so the 128 sites of a CTA are one contiguous run of
+// 128 x 12 double2.  The run moves between the canonical field and shared
+// memory with consecutive threads on consecutive 16-byte chunks (coalesced,
+// which matters when the field is page-locked host memory read or written
+// over the host-device link), and each thread converts its own site from
+// there.  Shared rows of 13 chunks keep the per-site accesses free of bank
+// conflicts.  blockDim.x = 128.
+constexpr int HB = 128, HROW = 13;
+
+template <int P>
+__global__ void __launch_bounds__(HB) pack_half_kernel(Geom g, const double2* __restrict__ canon,
+                                                       char* __restrict__ out, int p, long canon_stride,
+                                                       long out_stride, double scale) {
+  typedef typename PrecTraits<P>::R R;
+  __shared__ double2 sm[HB * HROW];
+  const int t = threadIdx.x, rhs = blockIdx.z;
+  const long i0 = (long)blockIdx.x * HB;
+  const int nsite = (int)(g.Vh - i0 < HB ? g.Vh - i0 : HB);
+  const double2* src = canon + rhs * canon_stride + i0 * 12;
+  for (int e = t; e < nsite * 12; e += HB) sm[(e / 12) * HROW + e % 12] = src[e];
+  __syncthreads();
+  if (t >= nsite) return;
+  const long i = i0 + t;
+  double sc = scale;
+  if (g.bc_t == 0.f) {  // Schroedinger-functional lattices: the field vanishes at x0 = 0
+    int x[4];
+    eo_coords(g, p, i, x);
+    if (x[0] == 0) sc = 0.0;
+  }
+  char* dst = out + rhs * out_stride;
+  if constexpr (P == P_BF16 || P == P_F16) {
+    uint4* b = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double2 v = sm[t * HROW + 4 * c + k];
+        const double re = v.x * sc, im = v.y * sc;
+        if constexpr (P == P_BF16) {
+          __nv_bfloat16 a = __double2bfloat16(re), bb = __double2bfloat16(im);
+          w[k] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(bb) << 16);
+        } else {
+          __half a = __double2half(re), bb = __double2half(im);
+          w[k] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(bb) << 16);
+        }
+      }
+      b[c * g.Vh + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    Spinor<R> sp;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const double2 v = sm[t * HROW + k];
+      sp.c[k / 3][k % 3] = cx<R>{(R)(v.x * sc), (R)(v.y * sc)};
+    }
+    store_spinor<P>(dst, g.Vh, i, sp);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(HB) unpack_half_kernel(Geom g, const char* __restrict__ in,
+                                                         double2* __restrict__ canon, long in_stride,
+                                                         long canon_stride, double inv_scale) {
+  typedef typename PrecTraits<P>::R R;
+  __shared__ double2 sm[HB * HROW];
+  const int t = threadIdx.x, rhs = blockIdx.z;
+  const long i0 = (long)blockIdx.x * HB;
+  const int nsite = (int)(g.Vh - i0 < HB ? g.Vh - i0 : HB);
+  if (t < nsite) {
+    Spinor<R> sp;
+    load_spinor<P>(in + rhs * in_stride, g.Vh, i0 + t, sp);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      sm[t * HROW + k] = make_double2((double)sp.c[k / 3][k % 3].re * inv_scale,
+                                      (double)sp.c[k / 3][k % 3].im * inv_scale);
+  }
+  __syncthreads();
+  double2* dst = canon + rhs * canon_stride + i0 * 12;
+  for (int e = t; e < nsite * 12; e += HB) dst[e] = sm[(e / 12) * HROW + e % 12];
+}
+
 cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon, void* out, double scale,
                         int nrhs, long canon_stride_d2, long out_stride_bytes, cudaStream_t s, int half) {
   if (half && subset == 2) return cudaErrorInvalidValue;
+  if (half) {
+    dim3 hb(HB), hg((unsigned)((g.Vh + HB - 1) / HB), 1, nrhs);
+    const double2* c = reinterpret_cast<const double2*>(canon);
+    char* o = reinterpret_cast<char*>(out);
+    switch (prec) {
+      case P_F64: pack_half_kernel<P_F64><<<hg, hb, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+      case P_F32: pack_half_kernel<P_F32><<<hg, hb, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+      case P_BF16: pack_half_kernel<P_BF16><<<hg, hb, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+      case P_F16: pack_half_kernel<P_F16><<<hg, hb, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+      case P_DF64: pack_half_kernel<P_DF64><<<hg, hb, 0, s>>>(g, c, o, subset, canon_stride_d2, out_stride_bytes, scale); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), subset == 2 ? 2 : 1, nrhs);
   const double2* c = reinterpret_cast<const double2*>(canon);
   char* o = reinterpret_cast<char*>(out);
@@ -211,6 +308,21 @@ cudaError_t pack_spinor(const Geom& g, int prec, int subset, const double* canon
 cudaError_t unpack_spinor(const Geom& g, int prec, int subset, const void* in, double* canon, double scale,
                           int nrhs, long in_stride_bytes, long canon_stride_d2, cudaStream_t s, int half) {
   if (half && subset == 2) return cudaErrorInvalidValue;
+  if (half) {
+    dim3 hb(HB), hg((unsigned)((g.Vh + HB - 1) / HB), 1, nrhs);
+    double2* c = reinterpret_cast<double2*>(canon);
+    const char* i = reinterpret_cast<const char*>(in);
+    const double inv = 1.0 / scale;
+    switch (prec) {
+      case P_F64: unpack_half_kernel<P_F64><<<hg, hb, 0, s>>>(g, i, c, in_stride_bytes, canon_stride_d2, inv); break;
+      case P_F32: unpack_half_kernel<P_F32><<<hg, hb, 0, s>>>(g, i, c, in_stride_bytes, canon_stride_d2, inv); break;
+      case P_BF16: unpack_half_kernel<P_BF16><<<hg, hb, 0, s>>>(g, i, c, in_stride_bytes, canon_stride_d2, inv); break;
+      case P_F16: unpack_half_kernel<P_F16><<<hg, hb, 0, s>>>(g, i, c, in_stride_bytes, canon_stride_d2, inv); break;
+      case P_DF64: unpack_half_kernel<P_DF64><<<hg, hb, 0, s>>>(g, i, c, in_stride_bytes, canon_stride_d2, inv); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   dim3 block(128), grid((unsigned)((g.Vh + 127) / 128), subset == 2 ? 2 : 1, nrhs);
   double2* c = reinterpret_cast<double2*>(canon);
   const char* i = reinterpret_cast<const char*>(in);

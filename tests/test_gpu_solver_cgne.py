@@ -157,3 +157,42 @@ def test_bench_configuration_end_to_end(launch):
         assert st[k]["converged"] and st[k]["resets"] >= 2
         check_residual(_normal_residual(u, a, ainv, eta[k], x[k]), st[k]["true_rel_res"])
     h.close()
+
+
+def test_cgne_on_pinned_host_fields():
+    """The solver takes page-locked host buffers (mapped into the device's
+    address space at the same address): its packing and unpacking kernels
+    read the sources and write the solutions there.  Same solution, bit for
+    bit, as with device buffers; pageable host memory is refused before any
+    launch (OQ_ERR_ARG)."""
+    import ctypes
+    import torch
+    oq = _oq()
+    dims = (4, 4, 4, 8)
+    u, a, ainv = oracle_case(dims, 0.4, 5, 0.13, 1.0)
+    n = 3
+    eta = np.stack([dirac.even_part(e) for e in synth.make_source(dims, 340, nrhs=n)])
+    ev = (np.indices(dims).sum(axis=0).reshape(-1) % 2) == 0
+    eta_half = np.ascontiguousarray(eta.reshape(n, -1, 4, 3)[:, ev])
+    h = make_handle(dims, u, 0.13, 1.0, oq.LINK_12)
+    prm = oq.SolverParams(res=1e-10, nmx=5000, sdtype=oq.F16)
+    e_dev = to_dev(eta_half)
+    p_dev = torch.zeros_like(e_dev)
+    rc, st = h.cgne_even(e_dev, p_dev, prm, nrhs=n)
+    assert rc == oq.OK
+    e_host = e_dev.cpu().pin_memory()
+    p_host = torch.full_like(e_host, float("nan")).pin_memory()
+    rc2, st2 = h.cgne_even(e_host, p_host, prm, nrhs=n)
+    torch.cuda.synchronize()
+    assert rc2 == oq.OK
+    assert torch.equal(p_host, p_dev.cpu())
+    assert [s["steps"] for s in st] == [s["steps"] for s in st2]
+    pageable = torch.zeros_like(e_host)                      # not page-locked
+    assert not pageable.is_pinned()
+    from paper_2202_07388_gb300.oq import lib, _stream, OqStatus
+    sts = (OqStatus * n)()
+    p = prm.c()
+    rc3 = lib().oq_cgne_solve_even(h.h, 0, ctypes.byref(p), ctypes.c_void_p(pageable.data_ptr()),
+                                   ctypes.c_void_p(p_host.data_ptr()), n, sts, _stream())
+    assert rc3 == oq.ERR_ARG
+    h.close()
