@@ -180,17 +180,81 @@ def merge_source_kernels(prof):
     return [v for v in out.values() if v["launches"] > 0]
 
 
+STENCIL_SOURCES = ("hop_impl.cuh", "hop_mr.cuh", "oq_device.cuh", "reduce.cuh")
+
+# the commands whose ncu logs --write-traffic turns into profiles/traffic.json
+TRAFFIC_CASE = "python bench.py --profile-case --profile-kind cgne"
+TRAFFIC_COMMANDS = [
+    TRAFFIC_CASE,
+    "ncu --profile-from-start off -k regex:hop_mr_kernel -c 4 --metrics dram__bytes_read.sum,dram__bytes_write.sum,"
+    "gpu__time_duration.sum --clock-control none --csv --log-file traffic_f16.csv " + TRAFFIC_CASE,
+    "ncu --profile-from-start off -k regex:hop_kernel -c 20 --metrics dram__bytes_read.sum,dram__bytes_write.sum,"
+    "gpu__time_duration.sum --clock-control none --csv --log-file traffic_reset.csv " + TRAFFIC_CASE,
+    "python bench.py --write-traffic traffic_f16.csv traffic_reset.csv",
+]
+
+
+def stencil_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STENCIL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2202_07388_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def write_traffic(csvs):
+    """profiles/traffic.json from ncu --csv logs of the cgne profile case (32x32^3, 12 rhs):
+    dram__bytes_read.sum + dram__bytes_write.sum per launch / Vh, averaged per kernel variant
+    (named as kernel_key names them, adjoint and plain instantiations together), with the
+    hash of the stencil sources the capture was taken on."""
+    import csv
+    import re
+    vh = 32 ** 4 // 2
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    kern = {}
+    for path in csvs:
+        hdr, launches = None, {}
+        for r in csv.reader(open(path)):
+            if not r:
+                continue
+            if "Kernel Name" in r:
+                hdr = r
+                continue
+            if hdr is None or len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, r))
+            m = launches.setdefault((int(d["ID"]), d["Kernel Name"]), {})
+            m[d["Metric Name"]] = float(d["Metric Value"].replace(",", "")) * scale.get(d["Metric Unit"], 1)
+        for (_, name), m in launches.items():
+            targs = [int(x) for x in re.search(r"<([^>]*)>", name).group(1).split(",")]
+            if "hop_mr_kernel" in name:
+                prec, fmt, mode, _dag, epi, nr, _cap = targs
+            else:
+                prec, fmt, mode, _dag, epi = targs
+                nr = 1
+            lf = -1 if prec in (0, 4) else fmt
+            key = kernel_key({"mode": mode, "epi": epi, "prec": prec, "nr": nr, "link_fmt": lf})
+            b = (m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]) / vh
+            e = kern.setdefault(key, {"dram_bytes_per_site": 0.0, "launches": 0, "capture": os.path.basename(path)})
+            e["dram_bytes_per_site"] = (e["dram_bytes_per_site"] * e["launches"] + b) / (e["launches"] + 1)
+            e["launches"] += 1
+    out = {"note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch / Vh, 32x32^3 lattice, 12 rhs; "
+                   "bench scales by its own Vh",
+           "commands": TRAFFIC_COMMANDS, "lattice": "32x32x32x32", "nrhs": 12, "kernels": kern,
+           "source_sha256": stencil_source_hash()}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(kern, indent=1))
+    return 0
+
+
 def traffic_for(kernel_key):
     """ncu DRAM bytes per launch recorded for this kernel, if the kernel source is unchanged since."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    h = hashlib.sha256()
-    for f in ("hop_impl.cuh", "hop_mr.cuh", "oq_device.cuh", "reduce.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2202_07388_gb300", "csrc", f), "rb").read())
-    if d.get("source_sha256") != h.hexdigest():
+    if d.get("source_sha256") != stencil_source_hash():
         return None
     # one entry per pass and epilogue: the adjoint instantiation moves the same bytes
     ent = d.get("kernels", {}).get(kernel_key[:-len("/dag")] if kernel_key.endswith("/dag") else kernel_key)
@@ -392,6 +456,8 @@ def run_ours(args):
     tuned = {}
     for pname, pc, nr in (("f16", oq.F16, NRHS), ("f64", oq.F64, NRHS), ("df64", oq.DF64, NRHS)):
         tuned[f"{pname}x{nr}"] = {MODE_NAMES[m]: v for m, v in h.autotune(pc, nrhs=nr).items()}
+    # pass 2 is tuned per epilogue: the launches the solve's norm and CG-update passes run
+    tuned[f"f16x{NRHS}"]["dw_hat_pass2_even_by_epilogue"] = h.tuned_epilogues(oq.F16, NRHS)
     if not args.no_tts:
         for pname, pc in (("f64", oq.F64), ("df64", oq.DF64), ("f32", oq.F32), ("bf16", oq.BF16), ("f16", oq.F16)):
             tuned[f"{pname}x1"] = {MODE_NAMES[m]: v for m, v in h.autotune(pc, nrhs=1).items()}
@@ -1116,7 +1182,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tts", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the compact c4 / c5 workloads")
+    ap.add_argument("--write-traffic", nargs="+", metavar="CSV", default=None,
+                    help="write profiles/traffic.json from the ncu logs of the traffic capture")
     args = ap.parse_args()
+    if args.write_traffic:
+        return write_traffic(args.write_traffic)
     if args.profile_case:
         return run_profile_case(args)
     if args.workload == "c4":

@@ -276,12 +276,19 @@ int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, 
  * on 12-real links the 18-real copy the handle keeps (fewer instructions,
  * more bytes).  oq_tune_get reports the chosen launch and its time
  * (link_fmt, nr, regcap nullable; mode 0 = Dw, 1 = Dhat pass 1, 2 = Dhat
- * pass 2); OQ_ERR_STATE if none is set.  oq_tune_set pins a launch without
+ * pass 2); OQ_ERR_STATE if none is set.  The autotuner times pass 2 once per
+ * epilogue (they differ in registers and bytes): oq_tune_get_epi reports the
+ * launch of one (epi 0 = store, 1 = store and squared norm, 2 = the CGNE
+ * update of x and r; OQ_ERR_ARG otherwise), or the mode's plain launch where
+ * the epilogue has none of its own (what runs then); oq_tune_get is epi 0.
+ * oq_tune_set pins a launch without
  * timing (link_fmt -1: the uploaded format; OQ_ERR_ARG for an inadmissible
  * launch, OQ_ERR_STATE before oq_gauge_upload). */
 int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* stream);
 int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
                 int* link_fmt, int* nr, int* regcap);
+int oq_tune_get_epi(oq_handle h, int lat, int prec, int mode, int epi, int nrhs, int* bx, int* by, float* ms,
+                    int* link_fmt, int* nr, int* regcap);
 int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int by, int nr, int regcap,
                 int link_fmt);
 

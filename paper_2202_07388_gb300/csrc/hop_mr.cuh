@@ -129,8 +129,10 @@ struct RawSp {
 // Per-thread staging of the next hop's operands in shared memory: 16-byte
 // asynchronous copies (cp.async) that hold no register while in flight.  A
 // thread reads back only the slots it filled itself, so waiting for its own
-// copy groups suffices (no barrier).  Slot k of stage st of thread tid is
-// stg[(st * nslot + k) * nthr + tid]: a warp reads 512 contiguous bytes.
+// copy groups suffices (no barrier).  A thread's slots are contiguous (slot
+// k of stage st at offset st * nslot + k, a compile-time constant) and the
+// slot count per thread is odd, so the 8 threads of a 128-byte phase of a
+// warp's 16-byte access fall in distinct bank groups.
 __device__ __forceinline__ void cp16(uint4* smem, const void* gmem) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
@@ -141,11 +143,8 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 struct Stage {
-  uint4* base;
-  uint32_t nthr, tid;
-  __device__ __forceinline__ uint4* at(int st, int k, int nslot) const {
-    return base + (size_t)((uint32_t)(st * nslot + k) * nthr + tid);
-  }
+  uint4* mine;  // this thread's first slot
+  __device__ __forceinline__ uint4* at(int st, int k, int nslot) const { return mine + (st * nslot + k); }
 };
 
 __device__ __forceinline__ void join(const Spinor<float>& a, const Spinor<float>& b, Sp2& s) {
@@ -431,7 +430,12 @@ __device__ __forceinline__ void coords(const Geom& g, int p, uint32_t i, int x[4
 // PF: the operands of hop k + 1 (neighbour spinors of the NR right-hand
 // sides and the 12-real link) are copied into the thread's shared-memory
 // stage (k + 1) % 2 while hop k is computed, and pass 1 stages its inverse
-// clover blocks the same way (stg: 2 stages of NR * chunks + 3 slots).
+// clover blocks the same way after the last hop (stg: 2 stages of
+// NR * chunks + 3 slots).  Staged pass 2 and Dw first copy in2 (into
+// NR * chunks / 2 extra slots of each stage) and the two clover blocks (into
+// the stages' hop slots) and form A in2 from there before the hops, the
+// summation order of the unstaged kernel; hop 0's operands are copied once
+// block 0 has been read.
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, bool PF>
 __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int p, const bool (&live)[NR],
                                      double (&red)[NR], const Stage& stg) {
@@ -484,6 +488,10 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
   // staged operands of hop H (mu = H / 2, forward for even H)
   constexpr int SC = RawSp<P>::NC;
   constexpr int NSLOT = NR * SC + 3;
+  constexpr bool LOC = PF && MODE != HOP_P1;  // in2 and the blocks of A staged too
+  // staged pass 2 and Dw: each stage has E more slots, which hold half of in2
+  constexpr int E = LOC ? NR * SC / 2 : 0;
+  constexpr int NS = NSLOT + E;  // slots per stage
   auto prefetch = [&](auto h_c, int st) {
     constexpr int H = decltype(h_c)::value;
     constexpr int MU = H >> 1;
@@ -493,21 +501,41 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
     for (int k = 0; k < NR; ++k)
 #pragma unroll
       for (int c = 0; c < SC; ++c)
-        cp16(stg.at(st, k * SC + c, NSLOT), reinterpret_cast<const uint4*>(in[k]) + (c * Vh + j));
+        cp16(stg.at(st, k * SC + c, NS), reinterpret_cast<const uint4*>(in[k]) + (c * Vh + j));
     const float4* b = reinterpret_cast<const float4*>(a.links) + (size_t)(((FWD ? p : 1 - p) * 4 + MU) * 3) * Vh;
     const uint32_t li = FWD ? i : j;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) cp16(stg.at(st, NR * SC + c, NSLOT), b + (c * Vh + li));
+    for (int c = 0; c < 3; ++c) cp16(stg.at(st, NR * SC + c, NS), b + (c * Vh + li));
     cp_commit();
   };
-  // clover block b of this site (9 chunks) into stage st
-  auto prefetch_blk = [&](const void* base, int b, int st) {
+  // clover block b of this site (9 chunks) into slots off .. off + 8 of stage st
+  auto copy_blk = [&](const void* base, int b, int st, int off) {
     const float4* q = reinterpret_cast<const float4*>(base) + (size_t)(p * 18) * Vh;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) cp16(stg.at(st, c, NSLOT), q + ((9 * b + c) * Vh + i));
+    for (int c = 0; c < 9; ++c) cp16(stg.at(st, off + c, NS), q + ((9 * b + c) * Vh + i));
+  };
+  auto prefetch_blk = [&](const void* base, int b, int st) {
+    copy_blk(base, b, st, 0);
     cp_commit();
   };
-  if constexpr (PF) prefetch(std::integral_constant<int, 0>{}, 0);
+  // chunk f of in2 (f = k * SC + c for right-hand side k): the last E slots of stage f / E
+  auto loc_at = [&](int f) { return f < E ? stg.at(0, NSLOT + f, NS) : stg.at(1, NSLOT + f - E, NS); };
+  if constexpr (LOC) {
+    // in2 and clover block 0 (into stage 0's hop slots), then block 1 (stage 1's)
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int r = rhs0 + k < a.nrhs ? rhs0 + k : a.nrhs - 1;
+      const uint4* l = reinterpret_cast<const uint4*>((const char*)a.in2 + (long)r * a.in2_stride + par_out);
+#pragma unroll
+      for (int c = 0; c < SC; ++c) cp16(loc_at(k * SC + c), l + (c * Vh + i));
+    }
+    copy_blk(a.clov, 0, 0, 0);
+    cp_commit();
+    copy_blk(a.clov, 1, 1, 0);
+    cp_commit();
+  } else if constexpr (PF) {
+    prefetch(std::integral_constant<int, 0>{}, 0);
+  }
 
   // The weighted hops accumulate onto acc: for pass 2 and Dw onto A in2,
   // formed first while few registers are live (the site-local spinors stay
@@ -515,7 +543,38 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
   // pass 1 onto zero, then multiplied by A^{-1}.
   const F2 w = bc(MODE == HOP_P2 ? 0.5f : -0.5f);
   Sp2 acc[NP];
-  if constexpr (MODE == HOP_P1) {
+  if constexpr (LOC) {
+    // acc = A in2, block b from stage b; hop 0's operands are copied into
+    // stage 0 once block 0 has been read, in flight while block 1 is applied
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      cp_wait<1>();
+      float4 w9[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) w9[c] = *reinterpret_cast<const float4*>(stg.at(b, c, NS));
+      if (b == 0) prefetch(std::integral_constant<int, 0>{}, 0);
+      Blk k;
+      blk_from(w9, k);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        RawSp<P> l0, l1;
+#pragma unroll
+        for (int c = 0; c < SC; ++c) {
+          l0.ch[c] = *loc_at((2 * q) * SC + c);
+          l1.ch[c] = *loc_at((2 * q + 1) * SC + c);
+        }
+        C2 xv[6], yv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          const cx<float> z0 = l0.get(6 * b + r), z1 = l1.get(6 * b + r);
+          xv[r] = {make_float2(z0.re, z1.re), make_float2(z0.im, z1.im)};
+        }
+        blk_apply(k, xv, yv);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) acc[q].c[2 * b + r / 3][r % 3] = yv[r];
+      }
+    }
+  } else if constexpr (MODE == HOP_P1) {
 #pragma unroll
     for (int q = 0; q < NP; ++q)
 #pragma unroll
@@ -587,16 +646,16 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       cp_wait<0>();
     }
     Su3<float> u;
-    link12_from(*reinterpret_cast<const float4*>(stg.at(st, NR * SC, NSLOT)),
-                *reinterpret_cast<const float4*>(stg.at(st, NR * SC + 1, NSLOT)),
-                *reinterpret_cast<const float4*>(stg.at(st, NR * SC + 2, NSLOT)), u);
+    link12_from(*reinterpret_cast<const float4*>(stg.at(st, NR * SC, NS)),
+                *reinterpret_cast<const float4*>(stg.at(st, NR * SC + 1, NS)),
+                *reinterpret_cast<const float4*>(stg.at(st, NR * SC + 2, NS)), u);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       RawSp<P> n0, n1;
 #pragma unroll
       for (int c = 0; c < SC; ++c) {
-        n0.ch[c] = *stg.at(st, (2 * q) * SC + c, NSLOT);
-        n1.ch[c] = *stg.at(st, (2 * q + 1) * SC + c, NSLOT);
+        n0.ch[c] = *stg.at(st, (2 * q) * SC + c, NS);
+        n1.ch[c] = *stg.at(st, (2 * q + 1) * SC + c, NS);
       }
       hop_pair<P, MU, FWD ? SF : -SF, !FWD, EPI != EPI_CG>(u, n0, n1, acc[q], MU == 0 ? (FWD ? wf : wb) : w);
     }
@@ -631,7 +690,7 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       }
       float4 w9[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) w9[c] = *reinterpret_cast<const float4*>(stg.at(b, c, NSLOT));
+      for (int c = 0; c < 9; ++c) w9[c] = *reinterpret_cast<const float4*>(stg.at(b, c, NS));
       Blk k;
       blk_from(w9, k);
 #pragma unroll
@@ -739,10 +798,7 @@ __device__ __forceinline__ void grid_reduce_nr(const double (&v)[NR], const RedA
     last = __shfl_sync(0xffffffffu, last, 0);
     if (last) {
       __threadfence();
-      double acc = 0.0;
-      const volatile double* part = ra.partials + (long)rhs * ncta;
-      for (unsigned b = tx; b < ncta; b += 32) acc += part[b];
-      acc = warp_sum(acc);
+      const double acc = warp_sum_partials(ra.partials + (long)rhs * ncta, ncta, tx);
       if (tx == 0) {
         ra.counters[rhs] = 0u;
         run_finisher(ra, rhs, acc);
@@ -764,19 +820,32 @@ template <int NR, int CAP>
 struct MrBounds {
   static constexpr int min_blocks = CAP == 0 ? 1 : NR == 2 ? 4 : 3;
 };
-// dynamic shared memory of a staged launch: 2 stages of NR * chunks + 3 slots of 16 bytes per thread
-template <int P, int NR>
+// 16-byte slots per thread of a staged launch: 2 stages of NR * chunks + 3,
+// for pass 2 and Dw of NR * chunks / 2 more (the site-local spinors); rounded
+// up to an odd count
+template <int P, int NR, int MODE>
+constexpr int mr_stage_slots() {
+  constexpr int sc = P == P_F32 ? 6 : 3;
+  return (2 * (NR * sc + 3 + (MODE == HOP_P1 ? 0 : NR * sc / 2))) | 1;
+}
+template <int P, int NR, int MODE>
 constexpr size_t mr_stage_bytes(int nthr) {
-  return (size_t)2 * (NR * (P == P_F32 ? 6 : 3) + 3) * 16 * nthr;
+  return (size_t)mr_stage_slots<P, NR, MODE>() * 16 * nthr;
+}
+// the per-thread slots of a launch (staged: CAP = 2)
+template <int P, int NR, int MODE, int CAP>
+constexpr int mr_slots() {
+  return CAP == 2 ? mr_stage_slots<P, NR, MODE>() : 0;
 }
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, int CAP>
 __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_kernel(const HopArgs a) {
   extern __shared__ double dyn_smem[];
   constexpr bool PF = CAP == 2;
+  constexpr int NSL = mr_slots<P, NR, MODE, CAP>();
   const uint32_t nthr = blockDim.x * blockDim.y;
-  // staged launches: the stages first, then the reduction scratch
-  double* red_smem = PF ? dyn_smem + mr_stage_bytes<P, NR>(nthr) / sizeof(double) : dyn_smem;
-  mr::Stage stg{reinterpret_cast<uint4*>(dyn_smem), nthr, threadIdx.y * blockDim.x + threadIdx.x};
+  // the threads' slots first, then the reduction scratch
+  double* red_smem = dyn_smem + (size_t)NSL * 16 * nthr / sizeof(double);
+  mr::Stage stg{reinterpret_cast<uint4*>(dyn_smem) + (size_t)(threadIdx.y * blockDim.x + threadIdx.x) * NSL};
   const unsigned per_cta = blockDim.y * NR;
   const unsigned ntile = (a.nrhs + per_cta - 1) / per_cta;
   const unsigned tile = blockIdx.x % ntile;
@@ -806,6 +875,28 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
   }
 }
 
+// a staged launch (CAP 2): the threads' slots, then `smem` bytes of
+// reduction scratch; above 48 KiB the kernel is allowed the device's opt-in
+// limit (once per instantiation)
+template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, int CAP>
+static cudaError_t launch_mr_smem(dim3 grid, dim3 block, size_t smem, const HopArgs& a, cudaStream_t s) {
+  const size_t bytes = smem + (size_t)mr_slots<P, NR, MODE, CAP>() * 16 * block.x * block.y;
+  static bool attr = false;
+  if (!attr && bytes > 48 * 1024) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, CAP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (bytes > 227 * 1024) return cudaErrorInvalidValue;
+  hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, CAP><<<grid, block, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR>
 static cudaError_t launch_mr_one(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
   if (L.bx % 32 != 0 || L.bx * L.by > 128 || L.by < 1) return cudaErrorInvalidValue;
@@ -815,18 +906,8 @@ static cudaError_t launch_mr_one(const HopLaunch& L, const HopArgs& a, cudaStrea
   dim3 grid((MODE == HOP_DW ? 2u * nb : nb) * ntile, 1u, 1u);
   const size_t smem = (EPI == EPI_NONE) ? 0 : sizeof(double) * (L.bx / 32) * L.by * NR;
   if (L.regcap == 2) {
-    if constexpr (FMT == LINK_12) {
-      const size_t bytes = smem + mr_stage_bytes<P, NR>(L.bx * L.by);
-      static bool attr = false;  // per instantiation: allow more than 48 KiB once
-      if (!attr && bytes > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 2>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
-      hop_mr_kernel<P, FMT, MODE, DAG, EPI, NR, 2><<<grid, block, bytes, s>>>(a);
-      return cudaGetLastError();
-    }
+    if constexpr (FMT == LINK_12)
+      return launch_mr_smem<P, FMT, MODE, DAG, EPI, NR, 2>(grid, block, smem, a, s);
     return cudaErrorInvalidValue;
   }
   if (L.regcap)

@@ -3,8 +3,9 @@
 // Every CTA reduces its threads' double partial sums per right-hand side
 // (warp shuffles, then shared memory), writes one partial per (rhs, CTA),
 // and the last CTA to arrive (atomic ticket) sums the partials of that rhs
-// in a fixed order with one warp and runs the finisher that turns the sum
-// into solver scalars (CG alpha / beta, restart norms).  The order of the
+// in a fixed order with one warp (16 loads in flight per lane) and runs the
+// finisher that turns the sum into solver scalars (CG alpha / beta, restart
+// norms).  The order of the
 // additions never depends on timing, so results are bitwise reproducible.
 #pragma once
 #include "oq_internal.h"
@@ -15,6 +16,33 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Sum of part[0 .. n) by one warp in a fixed order: lane l adds the entries
+// l + 32 j into 16 accumulators (j mod 16, the ragged end into the first),
+// combined pairwise, then across the warp.  The 16 loads of a round are
+// independent, so they are in flight together: the partials were written by
+// other CTAs of the launch and are read from L2 (ld.global.cg, no L1 copy)
+// after the ticket's fence.
+__device__ __forceinline__ double warp_sum_partials(const double* part, unsigned n, int lane) {
+  constexpr int U = 16;
+  double acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = 0.0;
+  unsigned b = (unsigned)lane;
+  for (; b + (U - 1) * 32 < n; b += U * 32) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = __ldcg(part + b + u * 32);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] += v[u];
+  }
+  for (; b < n; b += 32) acc[0] += __ldcg(part + b);
+#pragma unroll
+  for (int w = U / 2; w > 0; w >>= 1)
+#pragma unroll
+    for (int u = 0; u < w; ++u) acc[u] += acc[u + w];
+  return warp_sum(acc[0]);
 }
 
 __device__ __forceinline__ void run_finisher(const RedArgs& ra, int rhs, double sum) {
@@ -95,10 +123,7 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs
       last = __shfl_sync(0xffffffffu, last, 0);
       if (last) {
         __threadfence();
-        double acc = 0.0;
-        const volatile double* part = ra.partials + (long)rhs * ncta;
-        for (unsigned b = tx; b < ncta; b += 32) acc += part[b];
-        acc = warp_sum(acc);
+        const double acc = warp_sum_partials(ra.partials + (long)rhs * ncta, ncta, tx);
         if (tx == 0) {
           ra.counters[rhs] = 0u;
           run_finisher(ra, rhs, acc);

@@ -214,10 +214,13 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
   return ret;
 }
 
-extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
-                           int* link_fmt, int* nr, int* regcap) {
-  if (!h || !bx || !by || !ms || lat < 0 || lat >= (int)h->lats.size()) return OQ_ERR_ARG;
-  auto it = h->tuned.find(TuneKey{lat, prec, mode, nrhs, EPI_NONE});
+extern "C" int oq_tune_get_epi(oq_handle h, int lat, int prec, int mode, int epi, int nrhs, int* bx, int* by,
+                               float* ms, int* link_fmt, int* nr, int* regcap) {
+  if (!h || !bx || !by || !ms || lat < 0 || lat >= (int)h->lats.size() || epi < EPI_NONE || epi > EPI_CG)
+    return OQ_ERR_ARG;
+  // the launch lookup's rule: an epilogue without a launch of its own runs the mode's plain one
+  auto it = h->tuned.find(TuneKey{lat, prec, mode, nrhs, epi});
+  if (it == h->tuned.end()) it = h->tuned.find(TuneKey{lat, prec, mode, nrhs, EPI_NONE});
   if (it == h->tuned.end()) return OQ_ERR_STATE;
   const TuneVal& v = it->second;
   *bx = v.bx;
@@ -227,6 +230,11 @@ extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, i
   if (nr) *nr = v.nr;
   if (regcap) *regcap = v.regcap;
   return OQ_OK;
+}
+
+extern "C" int oq_tune_get(oq_handle h, int lat, int prec, int mode, int nrhs, int* bx, int* by, float* ms,
+                           int* link_fmt, int* nr, int* regcap) {
+  return oq_tune_get_epi(h, lat, prec, mode, EPI_NONE, nrhs, bx, by, ms, link_fmt, nr, regcap);
 }
 
 extern "C" int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int by, int nr, int regcap,

@@ -108,6 +108,9 @@ _SIGS = {
     "oq_tune_get": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                               C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int),
                               C.POINTER(C.c_int)]),
+    "oq_tune_get_epi": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "oq_tune_set": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                               C.c_int]),
     "oq_gauge_upload_halo": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),
@@ -419,10 +422,16 @@ class Handle:
         _check(lib().oq_autotune(self.h, lat, prec, nrhs, _stream(stream)), "oq_autotune")
         return {mode: self.tune_get(prec, mode, nrhs, lat) for mode in (0, 1, 2)}
 
-    def tune_get(self, prec, mode, nrhs=1, lat=0):
+    def tuned_epilogues(self, prec, nrhs=1, lat=0):
+        """Pass 2's chosen launch per epilogue (store, norm, cg) after autotune."""
+        return {name: self.tune_get(prec, 2, nrhs, lat, epi) for epi, name in enumerate(("store", "norm", "cg"))}
+
+    def tune_get(self, prec, mode, nrhs=1, lat=0, epi=0):
+        """The launch chosen for (prec, mode, nrhs); for pass 2 (mode 2) per epilogue
+        (epi 0 store, 1 store and norm, 2 CGNE update)."""
         bx, by, ms, fmt, nr, cap = C.c_int(), C.c_int(), C.c_float(), C.c_int(), C.c_int(), C.c_int()
-        _check(lib().oq_tune_get(self.h, lat, prec, mode, nrhs, C.byref(bx), C.byref(by), C.byref(ms),
-                                 C.byref(fmt), C.byref(nr), C.byref(cap)), "oq_tune_get")
+        _check(lib().oq_tune_get_epi(self.h, lat, prec, mode, epi, nrhs, C.byref(bx), C.byref(by), C.byref(ms),
+                                     C.byref(fmt), C.byref(nr), C.byref(cap)), "oq_tune_get_epi")
         return (bx.value, by.value, ms.value, "12-real" if fmt.value == LINK_12 else "18-real", nr.value, cap.value)
 
     def tune_set(self, prec, mode, nrhs, bx, by, nr=1, regcap=0, link_fmt=-1, lat=0, check=True):

@@ -115,6 +115,11 @@ def test_tune_set_rejects_inadmissible_launches():
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2) == oq.OK      # staged on the uploaded 12-real links
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=4, regcap=1) == oq.OK
     assert h.tune_get(oq.F16, 1, 4)[4:] == (4, 1)
+    # a pinned pass-2 launch serves every epilogue
+    assert h.tune_set(oq.F16, 2, 4, 64, 1, nr=2, regcap=2) == oq.OK
+    assert all(v[:2] == (64, 1) and v[4:] == (2, 2) for v in h.tuned_epilogues(oq.F16, nrhs=4).values())
+    assert oq.lib().oq_tune_get_epi(h.h, 0, oq.F16, 2, 3, 4, *[oq.C.byref(oq.C.c_int()) for _ in range(2)],
+                                    oq.C.byref(oq.C.c_float()), None, None, None) == oq.ERR_ARG
     h2 = make_handle(dims, u, 0.13, 1.0, oq.LINK_18)
     assert h2.tune_set(oq.F32, 1, 1, 64, 1, link_fmt=oq.LINK_12, check=False) == oq.ERR_ARG
     assert h2.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, check=False) == oq.ERR_ARG  # staged: 12-real links
