@@ -56,11 +56,23 @@ __device__ __forceinline__ void store_smem(float* sm, int nsite, int t, const Sp
   }
 }
 
-// sum of up to 3 doubles over the CTA, result in every thread
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
+// The block sums of an MR step, result in every thread.  The three sums
+// that give the MR coefficient omega = <D p, r> / <D p, D p> are binary32
+// (a preconditioner coefficient: a tree of warp shuffles, then the warp
+// partials in a fixed order; ~5e-7 relative for 256 sites); binary64
+// arithmetic runs at 1/64 of the binary32 rate on GB300, and these sums with
+// a binary64 division per thread had kept its FP64 pipe 36 % busy.  The
+// adaptive exit tests keep one binary64 sum (block_sum1).
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ void block_sum3(float& a, float& b, float& c, double* red_d) {
+  float* red = reinterpret_cast<float*>(red_d);
+  a = warp_sum_f(a);
+  b = warp_sum_f(b);
+  c = warp_sum_f(c);
   const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) {
@@ -69,12 +81,22 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
     red[3 * w + 2] = c;
   }
   __syncthreads();
-  a = b = c = 0.0;
+  a = b = c = 0.f;
   for (int k = 0; k < nw; ++k) {
     a += red[3 * k];
     b += red[3 * k + 1];
     c += red[3 * k + 2];
   }
+}
+__device__ __forceinline__ double block_sum1(double a, double* red) {
+  a = warp_sum(a);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = a;
+  __syncthreads();
+  a = 0.0;
+  for (int k = 0; k < nw; ++k) a += red[k];
+  return a;
 }
 
 // in-block hop along +mu / -mu from smem (Dirichlet: outside neighbours dropped)
@@ -168,9 +190,13 @@ __global__ void __launch_bounds__(256, MINB) sap_kernel(const SapArgs a) {
       for (int c = 0; c < 3; ++c) r.c[s][c] = rh.c[s][c] - (aph.c[s][c] + acc.c[s][c]);
     store_smem(sm, nsite, t, r);
   }
-  double n0 = 0.0, z1 = 0.0, z2 = 0.0;
-  if (act) n0 = site_norm2(r);
-  block_sum3(n0, z1, z2, red);
+  double n0 = 0.0;
+  if (a.adaptive) {
+    if (act) n0 = site_norm2(r);
+    n0 = block_sum1(n0, red);  // also the barrier after the block residual is stored
+  } else {
+    __syncthreads();
+  }
   double rn_prev = sqrt(n0);
 
   // 2. MR on D_i
@@ -182,7 +208,7 @@ __global__ void __launch_bounds__(256, MINB) sap_kernel(const SapArgs a) {
   int steps = 0;
   for (int k = 1; k <= a.nmr; ++k) {
     Spinor<float> pv;
-    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
+    float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
     if (act) {
       Spinor<float> own;
       load_smem(sm, nsite, t, own);
@@ -207,12 +233,12 @@ __global__ void __launch_bounds__(256, MINB) sap_kernel(const SapArgs a) {
     }
     block_sum3(pr_re, pr_im, pp, red);  // contains __syncthreads: all neighbour reads done
     float om_re = 0.f, om_im = 0.f;
-    if (pp > 0.0) {
-      om_re = (float)(pr_re / pp);
-      om_im = (float)(pr_im / pp);
+    if (pp > 0.f) {
+      om_re = pr_re / pp;
+      om_im = pr_im / pp;
     }
     const cx<float> om{om_re, om_im};
-    double n1 = 0.0, y1 = 0.0, y2 = 0.0;
+    double n1 = 0.0;
     if (act) {
       Spinor<float> own;
       load_smem(sm, nsite, t, own);
@@ -226,13 +252,15 @@ __global__ void __launch_bounds__(256, MINB) sap_kernel(const SapArgs a) {
       store_smem(sm, nsite, t, own);
       n1 = site_norm2(own);
     }
-    block_sum3(n1, y1, y2, red);
     steps = k;
-    const double rn_new = sqrt(n1);
     if (a.adaptive) {
+      n1 = block_sum1(n1, red);
+      const double rn_new = sqrt(n1);
       if ((k >= 4 && rn_new > (double)a.alpha * rn_prev) || rn_new > rn_prev || rn_new < a.tol) break;
+      rn_prev = rn_new;
+    } else {
+      __syncthreads();  // the updated residual is read by the neighbours next step
     }
-    rn_prev = rn_new;
   }
   // 3. phi_i += x
   if (act) {
@@ -405,10 +433,10 @@ __global__ void __launch_bounds__(256) sap_smem_kernel(const SapArgs a) {
       for (int c = 0; c < 3; ++c) r.c[s][c] = rh.c[s][c] - (aph.c[s][c] + acc.c[s][c]);
     store_smem(m.r, nsite, t, r);
   }
-  double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+  double n0 = 0.0;
   if (a.adaptive) {
     if (act) n0 = site_norm2(r);
-    block_sum3(n0, z1, z2, red);  // also the barrier after the staging
+    n0 = block_sum1(n0, red);  // also the barrier after the staging
   } else {
     __syncthreads();
   }
@@ -423,7 +451,7 @@ __global__ void __launch_bounds__(256) sap_smem_kernel(const SapArgs a) {
   int steps = 0;
   for (int k = 1; k <= a.nmr; ++k) {
     Spinor<float> pv;
-    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
+    float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
     if (act) {
       Spinor<float> own;
       load_smem(m.r, nsite, t, own);
@@ -448,12 +476,12 @@ __global__ void __launch_bounds__(256) sap_smem_kernel(const SapArgs a) {
     }
     block_sum3(pr_re, pr_im, pp, red);  // contains __syncthreads: all neighbour reads done
     float om_re = 0.f, om_im = 0.f;
-    if (pp > 0.0) {
-      om_re = (float)(pr_re / pp);
-      om_im = (float)(pr_im / pp);
+    if (pp > 0.f) {
+      om_re = pr_re / pp;
+      om_im = pr_im / pp;
     }
     const cx<float> om{om_re, om_im};
-    double n1 = 0.0, y1 = 0.0, y2 = 0.0;
+    double n1 = 0.0;
     if (act) {
       Spinor<float> own;
       load_smem(m.r, nsite, t, own);
@@ -469,7 +497,7 @@ __global__ void __launch_bounds__(256) sap_smem_kernel(const SapArgs a) {
     }
     steps = k;
     if (a.adaptive) {
-      block_sum3(n1, y1, y2, red);
+      n1 = block_sum1(n1, red);
       const double rn_new = sqrt(n1);
       if ((k >= 4 && rn_new > (double)a.alpha * rn_prev) || rn_new > rn_prev || rn_new < a.tol) break;
       rn_prev = rn_new;
@@ -649,10 +677,10 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
       for (int c = 0; c < 3; ++c) rh.c[s][c] = r.c[s][c] - acc.c[s][c];
     store_smem(m.r, nsite, t, rh);
   }
-  double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+  double n0 = 0.0;
   if (a.adaptive) {
     if (ev) n0 = site_norm2(rh);
-    block_sum3(n0, z1, z2, red);
+    n0 = block_sum1(n0, red);
   } else {
     __syncthreads();
   }
@@ -672,7 +700,7 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
     __syncthreads();
     // even half pass: q_e = A rhat_e - D_eo t_o, then <q, rhat>, <q, q>
     Spinor<float> pv;
-    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
+    float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
     if (ev) {
       Spinor<float> own, acc;
       load_smem(m.r, nsite, t, own);
@@ -695,12 +723,12 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
     }
     block_sum3(pr_re, pr_im, pp, red);  // barrier: every read of this step is done
     float om_re = 0.f, om_im = 0.f;
-    if (pp > 0.0) {
-      om_re = (float)(pr_re / pp);
-      om_im = (float)(pr_im / pp);
+    if (pp > 0.f) {
+      om_re = pr_re / pp;
+      om_im = pr_im / pp;
     }
     const cx<float> om{om_re, om_im};
-    double n1 = 0.0, y1 = 0.0, y2 = 0.0;
+    double n1 = 0.0;
     if (ev) {
       Spinor<float> own;
       load_smem(m.r, nsite, t, own);
@@ -716,7 +744,7 @@ __global__ void __launch_bounds__(256) sap_smem_eo_kernel(const SapArgs a) {
     }
     steps = k;
     if (a.adaptive) {
-      block_sum3(n1, y1, y2, red);
+      n1 = block_sum1(n1, red);
       const double rn_new = sqrt(n1);
       if ((k >= 4 && rn_new > (double)a.alpha * rn_prev) || rn_new > rn_prev || rn_new < a.tol) break;
       rn_prev = rn_new;
