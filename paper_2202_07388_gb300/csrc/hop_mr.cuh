@@ -147,6 +147,16 @@ struct Stage {
   __device__ __forceinline__ uint4* at(int st, int k, int nslot) const { return mine + (st * nslot + k); }
 };
 
+// squared norm of a site's binary32 spinor, summed in binary32
+__device__ __forceinline__ float norm2f(const Spinor<float>& s) {
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc = fmaf(s.c[k][c].re, s.c[k][c].re, fmaf(s.c[k][c].im, s.c[k][c].im, acc));
+  return acc;
+}
+
 __device__ __forceinline__ void join(const Spinor<float>& a, const Spinor<float>& b, Sp2& s) {
 #pragma unroll
   for (int k = 0; k < 4; ++k)
@@ -438,7 +448,7 @@ __device__ __forceinline__ void coords(const Geom& g, int p, uint32_t i, int x[4
 // block 0 has been read.
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, bool PF>
 __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int p, const bool (&live)[NR],
-                                     double (&red)[NR], const Stage& stg) {
+                                     float (&red)[NR], const Stage& stg) {
   static_assert(!PF || FMT == LINK_12, "staged hops read 12-real links");
   constexpr int NP = NR / 2;
   constexpr int SF = DAG ? +1 : -1;  // projector sign of the forward hop
@@ -731,8 +741,8 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       if (live[2 * q + 1])
         store_sp<P>((char*)a.out + (long)(rhs0 + 2 * q + 1) * a.out_stride + par_out, Vh, i, o1);
       if constexpr (EPI == EPI_NORM) {
-        red[2 * q] = site_norm2(o0);
-        red[2 * q + 1] = site_norm2(o1);
+        red[2 * q] = norm2f(o0);
+        red[2 * q + 1] = norm2f(o1);
       }
     }
   } else if constexpr (EPI == EPI_CG) {
@@ -761,7 +771,7 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
       if (live[k]) {
         store_sp<P_F32>((char*)a.ep_x + (long)rr * a.ep_x_stride, Vh, i, xo);
         store_sp<P>((char*)a.ep_r + (long)rr * a.ep_r_stride, Vh, i, ro);
-        red[k] = site_norm2(ro);
+        red[k] = norm2f(ro);
       }
     }
   }
@@ -769,16 +779,18 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
 
 // grid_reduce for NR values per thread (right-hand sides rhs0 .. rhs0+NR-1
 // of the thread's row): smem needs (blockDim.x / 32) * blockDim.y * NR doubles
-// off[k]: rhs0 + k is gated off in this launch (skipped by every CTA, see grid_reduce)
+// off[k]: rhs0 + k is gated off in this launch (skipped by every CTA, see grid_reduce).
+// The per-site values and their warp sums are binary32 (sums of 24 and then
+// 32 terms); everything beyond a warp is summed in binary64.
 template <int NR>
-__device__ __forceinline__ void grid_reduce_nr(const double (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
+__device__ __forceinline__ void grid_reduce_nr(const float (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
                                                double* smem, unsigned cta, unsigned ncta, const bool (&off)[NR]) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NR; ++k) {
-    const double s = warp_sum(v[k]);
-    if ((tx & 31) == 0) smem[(ty * NR + k) * nw + (tx >> 5)] = s;
+    const float s = warp_sum_f(v[k]);
+    if ((tx & 31) == 0) smem[(ty * NR + k) * nw + (tx >> 5)] = (double)s;
   }
   __syncthreads();
   if (tx >= 32) return;
@@ -863,14 +875,14 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
     live[k] = (i < (uint32_t)a.g.Vh) && (rhs0 + k < a.nrhs) && !off[k];
     any |= live[k];
   }
-  double red[NR];
+  float red[NR];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) red[k] = 0.0;
+  for (int k = 0; k < NR; ++k) red[k] = 0.f;
   if (any) mr::site<P, FMT, MODE, DAG, EPI, NR, PF>(a, i, rhs0, p, live, red, stg);
   if constexpr (EPI != EPI_NONE) {
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-      if (!live[k]) red[k] = 0.0;
+      if (!live[k]) red[k] = 0.f;
     mr::grid_reduce_nr<NR>(red, a.red, rhs0, a.nrhs, red_smem, blk, gridDim.x / ntile, off);
   }
 }

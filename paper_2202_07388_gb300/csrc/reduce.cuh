@@ -17,6 +17,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// the same tree in binary32 (sums of 32 binary32 site values; binary64
+// arithmetic runs at 1/64 of the binary32 rate on GB300)
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Sum of part[0 .. n) by one warp in a fixed order: lane l adds the entries
 // l + 32 j into 16 accumulators (j mod 16, the ragged end into the first),

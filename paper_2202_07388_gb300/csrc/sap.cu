@@ -63,11 +63,6 @@ __device__ __forceinline__ void store_smem(float* sm, int nsite, int t, const Sp
 // arithmetic runs at 1/64 of the binary32 rate on GB300, and these sums with
 // a binary64 division per thread had kept its FP64 pipe 36 % busy.  The
 // adaptive exit tests keep one binary64 sum (block_sum1).
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 __device__ __forceinline__ void block_sum3(float& a, float& b, float& c, double* red_d) {
   float* red = reinterpret_cast<float*>(red_d);
   a = warp_sum_f(a);
