@@ -205,7 +205,11 @@ int oq_clover_build_ex(oq_handle h, int lat, const oq_clover_params* p, void* st
 /* Convert canonical binary64 spinors (device) to packed `prec` fields and
  * back.  pack multiplies by `scale` before rounding (round to nearest even),
  * unpack divides by it.  subset OQ_EVEN / OQ_ODD read/write only those sites
- * of the canonical field (unpack leaves the other sites untouched). */
+ * of the canonical field (unpack leaves the other sites untouched); the
+ * canonical buffer holds nrhs full-lattice fields either way (V sites x 24
+ * doubles each, V = L0 L1 L2 L3), and the packed buffer the size
+ * oq_spinor_bytes gives for the subset.  Neither size can be checked here:
+ * a shorter buffer is read or written past its end. */
 int oq_spinor_pack(oq_handle h, int lat, int prec, int subset, const double* canon_dev,
                    void* packed_dev, double scale, int nrhs, void* stream);
 int oq_spinor_unpack(oq_handle h, int lat, int prec, int subset, const void* packed_dev,

@@ -22,6 +22,7 @@ cudaError_t launch_hop(const HopLaunch& L, const HopArgs& a, cudaStream_t s) {
       case P_F32: return L.nr == 2 ? launch_hop_mr2_f32(L, a, s) : launch_hop_mr4_f32(L, a, s);
       case P_BF16: return L.nr == 2 ? launch_hop_mr2_bf16(L, a, s) : launch_hop_mr4_bf16(L, a, s);
       case P_F16: return L.nr == 2 ? launch_hop_mr2_f16(L, a, s) : launch_hop_mr4_f16(L, a, s);
+      case P_DF64: return L.nr == 2 ? launch_hop_df2(L, a, s) : cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
   }

@@ -777,48 +777,6 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
   }
 }
 
-// grid_reduce for NR values per thread (right-hand sides rhs0 .. rhs0+NR-1
-// of the thread's row): smem needs (blockDim.x / 32) * blockDim.y * NR doubles
-// off[k]: rhs0 + k is gated off in this launch (skipped by every CTA, see grid_reduce).
-// The per-site values and their warp sums are binary32 (sums of 24 and then
-// 32 terms); everything beyond a warp is summed in binary64.
-template <int NR>
-__device__ __forceinline__ void grid_reduce_nr(const float (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
-                                               double* smem, unsigned cta, unsigned ncta, const bool (&off)[NR]) {
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    const float s = warp_sum_f(v[k]);
-    if ((tx & 31) == 0) smem[(ty * NR + k) * nw + (tx >> 5)] = (double)s;
-  }
-  __syncthreads();
-  if (tx >= 32) return;
-  for (int k = 0; k < NR; ++k) {
-    const int rhs = rhs0 + k;
-    if (rhs >= nrhs) break;
-    if (off[k]) continue;
-    bool last = false;
-    if (tx == 0) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += smem[(ty * NR + k) * nw + w];
-      ra.partials[(long)rhs * ncta + cta] = s;
-      __threadfence();
-      const unsigned t = atomicAdd(ra.counters + rhs, 1u);
-      last = (t == ncta - 1);
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      const double acc = warp_sum_partials(ra.partials + (long)rhs * ncta, ncta, tx);
-      if (tx == 0) {
-        ra.counters[rhs] = 0u;
-        run_finisher(ra, rhs, acc);
-      }
-    }
-  }
-}
-
 }  // namespace mr
 
 // CTA = blockDim.x sites x blockDim.y groups of NR right-hand sides
@@ -883,7 +841,7 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
 #pragma unroll
     for (int k = 0; k < NR; ++k)
       if (!live[k]) red[k] = 0.f;
-    mr::grid_reduce_nr<NR>(red, a.red, rhs0, a.nrhs, red_smem, blk, gridDim.x / ntile, off);
+    grid_reduce_nr<NR>(red, a.red, rhs0, a.nrhs, red_smem, blk, gridDim.x / ntile, off);
   }
 }
 

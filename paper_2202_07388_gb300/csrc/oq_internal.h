@@ -125,6 +125,8 @@ cudaError_t launch_hop_mr2_bf16(const HopLaunch& L, const HopArgs& a, cudaStream
 cudaError_t launch_hop_mr4_bf16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_mr2_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 cudaError_t launch_hop_mr4_f16(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
+// double-float, 2 right-hand sides per thread (packed two-lane arithmetic)
+cudaError_t launch_hop_df2(const HopLaunch& L, const HopArgs& a, cudaStream_t s);
 
 // geometry of a sub-domain extended by one time slice on each side
 inline Geom halo_ext_geom(const Geom& g) {

@@ -140,4 +140,49 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs
   }
 }
 
+// grid_reduce for NR values per thread (right-hand sides rhs0 .. rhs0+NR-1
+// of the thread's row): smem needs (blockDim.x / 32) * blockDim.y * NR doubles;
+// off[k]: rhs0 + k is gated off in this launch (skipped by every CTA, as in
+// grid_reduce).  Binary32 per-site values (the multi-rhs binary32 kernels:
+// sums of 24 squares) are summed over the warp in binary32 (32 terms);
+// binary64 values in binary64.  Everything beyond a warp is binary64.
+__device__ __forceinline__ double warp_total(float v) { return (double)warp_sum_f(v); }
+__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
+template <int NR, typename T>
+__device__ __forceinline__ void grid_reduce_nr(const T (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
+                                               double* smem, unsigned cta, unsigned ncta, const bool (&off)[NR]) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const double s = warp_total(v[k]);
+    if ((tx & 31) == 0) smem[(ty * NR + k) * nw + (tx >> 5)] = s;
+  }
+  __syncthreads();
+  if (tx >= 32) return;
+  for (int k = 0; k < NR; ++k) {
+    const int rhs = rhs0 + k;
+    if (rhs >= nrhs) break;
+    if (off[k]) continue;
+    bool last = false;
+    if (tx == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += smem[(ty * NR + k) * nw + w];
+      ra.partials[(long)rhs * ncta + cta] = s;
+      __threadfence();
+      const unsigned t = atomicAdd(ra.counters + rhs, 1u);
+      last = (t == ncta - 1);
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      const double acc = warp_sum_partials(ra.partials + (long)rhs * ncta, ncta, tx);
+      if (tx == 0) {
+        ra.counters[rhs] = 0u;
+        run_finisher(ra, rhs, acc);
+      }
+    }
+  }
+}
+
 }  // namespace oq

@@ -43,6 +43,21 @@ std::vector<TuneVal> candidates(int prec, int nrhs) {
           c.push_back(v);
         }
   }
+  // double-float, two right-hand sides per thread (packed two-lane arithmetic)
+  if (prec == P_DF64 && nrhs >= 2) {
+    const int bxs2[] = {32, 64, 128};
+    for (int cap = 0; cap < 2; ++cap)
+      for (int bx : bxs2)
+        for (int by = 1; by <= 2; ++by) {
+          if (bx * by > 128 || 2 * by > nrhs) continue;
+          TuneVal v;
+          v.bx = bx;
+          v.by = by;
+          v.nr = 2;
+          v.regcap = cap;
+          c.push_back(v);
+        }
+  }
   // several right-hand sides per thread (binary32 arithmetic types)
   if (prec == P_F32 || prec == P_BF16 || prec == P_F16) {
     const int nrs[] = {2, 4};
@@ -70,6 +85,9 @@ bool valid_shape(const LatCtx& L, int prec, int nrhs, const TuneVal& v) {
     if (v.bx * v.by > 256) return false;
     if (v.regcap != 0 && !(prec == P_DF64 && (v.regcap == 1 || v.regcap == 2) && v.bx * v.by <= 128))
       return false;
+  } else if (v.nr == 2 && prec == P_DF64) {
+    // two rhs per thread in packed double-float: <= 128 threads, regcap 0 / 1
+    if (v.bx * v.by > 128 || 2 * v.by > nrhs || v.regcap < 0 || v.regcap > 1) return false;
   } else if (v.nr == 2 || v.nr == 4) {
     if (prec != P_F32 && prec != P_BF16 && prec != P_F16) return false;
     if (v.bx * v.by > 128 || v.regcap < 0 || v.regcap > 2) return false;

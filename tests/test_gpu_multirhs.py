@@ -24,6 +24,21 @@ def _oq():
     return oq
 
 
+def torch_equal(x, y):
+    import torch
+    return bool(torch.equal(x, y))
+
+
+def unpack(h, packed, shape, n, even=False):
+    oq = _oq()
+    out = to_dev(np.zeros(shape, dtype=np.complex128))
+    if even:
+        h.unpack(packed, out, oq.DF64, oq.EVEN, nrhs=n)
+    else:
+        h.unpack(packed, out, oq.DF64, nrhs=n)
+    return out
+
+
 def _pin(h, prec, nrhs, bx, by, nr, cap, fmt):
     for mode in (0, 1, 2):
         h.tune_set(prec, mode, nrhs, bx, by, nr=nr, regcap=cap, link_fmt=fmt)
@@ -159,6 +174,89 @@ def test_double_float_kernels_pinned(case, cap):
         for k in range(n):
             ref = dirac.dw_hat_dagger(u, a, ainv, ev[k]) if dagger else dirac.dw_hat(u, a, ainv, ev[k])
             assert rel_err(got[k], ref) < TOL[4]
+
+
+def _df64_outputs(h, psi, ev, n):
+    """Packed double-float Dw, Dhat and their adjoints of n right-hand sides."""
+    oq = _oq()
+    outs = []
+    for dagger in (False, True):
+        pin, pout = h.new_packed(oq.DF64, nrhs=n), h.new_packed(oq.DF64, nrhs=n)
+        h.pack(to_dev(psi), pin, oq.DF64, nrhs=n)
+        h.dw(pin, pout, oq.DF64, nrhs=n, dagger=dagger)
+        outs.append(pout.clone())
+        pin, pout = h.new_packed(oq.DF64, oq.EVEN, nrhs=n), h.new_packed(oq.DF64, oq.EVEN, nrhs=n)
+        h.pack(to_dev(ev), pin, oq.DF64, oq.EVEN, nrhs=n)
+        h.dw_hat(pin, pout, oq.DF64, nrhs=n, dagger=dagger)
+        outs.append(pout.clone())
+    return outs
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("bx,by,cap", [(32, 1, 0), (64, 2, 0), (32, 2, 1)])
+def test_double_float_two_rhs_per_thread(case, bx, by, cap):
+    """Double-float passes with two right-hand sides per thread (packed
+    two-lane arithmetic, links and clover loaded once): bit for bit the
+    one-rhs kernel's Dw, Dhat and adjoints for 5 right-hand sides (a ragged
+    pair), and within 1e-12 of the FP64 oracle."""
+    oq = _oq()
+    dims, eps, seed, kappa, csw = case
+    u, a, ainv = oracle_case(dims, eps, seed, kappa, csw)
+    h = make_handle(dims, u, kappa, csw, oq.LINK_12)
+    n = 5
+    psi = synth.make_source(dims, seed + 600, nrhs=n)
+    ev = np.stack([dirac.even_part(p) for p in psi])
+    for mode in (0, 1, 2):
+        h.tune_set(oq.DF64, mode, n, 32, 2, nr=1, regcap=0)
+    one = _df64_outputs(h, psi, ev, n)
+    for mode in (0, 1, 2):
+        h.tune_set(oq.DF64, mode, n, bx, by, nr=2, regcap=cap)
+    assert h.tune_get(oq.DF64, 1, n)[4:] == (2, cap)
+    two = _df64_outputs(h, psi, ev, n)
+    for k, (x1, x2) in enumerate(zip(one, two)):
+        assert torch_equal(x1, x2), k
+    outs = iter(two)
+    for dagger in (False, True):
+        got = from_dev(unpack(h, next(outs), psi.shape, n), psi.shape)
+        for k in range(n):
+            ref = dirac.dw_dagger(u, a, psi[k]) if dagger else dirac.dw(u, a, psi[k])
+            assert rel_err(got[k], ref) < TOL[4]
+        got = from_dev(unpack(h, next(outs), ev.shape, n, even=True), ev.shape)
+        for k in range(n):
+            ref = dirac.dw_hat_dagger(u, a, ainv, ev[k]) if dagger else dirac.dw_hat(u, a, ainv, ev[k])
+            assert rel_err(got[k], ref) < TOL[4]
+    assert h.tune_set(oq.DF64, 1, n, 128, 2, nr=2, regcap=0, check=False) == oq.ERR_ARG   # <= 128 threads
+    assert h.tune_set(oq.DF64, 1, n, 64, 1, nr=2, regcap=2, check=False) == oq.ERR_ARG   # regcap 0 / 1
+    assert h.tune_set(oq.DF64, 1, n, 64, 1, nr=4, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.DF64, 1, 1, 64, 1, nr=2, check=False) == oq.ERR_ARG             # nr > nrhs
+
+
+def test_double_float_resets_two_rhs_per_thread_same_solve():
+    """The batched F16 CGNE with double-float resets gives the same solution
+    bit for bit, and the same steps and resets, whether its double-float
+    reset passes run one or two right-hand sides per thread."""
+    oq = _oq()
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.135, 1.0)
+    n = 5
+    eta = np.stack([dirac.even_part(e) for e in synth.make_source(dims, 93, nrhs=n)])
+    runs = []
+    for nr in (1, 2):
+        h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+        for mode in (0, 1, 2):
+            h.tune_set(oq.DF64, mode, n, 32, 2, nr=nr, regcap=0)
+        psi = to_dev(np.zeros_like(eta))
+        rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5000, sdtype=oq.F16), nrhs=n)
+        assert rc == oq.OK and all(s["converged"] for s in st)
+        assert max(s["resets"] for s in st) >= 2      # intermediate double-float resets ran
+        runs.append((from_dev(psi, eta.shape), [(s["steps"], s["resets"]) for s in st]))
+    assert runs[0][1] == runs[1][1]
+    assert np.array_equal(runs[0][0], runs[1][0])
+    x = runs[1][0]
+    for k in range(n):
+        ax = dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, x[k]))
+        r = np.linalg.norm((eta[k] - ax).reshape(-1)) / np.linalg.norm(eta[k].reshape(-1))
+        assert r <= 1.05e-10
 
 
 def test_profile_separates_passes_and_adjoints():
