@@ -34,6 +34,35 @@ __device__ __forceinline__ const char* fsite(const char* base, long Vh, long hal
   return base + h * half_bytes;
 }
 
+// <a, b> of one site added to (re, im).  Binary32 fields (the GCR Krylov
+// vectors): the site's 12 complex terms summed in binary32 by FMAs, the sums
+// over sites in binary64 -- binary64 arithmetic runs at 1/64 of the binary32
+// rate on GB300, and widening every term had made these dots FP64-bound.
+// Binary64 fields: binary64 throughout.
+template <typename R>
+__device__ __forceinline__ void site_dot(const Spinor<R>& a, const Spinor<R>& b, double& re, double& im) {
+  if constexpr (std::is_same<R, float>::value) {
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sr = fmaf(a.c[s][c].re, b.c[s][c].re, fmaf(a.c[s][c].im, b.c[s][c].im, sr));
+        si = fmaf(a.c[s][c].re, b.c[s][c].im, fmaf(-a.c[s][c].im, b.c[s][c].re, si));
+      }
+    re += (double)sr;
+    im += (double)si;
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        re += (double)a.c[s][c].re * b.c[s][c].re + (double)a.c[s][c].im * b.c[s][c].im;
+        im += (double)a.c[s][c].re * b.c[s][c].im - (double)a.c[s][c].im * b.c[s][c].re;
+      }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(VB) vec_dots_kernel(const char* X, long xstride, const char* y, long Vh,
                                                       long hb, RedArgs ra, int nl) {
@@ -46,13 +75,7 @@ __global__ void __launch_bounds__(VB) vec_dots_kernel(const char* X, long xstrid
     Spinor<R> a, b;
     load_spinor<P>(fsite(X + l * xstride, Vh, hb, j, &i), Vh, i, a);
     load_spinor<P>(fsite(y, Vh, hb, j, &i), Vh, i, b);
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        re += (double)a.c[s][c].re * b.c[s][c].re + (double)a.c[s][c].im * b.c[s][c].im;
-        im += (double)a.c[s][c].re * b.c[s][c].im - (double)a.c[s][c].im * b.c[s][c].re;
-      }
+    site_dot(a, b, re, im);
   }
   grid_reduce(re, ra, 2 * l, 2 * nl, smem, blockIdx.x, gridDim.x);
   __syncthreads();
@@ -102,11 +125,8 @@ __global__ void __launch_bounds__(VB) vec_scale_dot_kernel(char* chi, const char
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        v.c[s][a] = (R)inv_b * v.c[s][a];
-        re += (double)v.c[s][a].re * r.c[s][a].re + (double)v.c[s][a].im * r.c[s][a].im;
-        im += (double)v.c[s][a].re * r.c[s][a].im - (double)v.c[s][a].im * r.c[s][a].re;
-      }
+      for (int a = 0; a < 3; ++a) v.c[s][a] = (R)inv_b * v.c[s][a];
+    site_dot(v, r, re, im);
     store_spinor<P>(cb, Vh, i, v);
   }
   grid_reduce(re, ra, 0, 2, smem, blockIdx.x, gridDim.x);
