@@ -172,13 +172,19 @@ __device__ __forceinline__ void hop_loop_df(const HopArgs& a, const char* in, in
     for (int c = 0; c < 3; ++c) acc.c[s2][c] = cx<dfloat>{df_norm(acc.c[s2][c].re), df_norm(acc.c[s2][c].im)};
 }
 
+// value type of a site's reduction contribution: binary32 for the
+// binary32-arithmetic types (their per-site norms are binary32 sums), else
+// binary64 (see warp_total)
+template <int P>
+using RedT = typename std::conditional<P == P_F64 || P == P_DF64, double, float>::type;
+
 // One output site i (parity p) of right-hand side rhs: the stencil, the
 // clover term and the epilogue.  Returns the site's contribution to the
 // epilogue's reduction (0 if none).
 template <int P, int FMT, int MODE, bool DAG, int EPI>
-__device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, int p) {
+__device__ __forceinline__ RedT<P> hop_site(const HopArgs& a, long i, int rhs, int p) {
   typedef typename PrecTraits<P>::R R;
-  double red = 0.0;
+  RedT<P> red = 0;
     int x[4];
     eo_coords(a.g, p, i, x);
     const long par_in = (MODE == HOP_DW) ? (long)(1 - p) * a.half_bytes : 0;
@@ -246,7 +252,7 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
 
     if constexpr (EPI == EPI_NONE || EPI == EPI_NORM) {
       store_spinor<P>((char*)a.out + rhs * a.out_stride + par_out, a.g.Vh, i, res);
-      if constexpr (EPI == EPI_NORM) red = site_norm2(res);
+      if constexpr (EPI == EPI_NORM) red = (RedT<P>)site_norm2(res);
     } else if constexpr (EPI == EPI_CG) {
       // q = res; x += alpha p; r -= alpha q  (x in F64 for F64 solves, else F32)
       constexpr int XP = (P == P_F64) ? P_F64 : P_F32;
@@ -271,7 +277,7 @@ __device__ __forceinline__ double hop_site(const HopArgs& a, long i, int rhs, in
       round_trip<P>(rv);
       store_spinor<XP>((char*)a.ep_x + rhs * a.ep_x_stride, a.g.Vh, i, xv);
       store_spinor<P>((char*)a.ep_r + rhs * a.ep_r_stride, a.g.Vh, i, rv);
-      red = site_norm2(rv);
+      red = (RedT<P>)site_norm2(rv);
     } else if constexpr (EPI == EPI_RESID64) {
       Spinor<R> e;
       load_spinor<P>((const char*)a.ep_eta + rhs * a.ep_eta_stride, a.g.Vh, i, e);
@@ -320,7 +326,7 @@ __device__ __forceinline__ void hop_kernel_body(const HopArgs& a, double* red_sm
   record_live(a);
   const bool off = a.cg && rhs < a.nrhs && a.cg[rhs].mode != a.gate;  // gated off by the solver state
   const bool live = (i < a.g.Vh) && (rhs < a.nrhs) && !off;
-  double red = 0.0;
+  RedT<P> red = 0;
   if (live) red = hop_site<P, FMT, MODE, DAG, EPI>(a, i, rhs, p);
   if constexpr (EPI != EPI_NONE) {
     grid_reduce(red, a.red, rhs, a.nrhs, red_smem, (unsigned)blk, gridDim.x / ntile, off);
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(256) hop_batch_kernel(const HopArgs* __restric
     const long i = blk * blockDim.x + threadIdx.x;
     const bool off = a.cg && a.cg[0].mode != a.gate;  // the system is gated off by its solver state
     const bool live = i < a.g.Vh && !off;
-    double red = 0.0;
+    RedT<P> red = 0;
     if (live) red = hop_site<P, FMT, MODE, DAG, EPI>(a, i, 0, p);
     if constexpr (EPI != EPI_NONE) {
       const unsigned nblk = (unsigned)((a.g.Vh + blockDim.x - 1) / blockDim.x);

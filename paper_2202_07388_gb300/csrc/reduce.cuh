@@ -52,6 +52,13 @@ __device__ __forceinline__ double warp_sum_partials(const double* part, unsigned
   return warp_sum(acc[0]);
 }
 
+// The sum of a warp's values: binary32 values (per-site sums of binary32
+// fields, e.g. 24 squares) are summed over the warp in binary32 (32 terms),
+// binary64 values in binary64; either way the result and everything beyond
+// the warp are binary64.
+__device__ __forceinline__ double warp_total(float v) { return (double)warp_sum_f(v); }
+__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
+
 __device__ __forceinline__ void run_finisher(const RedArgs& ra, int rhs, double sum) {
   CgState* st = ra.cg ? ra.cg + rhs : nullptr;
   if (ra.fin != FIN_STORE && st->mode != ra.gate) return;  // rhs was not live in this launch
@@ -103,18 +110,20 @@ __device__ __forceinline__ void run_finisher(const RedArgs& ra, int rhs, double 
 }
 
 // Called by all threads of a CTA of shape (bx, by): thread (tx, ty) holds v
-// for right-hand side `rhs` (one rhs per row).  `cta` numbers this CTA among
+// (binary32 or binary64, see warp_total) for right-hand side `rhs` (one rhs
+// per row).  `cta` numbers this CTA among
 // the `ncta` CTAs that contribute to the same rhs.  smem needs bx*by/32 doubles.
 // off: the rhs is gated off in this launch (its solver state is not in the
 // launch's mode).  Every CTA of the launch sees the same state (it changes
 // only in the finisher of the last CTA), so all of them skip the rhs: no
 // partial, no ticket, no finisher.
-__device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs, int nrhs,
-                                            double* smem, unsigned cta, unsigned ncta, bool off = false) {
+template <typename T>
+__device__ __forceinline__ void grid_reduce(T v, const RedArgs& ra, int rhs, int nrhs, double* smem, unsigned cta,
+                                            unsigned ncta, bool off = false) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nw = blockDim.x >> 5;  // warps per rhs row (blockDim.x % 32 == 0)
-  v = warp_sum(v);
-  if ((tx & 31) == 0) smem[ty * nw + (tx >> 5)] = v;
+  const double w = warp_total(v);
+  if ((tx & 31) == 0) smem[ty * nw + (tx >> 5)] = w;
   __syncthreads();
   if (tx < 32) {
     bool last = false;
@@ -143,11 +152,7 @@ __device__ __forceinline__ void grid_reduce(double v, const RedArgs& ra, int rhs
 // grid_reduce for NR values per thread (right-hand sides rhs0 .. rhs0+NR-1
 // of the thread's row): smem needs (blockDim.x / 32) * blockDim.y * NR doubles;
 // off[k]: rhs0 + k is gated off in this launch (skipped by every CTA, as in
-// grid_reduce).  Binary32 per-site values (the multi-rhs binary32 kernels:
-// sums of 24 squares) are summed over the warp in binary32 (32 terms);
-// binary64 values in binary64.  Everything beyond a warp is binary64.
-__device__ __forceinline__ double warp_total(float v) { return (double)warp_sum_f(v); }
-__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
+// grid_reduce); value types as in grid_reduce.
 template <int NR, typename T>
 __device__ __forceinline__ void grid_reduce_nr(const T (&v)[NR], const RedArgs& ra, int rhs0, int nrhs,
                                                double* smem, unsigned cta, unsigned ncta, const bool (&off)[NR]) {
