@@ -275,7 +275,8 @@ int oq_dw_hat_apply_noalloc(oq_handle h, int lat, int prec, const void* in_dev, 
  * 128; regcap 1: at most 128 registers per thread, 2: at most 168), for the
  * nr > 1 kernels regcap 2: the cap of 1 with each hop's neighbour spinors and
  * link copied ahead into shared memory while the previous hop is computed
- * (12-real links only), and for
+ * (12-real links only), regcap 3 (nr = 2): the staged kernel of regcap 2
+ * capped at 168 registers instead of 128, and for
  * binary32-arithmetic kernels
  * on 12-real links the 18-real copy the handle keeps (fewer instructions,
  * more bytes).  oq_tune_get reports the chosen launch and its time

@@ -785,10 +785,12 @@ __device__ __forceinline__ void site(const HopArgs& a, uint32_t i, int rhs0, int
 // NR = 4: at least 16 / 12 warps per SM, with some spilling); CAP = 0 lets
 // the compiler keep all neighbour loads of a site in flight.
 // CAP = 2: the register cap of CAP = 1 and the hop operands staged in
-// shared memory (site<..., PF = true>; 12-real links only).
+// shared memory (site<..., PF = true>; 12-real links only).  CAP = 3 (NR = 2):
+// staged with the cap of 168 registers (12 warps per SM): fewer spills, which
+// the pass-2 kernels gain more from than from the extra warps.
 template <int NR, int CAP>
 struct MrBounds {
-  static constexpr int min_blocks = CAP == 0 ? 1 : NR == 2 ? 4 : 3;
+  static constexpr int min_blocks = CAP == 0 ? 1 : (NR == 2 && CAP != 3) ? 4 : 3;
 };
 // 16-byte slots per thread of a staged launch: 2 stages of NR * chunks + 3,
 // for pass 2 and Dw of NR * chunks / 2 more (the site-local spinors); rounded
@@ -802,15 +804,15 @@ template <int P, int NR, int MODE>
 constexpr size_t mr_stage_bytes(int nthr) {
   return (size_t)mr_stage_slots<P, NR, MODE>() * 16 * nthr;
 }
-// the per-thread slots of a launch (staged: CAP = 2)
+// the per-thread slots of a launch (staged: CAP = 2, 3)
 template <int P, int NR, int MODE, int CAP>
 constexpr int mr_slots() {
-  return CAP == 2 ? mr_stage_slots<P, NR, MODE>() : 0;
+  return CAP >= 2 ? mr_stage_slots<P, NR, MODE>() : 0;
 }
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, int CAP>
 __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_kernel(const HopArgs a) {
   extern __shared__ double dyn_smem[];
-  constexpr bool PF = CAP == 2;
+  constexpr bool PF = CAP >= 2;
   constexpr int NSL = mr_slots<P, NR, MODE, CAP>();
   const uint32_t nthr = blockDim.x * blockDim.y;
   // the threads' slots first, then the reduction scratch
@@ -845,7 +847,7 @@ __global__ void __launch_bounds__(128, (MrBounds<NR, CAP>::min_blocks)) hop_mr_k
   }
 }
 
-// a staged launch (CAP 2): the threads' slots, then `smem` bytes of
+// a staged launch (CAP 2, 3): the threads' slots, then `smem` bytes of
 // reduction scratch; above 48 KiB the kernel is allowed the device's opt-in
 // limit (once per instantiation)
 template <int P, int FMT, int MODE, bool DAG, int EPI, int NR, int CAP>
@@ -878,6 +880,11 @@ static cudaError_t launch_mr_one(const HopLaunch& L, const HopArgs& a, cudaStrea
   if (L.regcap == 2) {
     if constexpr (FMT == LINK_12)
       return launch_mr_smem<P, FMT, MODE, DAG, EPI, NR, 2>(grid, block, smem, a, s);
+    return cudaErrorInvalidValue;
+  }
+  if (L.regcap == 3) {
+    if constexpr (FMT == LINK_12 && NR == 2)
+      return launch_mr_smem<P, FMT, MODE, DAG, EPI, NR, 3>(grid, block, smem, a, s);
     return cudaErrorInvalidValue;
   }
   if (L.regcap)

@@ -8,6 +8,8 @@
 // pass 2 is also timed with its norm and CG-update epilogues (on scratch
 // operands: alpha = 0, reductions only stored), which keep their own choice.
 // oq_tune_set pins a launch by hand for every epilogue of a mode.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -18,6 +20,36 @@
 using namespace oq;
 
 namespace {
+
+// Scratch fields for timing: a fixed pseudo-random pattern of values in
+// [-1, 1) in the storage type (element k from an integer hash of k), so that
+// the launches are timed on data like a solver's rather than on zeros.
+// Double-float elements are (hi, 0) pairs.
+__global__ void tune_fill_kernel(void* p, size_t n, int prec) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)k * 2654435761u ^ (uint32_t)(k >> 32) * 2246822519u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const float v = (float)(int32_t)h * (1.f / 2147483648.f);
+    switch (prec) {
+      case P_F64: static_cast<double*>(p)[k] = (double)v; break;
+      case P_F32: static_cast<float*>(p)[k] = v; break;
+      case P_BF16: static_cast<__nv_bfloat16*>(p)[k] = __float2bfloat16_rn(v); break;
+      case P_F16: static_cast<__half*>(p)[k] = __float2half_rn(v); break;
+      default: static_cast<float2*>(p)[k] = make_float2(v, 0.f); break;  // double-float
+    }
+  }
+}
+cudaError_t tune_fill(void* p, size_t bytes, int prec, cudaStream_t s) {
+  const size_t esize = (prec == P_F64 || prec == P_DF64) ? 8 : prec == P_F32 ? 4 : 2;
+  const size_t n = bytes / esize;
+  if (n == 0) return cudaSuccess;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  tune_fill_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, n, prec);
+  return cudaGetLastError();
+}
 
 std::vector<TuneVal> candidates(int prec, int nrhs) {
   std::vector<TuneVal> c;
@@ -63,7 +95,7 @@ std::vector<TuneVal> candidates(int prec, int nrhs) {
     const int nrs[] = {2, 4};
     for (int nr : nrs) {
       if (nr > nrhs) continue;
-      for (int cap = 0; cap < 3; ++cap)
+      for (int cap = 0; cap < (nr == 2 ? 4 : 3); ++cap)
         for (int bx : bxs)
           for (int by = 1; by <= 2; ++by) {
             if (bx * by > 128 || by * nr > nrhs) continue;
@@ -90,9 +122,9 @@ bool valid_shape(const LatCtx& L, int prec, int nrhs, const TuneVal& v) {
     if (v.bx * v.by > 128 || 2 * v.by > nrhs || v.regcap < 0 || v.regcap > 1) return false;
   } else if (v.nr == 2 || v.nr == 4) {
     if (prec != P_F32 && prec != P_BF16 && prec != P_F16) return false;
-    if (v.bx * v.by > 128 || v.regcap < 0 || v.regcap > 2) return false;
-    // staged hops (regcap 2) read 12-real links
-    if (v.regcap == 2 && (v.link_fmt == LINK_18 || (v.link_fmt == -1 && L.link_fmt != LINK_12))) return false;
+    if (v.bx * v.by > 128 || v.regcap < 0 || v.regcap > 3 || (v.regcap == 3 && v.nr != 2)) return false;
+    // staged hops (regcap 2, 3) read 12-real links
+    if (v.regcap >= 2 && (v.link_fmt == LINK_18 || (v.link_fmt == -1 && L.link_fmt != LINK_12))) return false;
   } else {
     return false;
   }
@@ -122,7 +154,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
   int rc = h->workspace(lat, "tune_in", full, &in);
   if (!rc) rc = h->workspace(lat, "tune_out", full, &out);
   if (rc) return rc;
-  if (cudaMemsetAsync(in, 0, full, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (tune_fill(in, full, prec, s) != cudaSuccess) return OQ_ERR_CUDA;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return OQ_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -146,8 +178,8 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
       cudaEventDestroy(e1);
       return rc;
     }
-    if (cudaMemsetAsync(xs, 0, (size_t)spinor_half_bytes(L.g.Vh, XP) * nrhs, s) != cudaSuccess ||
-        cudaMemsetAsync(rs, 0, half * nrhs, s) != cudaSuccess ||
+    if (tune_fill(xs, (size_t)spinor_half_bytes(L.g.Vh, XP) * nrhs, XP, s) != cudaSuccess ||
+        tune_fill(rs, half * nrhs, prec, s) != cudaSuccess ||
         cudaMemsetAsync(cgs, 0, sizeof(CgState) * nrhs, s) != cudaSuccess)  // mode RUN, alpha 0
       ret = OQ_ERR_CUDA;
   }
@@ -195,7 +227,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
     const bool two_fmts = prec != P_F64 && prec != P_DF64 && L.link_fmt == LINK_12 && L.u32_18.p;
     for (int fmt = L.link_fmt; fmt >= 0; fmt = (two_fmts && fmt == LINK_12) ? LINK_18 : -1) {
       for (TuneVal c : candidates(prec, nrhs)) {
-        if (c.regcap == 2 && c.nr > 1 && fmt != LINK_12) continue;  // staged hops read 12-real links
+        if (c.regcap >= 2 && c.nr > 1 && fmt != LINK_12) continue;  // staged hops read 12-real links
         HopLaunch l = h->hop_launch(lat, prec, mode, 0, var.epi, nrhs);
         l.bx = c.bx;
         l.by = c.by;

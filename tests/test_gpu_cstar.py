@@ -67,7 +67,7 @@ def test_cstar_dw_and_dhat(cs, prec, fmt):
 
 
 @pytest.mark.parametrize("cs", [2, 3])
-@pytest.mark.parametrize("nr,cap", [(2, 0), (2, 1), (2, 2), (4, 2)])
+@pytest.mark.parametrize("nr,cap", [(2, 0), (2, 1), (2, 2), (4, 2), (2, 3)])
 def test_cstar_multi_rhs_kernels(cs, nr, cap):
     """The multi-rhs kernel computes its neighbour indices itself (32-bit
     strides): the shifted wraps of x2 and x3 there."""

@@ -44,10 +44,16 @@ def _pin(h, prec, nrhs, bx, by, nr, cap, fmt):
         h.tune_set(prec, mode, nrhs, bx, by, nr=nr, regcap=cap, link_fmt=fmt)
 
 
+SHAPES = [(2, 5, 64, 2), (4, 5, 32, 1), (4, 8, 128, 1), (2, 2, 32, 1)]
+# (regcap, link format): regcap 2 and 3 stage the hop operands (12-real links);
+# regcap 3 (the staged kernel at 168 registers) exists for 2 rhs per thread
+CAPS = [(0, 0), (0, 1), (1, 0), (1, 1), (2, 1), (3, 1)]
+LAUNCHES = [sh + cf for sh in SHAPES for cf in CAPS if not (cf[0] == 3 and sh[0] != 2)]
+
+
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("prec", [1, 2, 3])
-@pytest.mark.parametrize("nr,nrhs,bx,by", [(2, 5, 64, 2), (4, 5, 32, 1), (4, 8, 128, 1), (2, 2, 32, 1)])
-@pytest.mark.parametrize("cap,fmt", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("nr,nrhs,bx,by,cap,fmt", LAUNCHES)
 def test_multi_rhs_dw_and_dw_hat(case, prec, nr, nrhs, bx, by, cap, fmt):
     oq = _oq()
     dims, eps, seed, kappa, csw = case
@@ -78,7 +84,7 @@ def test_multi_rhs_dw_and_dw_hat(case, prec, nr, nrhs, bx, by, cap, fmt):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
-@pytest.mark.parametrize("nr,cap", [(2, 0), (4, 1), (2, 2), (4, 2)])
+@pytest.mark.parametrize("nr,cap", [(2, 0), (4, 1), (2, 2), (4, 2), (2, 3)])
 def test_multi_rhs_cgne_epilogues(prec, nr, cap):
     """The norm and CG-update epilogues of the multi-rhs kernel inside the
     batched CGNE: 5 right-hand sides (a ragged group), every one to a binary64
@@ -121,7 +127,9 @@ def test_tune_set_rejects_inadmissible_launches():
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=3, check=False) == oq.ERR_ARG
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, link_fmt=0, check=False) == oq.ERR_ARG  # staged: 12-real
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, link_fmt=1) == oq.OK
-    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=3, check=False) == oq.ERR_ARG
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=3) == oq.OK     # staged, 168 registers
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=4, regcap=3, check=False) == oq.ERR_ARG   # 2 rhs per thread only
+    assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=4, check=False) == oq.ERR_ARG
     assert h.tune_set(oq.F16, 1, 4, 64, 1, nr=1, regcap=1, check=False) == oq.ERR_ARG   # cap: nr > 1 or DF64
     assert h.tune_set(oq.DF64, 1, 4, 128, 2, nr=1, regcap=1, check=False) == oq.ERR_ARG  # capped: <= 128 threads
     assert h.tune_set(oq.DF64, 1, 4, 64, 2, nr=1, regcap=1) == oq.OK
@@ -138,6 +146,7 @@ def test_tune_set_rejects_inadmissible_launches():
     h2 = make_handle(dims, u, 0.13, 1.0, oq.LINK_18)
     assert h2.tune_set(oq.F32, 1, 1, 64, 1, link_fmt=oq.LINK_12, check=False) == oq.ERR_ARG
     assert h2.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=2, check=False) == oq.ERR_ARG  # staged: 12-real links
+    assert h2.tune_set(oq.F16, 1, 4, 64, 1, nr=2, regcap=3, check=False) == oq.ERR_ARG
 
 
 @pytest.mark.parametrize("case", CASES)

@@ -157,13 +157,14 @@ def test_autotuner_picks_valid_shapes_and_keeps_results():
         shapes = h.autotune(prec, nrhs=4)
         for mode, (bx, by, ms, fmt, nr, cap) in shapes.items():
             assert bx % 32 == 0 and bx * by <= (256 if nr == 1 else 128) and ms > 0
-            assert fmt in ("12-real", "18-real") and nr in (1, 2, 4) and cap in (0, 1, 2)
-            assert cap != 2 or (nr > 1 and fmt == "12-real")      # staged hops: multi-rhs, 12-real links
+            assert fmt in ("12-real", "18-real") and nr in (1, 2, 4) and cap in (0, 1, 2, 3)
+            assert cap < 2 or (nr > 1 and fmt == "12-real")       # staged hops: multi-rhs, 12-real links
+            assert cap != 3 or nr == 2
         # pass 2 is tuned once per epilogue; epi 0 is what oq_tune_get reports
         epis = h.tuned_epilogues(prec, nrhs=4)
         assert epis["store"] == shapes[2]
         for bx, by, ms, fmt, nr, cap in epis.values():
-            assert bx % 32 == 0 and ms > 0 and (cap != 2 or (nr > 1 and fmt == "12-real"))
+            assert bx % 32 == 0 and ms > 0 and (cap < 2 or (nr > 1 and fmt == "12-real"))
         pin, pout = h.new_packed(prec, nrhs=4), h.new_packed(prec, nrhs=4)
         h.pack(to_dev(psi), pin, prec, nrhs=4)
         h.dw(pin, pout, prec, nrhs=4)
