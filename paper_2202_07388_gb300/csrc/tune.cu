@@ -154,7 +154,8 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
   int rc = h->workspace(lat, "tune_in", full, &in);
   if (!rc) rc = h->workspace(lat, "tune_out", full, &out);
   if (rc) return rc;
-  if (tune_fill(in, full, prec, s) != cudaSuccess) return OQ_ERR_CUDA;
+  if (tune_fill(in, full, prec, s) != cudaSuccess || tune_fill(out, full, prec, s) != cudaSuccess)
+    return OQ_ERR_CUDA;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return OQ_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -196,8 +197,10 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
     const int mode = var.mode;
     HopArgs a = h->hop_args(lat, prec);
     a.nrhs = nrhs;
+    // distinct fields as in a solve: pass 2 reads its odd input from the first
+    // half of `in` and its even in2 from the second (Dw: in2 is its input)
     a.in = in;
-    a.in2 = in;
+    a.in2 = mode == HOP_P2 ? (void*)((char*)in + half * nrhs) : in;
     a.out = out;
     a.p = mode == HOP_P1 ? 1 : 0;
     if (mode == HOP_DW) {
@@ -215,7 +218,7 @@ extern "C" int oq_autotune(oq_handle h, int lat, int prec, int nrhs, void* strea
         a.gate = MODE_RUN;
         a.ep_x = xs;
         a.ep_x_stride = (long)spinor_half_bytes(L.g.Vh, XP);
-        a.ep_p = in;
+        a.ep_p = out;  // the CG update writes no out: the search direction p
         a.ep_p_stride = (long)half;
         a.ep_r = rs;
         a.ep_r_stride = (long)half;
