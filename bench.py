@@ -202,11 +202,11 @@ def stencil_source_hash():
     return h.hexdigest()
 
 
-def write_traffic(csvs):
-    """profiles/traffic.json from ncu --csv logs of the cgne profile case (32x32^3, 12 rhs):
-    dram__bytes_read.sum + dram__bytes_write.sum per launch / Vh, averaged per kernel variant
-    (named as kernel_key names them, adjoint and plain instantiations together), with the
-    hash of the stencil sources the capture was taken on."""
+def traffic_kernels(csvs):
+    """DRAM bytes per even site of each stencil kernel variant in ncu --csv logs of the cgne
+    profile case (32x32^3, 12 rhs): dram__bytes_read.sum + dram__bytes_write.sum per launch / Vh,
+    averaged over the variant's launches (named as kernel_key names them, adjoint and plain
+    instantiations together)."""
     import csv
     import re
     vh = 32 ** 4 // 2
@@ -238,11 +238,18 @@ def write_traffic(csvs):
             e = kern.setdefault(key, {"dram_bytes_per_site": 0.0, "launches": 0, "capture": os.path.basename(path)})
             e["dram_bytes_per_site"] = (e["dram_bytes_per_site"] * e["launches"] + b) / (e["launches"] + 1)
             e["launches"] += 1
+    return kern
+
+
+def write_traffic(csvs, path=None):
+    """profiles/traffic.json (or `path`): traffic_kernels of the logs, the commands that made
+    them and the hash of the stencil sources the capture was taken on."""
+    kern = traffic_kernels(csvs)
     out = {"note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch / Vh, 32x32^3 lattice, 12 rhs; "
                    "bench scales by its own Vh",
            "commands": TRAFFIC_COMMANDS, "lattice": "32x32x32x32", "nrhs": 12, "kernels": kern,
            "source_sha256": stencil_source_hash()}
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+    with open(path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(kern, indent=1))
     return 0
