@@ -194,11 +194,23 @@ TRAFFIC_COMMANDS = [
 ]
 
 
-def stencil_source_hash():
+def code_only(text):
+    """A CUDA source without its comments and with whitespace collapsed: what the compiler sees
+    of it (the stencil sources hold no string literal with a comment marker)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def stencil_source_hash(read=None):
+    """sha256 of the stencil sources' code (comments and layout do not count); `read(name)`
+    gives a source's text (default: the working tree)."""
     import hashlib
+    read = read or (lambda f: open(os.path.join(ROOT, "paper_2202_07388_gb300", "csrc", f)).read())
     h = hashlib.sha256()
     for f in STENCIL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2202_07388_gb300", "csrc", f), "rb").read())
+        h.update(code_only(read(f)).encode())
     return h.hexdigest()
 
 
@@ -246,7 +258,7 @@ def write_traffic(csvs, path=None):
     them and the hash of the stencil sources the capture was taken on."""
     kern = traffic_kernels(csvs)
     out = {"note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch / Vh, 32x32^3 lattice, 12 rhs; "
-                   "bench scales by its own Vh",
+                   "bench scales by its own Vh; source_sha256: the stencil sources' code without comments",
            "commands": TRAFFIC_COMMANDS, "lattice": "32x32x32x32", "nrhs": 12, "kernels": kern,
            "source_sha256": stencil_source_hash()}
     with open(path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:

@@ -1,12 +1,13 @@
 // Deterministic grid reductions in binary64 with a fused "finisher".
 //
-// Every CTA reduces its threads' double partial sums per right-hand side
-// (warp shuffles, then shared memory), writes one partial per (rhs, CTA),
-// and the last CTA to arrive (atomic ticket) sums the partials of that rhs
-// in a fixed order with one warp (16 loads in flight per lane) and runs the
-// finisher that turns the sum into solver scalars (CG alpha / beta, restart
-// norms).  The order of the
-// additions never depends on timing, so results are bitwise reproducible.
+// Every CTA reduces its threads' partial sums per right-hand side (warp
+// shuffles -- binary32 for binary32 site values, see warp_total -- then
+// binary64 through shared memory), writes one binary64 partial per (rhs,
+// CTA), and the last CTA to arrive (atomic ticket) sums the partials of that
+// rhs in a fixed order with one warp (16 loads in flight per lane) and runs
+// the finisher that turns the sum into solver scalars (CG alpha / beta,
+// restart norms).  The order of the additions never depends on timing, so
+// results are bitwise reproducible.
 #pragma once
 #include "oq_internal.h"
 

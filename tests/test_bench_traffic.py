@@ -48,3 +48,14 @@ def test_traffic_from_ncu_logs(tmp_path):
     assert d["source_sha256"] == bench.stencil_source_hash()
     assert d["commands"] == bench.TRAFFIC_COMMANDS and any("--write-traffic" in c for c in d["commands"])
     assert all("--clock-control none" in c for c in d["commands"] if c.startswith("ncu"))
+
+
+def test_source_hash_ignores_comments_not_code():
+    import bench
+    src = {f: "int a = 1; // one\n/* block\n comment */ float b;\n" for f in bench.STENCIL_SOURCES}
+    h0 = bench.stencil_source_hash(lambda f: src[f])
+    commented = dict(src, **{bench.STENCIL_SOURCES[0]: "// header\nint a = 1;   // other words\nfloat b;\n"})
+    assert bench.stencil_source_hash(lambda f: commented[f]) == h0
+    changed = dict(src, **{bench.STENCIL_SOURCES[0]: "int a = 2; float b;\n"})
+    assert bench.stencil_source_hash(lambda f: changed[f]) != h0
+    assert bench.traffic_for("dw_hat_pass1_odd/store/f16/nr2/u12") is not None   # the committed capture is current
