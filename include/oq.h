@@ -323,8 +323,27 @@ int oq_tune_set(oq_handle h, int lat, int prec, int mode, int nrhs, int bx, int 
  *   global memory, ~217 registers, one 256-site block per SM; 2 = operands
  *   from global memory, registers capped so that two blocks run per SM.
  *   Other values: OQ_ERR_ARG. */
-enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2, OQ_OPT_NN_TENSOR_CORES = 3, OQ_OPT_SAP_KERNEL = 4 };
+/* OQ_OPT_HISTORY: 1 = the CGNE solves (oq_cgne_solve, oq_cgne_solve_even)
+ *   record solver diagnostics for oq_solve_history; default 0.  Recording
+ *   costs one store per right-hand side and regular step. */
+enum { OQ_OPT_DF64_RESETS = 1, OQ_OPT_TEST_TC_SKIP_MMA = 2, OQ_OPT_NN_TENSOR_CORES = 3, OQ_OPT_SAP_KERNEL = 4,
+       OQ_OPT_HISTORY = 5 };
 int oq_set_option(oq_handle h, int key, int value);
+
+/* Solver diagnostics of the last CGNE solve run with OQ_OPT_HISTORY 1
+ * (Sec. 2, Fig. 4: the recursive residual of the regular steps against the
+ * exact residual of the reset steps), right-hand side rhs:
+ *   kind 0: the relative recursive residual ||r_rec|| / ||eta|| after regular
+ *     step k at out_host[k-1], k = 1 .. steps (the small-type residual norm
+ *     times the inner solve's scale; steps beyond 100,000 are not recorded);
+ *   kind 1: every reset step as a pair out_host[2j] = regular steps done
+ *     before it, out_host[2j+1] = ||eta - Dhat^dag Dhat x|| / ||eta|| from
+ *     the reset's residual (binary64; double-float for an intermediate
+ *     double-float reset that did not meet the target).
+ * Copies min(cap, available) doubles into out_host (host memory) and sets *n
+ * to the number of steps (kind 0) or resets (kind 1) recorded.  OQ_ERR_STATE
+ * if no solve recorded any; OQ_ERR_ARG for rhs or kind out of range. */
+int oq_solve_history(oq_handle h, int rhs, int kind, double* out_host, int cap, int* n);
 
 /* Binary64 reductions over packed fields: out[k] = ||x_k||^2, and
  * out[2k], out[2k+1] = Re, Im <x_k, y_k> (host arrays of nrhs / 2 nrhs). */

@@ -452,6 +452,18 @@ extern "C" int oq_set_option(oq_handle h, int key, int value) {
       if (value < 0 || value > 2) return OQ_ERR_ARG;
       h->sap_kernel = value;
       return OQ_OK;
+    case OQ_OPT_HISTORY: h->history = value != 0; return OQ_OK;
   }
   return OQ_ERR_ARG;
+}
+
+extern "C" int oq_solve_history(oq_handle h, int rhs, int kind, double* out_host, int cap, int* n) {
+  if (!h || !n || cap < 0 || (cap > 0 && !out_host) || (kind != 0 && kind != 1)) return OQ_ERR_ARG;
+  if (h->hist_nrhs == 0) return OQ_ERR_STATE;
+  if (rhs < 0 || rhs >= h->hist_nrhs) return OQ_ERR_ARG;
+  const std::vector<double>& v = kind == 0 ? h->hist_rec[rhs] : h->hist_reset[rhs];
+  *n = kind == 0 ? (int)v.size() : (int)(v.size() / 2);
+  const size_t m = v.size() < (size_t)cap ? v.size() : (size_t)cap;
+  if (m) memcpy(out_host, v.data(), sizeof(double) * m);
+  return OQ_OK;
 }

@@ -96,12 +96,21 @@ cudaError_t reduce_dot(int prec, const void* x, const void* y, long Vh, long str
 // CGNE vector steps
 // ---------------------------------------------------------------------------
 
-// p = r + beta p   (right-hand sides in MODE_RUN)
+// p = r + beta p   (right-hand sides in MODE_RUN).  hist (diagnostics,
+// nullable): thread 0 of each rhs records the recursive residual
+// sqrt(rr) * scale of the regular step just done at hist[rhs][steps - 1]
+// (launched after every step's CG update and before any restart, so a
+// gated-off rhs only rewrites its last entry with the same value)
 template <int P>
-__global__ void __launch_bounds__(256) cg_p_kernel(char* p, const char* r, long Vh, long stride, const CgState* cg) {
+__global__ void __launch_bounds__(256) cg_p_kernel(char* p, const char* r, long Vh, long stride, const CgState* cg,
+                                                   double* hist, int hcap) {
   typedef typename PrecTraits<P>::R R;
   const int rhs = blockIdx.y;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (hist && i == 0) {
+    const CgState& c = cg[rhs];
+    if (c.steps >= 1 && c.steps <= hcap) hist[(long)rhs * hcap + c.steps - 1] = sqrt(c.rr) * c.scale;
+  }
   if (i >= Vh || cg[rhs].mode != MODE_RUN) return;
   const R beta = (R)cg[rhs].beta;
   Spinor<R> pv, rv;
@@ -118,15 +127,15 @@ __global__ void __launch_bounds__(256) cg_p_kernel(char* p, const char* r, long 
 }
 
 cudaError_t cg_update_p(int prec, void* p, const void* r, long Vh, long stride, int nrhs, const CgState* cg,
-                        cudaStream_t s) {
+                        cudaStream_t s, double* hist, int hcap) {
   dim3 grid((unsigned)((Vh + 255) / 256), nrhs), block(256);
   char* pp = (char*)p;
   const char* rr = (const char*)r;
   switch (prec) {
-    case P_F64: cg_p_kernel<P_F64><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg); break;
-    case P_F32: cg_p_kernel<P_F32><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg); break;
-    case P_BF16: cg_p_kernel<P_BF16><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg); break;
-    case P_F16: cg_p_kernel<P_F16><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg); break;
+    case P_F64: cg_p_kernel<P_F64><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg, hist, hcap); break;
+    case P_F32: cg_p_kernel<P_F32><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg, hist, hcap); break;
+    case P_BF16: cg_p_kernel<P_BF16><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg, hist, hcap); break;
+    case P_F16: cg_p_kernel<P_F16><<<grid, block, 0, s>>>(pp, rr, Vh, stride, cg, hist, hcap); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -166,6 +166,16 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
     cs[k].rd2 = h->results_host[k];
     cs[k].nmx = prm->nmx;
   }
+  // diagnostics (OQ_OPT_HISTORY): the recursive residual of every regular step
+  // (recorded on the device by the p update) and the residual of every reset
+  double* hist = nullptr;
+  const int hcap = prm->nmx < 100000 ? prm->nmx : 100000;
+  std::vector<std::vector<double>> reset_hist;
+  if (h->history) {
+    RK(h->workspace(lat, "cg_hist", sizeof(double) * (size_t)hcap * nrhs, (void**)&hist));
+    CK(cudaMemsetAsync(hist, 0, sizeof(double) * (size_t)hcap * nrhs, s));
+    reset_hist.assign(nrhs, {});
+  }
 
   // decide, per rhs in MODE_RESET, between DONE, PARK (a later phase of the
   // ladder) and a restart of the small CG in the current phase
@@ -298,7 +308,7 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
     a.ep_r = rv; a.ep_r_stride = (long)hP;
     a.red = h->red_args(FIN_BETA, MODE_RUN);
     RK(h->run_hop(h->hop_launch(lat, P, HOP_P2, 1, EPI_CG, nrhs), a, s));
-    KL(cg_update_p(P, pv, rv, Vh, (long)hP, nrhs, h->cg_dev, s));
+    KL(cg_update_p(P, pv, rv, Vh, (long)hP, nrhs, h->cg_dev, s, hist, hcap));
     return OQ_OK;
   };
 
@@ -395,6 +405,12 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
               df_ok = false;
         }
       }
+      if (hist)
+        for (int k = 0; k < nrhs; ++k)
+          if (cs[k].mode == MODE_RESET) {
+            reset_hist[k].push_back((double)cs[k].steps);
+            reset_hist[k].push_back(eta_n[k] > 0.0 ? sqrt(cs[k].rd2) / eta_n[k] : 0.0);
+          }
       pending = decide(true);
       mark_starts();
       RK(upload());
@@ -417,6 +433,18 @@ static int cgne_impl(oq_handle h, int lat, const oq_solver_params* prm, const do
   if (!half) CK(cudaMemsetAsync(psi_dev, 0, canon_field * nrhs, s));
   KL(unpack_spinor(L.g, P_F64, OQ_EVEN, xd, psi_dev, 1.0, nrhs, (long)h64, canon_stride, s, half));
   CK(cudaStreamSynchronize(s));
+  if (hist) {
+    std::vector<double> rec((size_t)hcap * nrhs);
+    CK(cudaMemcpy(rec.data(), hist, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost));
+    h->hist_rec.assign(nrhs, {});
+    for (int k = 0; k < nrhs; ++k) {
+      const int m = cs[k].steps < hcap ? cs[k].steps : hcap;
+      for (int j = 0; j < m; ++j)
+        h->hist_rec[k].push_back(eta_n[k] > 0.0 ? rec[(size_t)k * hcap + j] / eta_n[k] : 0.0);
+    }
+    h->hist_reset = reset_hist;
+    h->hist_nrhs = nrhs;
+  }
   int ret = OQ_OK;
   for (int k = 0; k < nrhs; ++k) {
     phase_steps[4 * k + phase] = cs[k].steps - steps_before[k];

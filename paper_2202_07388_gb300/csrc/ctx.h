@@ -103,17 +103,24 @@ struct oq_ctx {
   std::map<oq::TuneKey, oq::TuneVal> tuned;
   // kernels launched by this handle so far
   long long launches = 0;
-  // CGNE: intermediate reset residuals in double-float arithmetic (off by
-  // default: measured slower than native binary64 on GB300)
+  // CGNE: intermediate reset residuals in double-float arithmetic (default:
+  // ~3x faster per pass than binary64 on GB300; every stop decision binary64)
   bool df64_resets = true;   // OQ_OPT_DF64_RESETS
   // test hook: the tensor-core PTC layer issues no MMA, so its bounded wait runs out
   bool hook_tc_skip_commit = false;
-  // SAP block kernel with registers capped for two CTAs per SM (measured ~5 %
-  // faster on GB300 than one CTA with ~217 registers)
+  // SAP block kernel: 0 operands staged in shared memory, 1 operands from
+  // global memory, 2 the same register-capped for two CTAs per SM
   int sap_kernel = 0;        // OQ_OPT_SAP_KERNEL
   // NN-preconditioned GCR applies the network with the tensor-core layers
   // instead of the (measured faster) binary32 CUDA-core ones
   bool nn_tensor_cores = false;
+  // solver diagnostics (OQ_OPT_HISTORY): CGNE's relative recursive residual
+  // after every regular step and its relative residual at every reset, per
+  // rhs, of the last solve that recorded them
+  bool history = false;
+  int hist_nrhs = 0;                                    // 0: nothing recorded
+  std::vector<std::vector<double>> hist_rec;            // [rhs][step - 1]
+  std::vector<std::vector<double>> hist_reset;          // [rhs]: step, residual, step, residual, ...
   // profiling
   bool prof_on = false;
   std::vector<oq::ProfRec> prof;

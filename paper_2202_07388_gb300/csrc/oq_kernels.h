@@ -41,8 +41,9 @@ cudaError_t reduce_dot(int prec, const void* x, const void* y, long Vh, long str
 int reduce_grid(long nsites);
 
 // CGNE vector kernels (gated on CgState::mode)
+// hist (nullable): [nrhs][hcap] record of sqrt(rr) * scale after every regular step
 cudaError_t cg_update_p(int prec, void* p, const void* r, long Vh, long stride, int nrhs, const CgState* cg,
-                        cudaStream_t s);
+                        cudaStream_t s, double* hist = nullptr, int hcap = 0);
 // xdf (optional): also write the double-float split of the new x_d (rhs in MODE_RESET)
 cudaError_t cg_accumulate_x(int xprec, double* xd, const void* xs, long Vh, long stride_xd, long stride_xs,
                             int nrhs, const CgState* cg, cudaStream_t s,

@@ -23,7 +23,7 @@ F64, F32, BF16, F16, DF64 = 0, 1, 2, 3, 4
 LINK_18, LINK_12 = 0, 1
 EVEN, ODD, FULL = 0, 1, 2
 PREC = {"fp64": F64, "fp32": F32, "bf16": BF16, "fp16": F16, "df64": DF64}
-OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA, OPT_NN_TENSOR_CORES, OPT_SAP_KERNEL = 1, 2, 3, 4
+OPT_DF64_RESETS, OPT_TEST_TC_SKIP_MMA, OPT_NN_TENSOR_CORES, OPT_SAP_KERNEL, OPT_HISTORY = 1, 2, 3, 4, 5
 
 BC_HALO = 2   # bc_t of a time-split sub-domain
 
@@ -120,6 +120,7 @@ _SIGS = {
     "oq_dhat_pass": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, C.POINTER(OqHalo), _P]),
     "oq_axpby": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), _P, C.POINTER(C.c_double), _P,
                            C.c_int, _P]),
+    "oq_solve_history": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "oq_profile_start": (C.c_int, [_P]),
     "oq_kernel_launches": (C.c_longlong, [_P]),
     "oq_profile_stop": (C.c_int, [_P, C.POINTER(OqKernelTime), C.c_int, C.POINTER(C.c_int)]),
@@ -414,6 +415,22 @@ class Handle:
 
     def set_option(self, key, value):
         _check(lib().oq_set_option(self.h, key, int(value)), "oq_set_option")
+
+    def solve_history(self, rhs=0):
+        """Diagnostics of the last CGNE solve run with OPT_HISTORY: (recursive, resets) for one
+        right-hand side, recursive[k-1] = ||r_rec|| / ||eta|| after regular step k, resets an
+        (n, 2) array of (steps before the reset, relative residual of the reset)."""
+        import numpy as np
+        n = C.c_int()
+        _check(lib().oq_solve_history(self.h, rhs, 0, None, 0, C.byref(n)), "oq_solve_history")
+        rec = np.zeros(n.value)
+        _check(lib().oq_solve_history(self.h, rhs, 0, rec.ctypes.data_as(C.POINTER(C.c_double)), n.value,
+                                      C.byref(n)), "oq_solve_history")
+        _check(lib().oq_solve_history(self.h, rhs, 1, None, 0, C.byref(n)), "oq_solve_history")
+        rst = np.zeros(2 * n.value)
+        _check(lib().oq_solve_history(self.h, rhs, 1, rst.ctypes.data_as(C.POINTER(C.c_double)), 2 * n.value,
+                                      C.byref(n)), "oq_solve_history")
+        return rec, rst.reshape(-1, 2)
 
     # tuning ------------------------------------------------------------
     def autotune(self, prec, nrhs=1, lat=0, stream=None):

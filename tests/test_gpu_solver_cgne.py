@@ -196,3 +196,55 @@ def test_cgne_on_pinned_host_fields():
                                    ctypes.c_void_p(p_host.data_ptr()), n, sts, _stream())
     assert rc3 == oq.ERR_ARG
     h.close()
+
+
+def test_cgne_history():
+    """OQ_OPT_HISTORY (Sec. 2, Fig. 4): the relative recursive residual after
+    every regular step and the relative residual of every reset step.
+    Binary64 storage: the recursive residuals agree with the oracle's binary64
+    CGNE history.  Binary16 storage, 3 rhs: one record per step, one per
+    reset, the last reset the reported residual, and every inner solve ends
+    at the first step whose recursive residual is below delta (10 eps of
+    binary16) times the residual it started from, or below the target."""
+    oq = _oq()
+    dims = (8, 6, 4, 10)
+    u, a, ainv = oracle_case(dims, 0.5, 3, 0.135, 1.0)
+    h = make_handle(dims, u, 0.135, 1.0, oq.LINK_12)
+    n_ = oq.C.c_int()
+    assert oq.lib().oq_solve_history(h.h, 0, 0, None, 0, oq.C.byref(n_)) == oq.ERR_STATE   # none recorded
+    h.set_option(oq.OPT_HISTORY, 1)
+
+    eta = dirac.even_part(synth.make_source(dims, 311))
+    psi = to_dev(np.zeros_like(eta))
+    rc, st = h.cgne(to_dev(eta), psi, oq.SolverParams(res=1e-10, nmx=5000, sdtype=oq.F64))
+    assert rc == oq.OK
+    rec, rst = h.solve_history(0)
+    assert len(rec) == st[0]["steps"] and len(rst) == st[0]["resets"] >= 1
+    assert rst[-1, 0] == st[0]["steps"] and np.isclose(rst[-1, 1], st[0]["true_rel_res"], rtol=1e-14)
+    ref = solvers.cgne(lambda v: dirac.dw_hat_dagger(u, a, ainv, dirac.dw_hat(u, a, ainv, v)),
+                       eta, 1e-10, 5000, "fp64", history=True, ncomp=eta.size // 2)
+    m = min(12, len(rec), len(ref.history))
+    assert np.allclose(rec[:m], [hh[2] for hh in ref.history[:m]], rtol=1e-8, atol=0.0)
+    assert oq.lib().oq_solve_history(h.h, 1, 0, None, 0, oq.C.byref(n_)) == oq.ERR_ARG    # one rhs solved
+    assert oq.lib().oq_solve_history(h.h, 0, 2, None, 0, oq.C.byref(n_)) == oq.ERR_ARG    # kind 0 / 1
+
+    n = 3
+    eta3 = np.stack([dirac.even_part(e) for e in synth.make_source(dims, 312, nrhs=n)])
+    psi3 = to_dev(np.zeros_like(eta3))
+    rc, st = h.cgne(to_dev(eta3), psi3, oq.SolverParams(res=1e-10, nmx=5000, sdtype=oq.F16), nrhs=n)
+    assert rc == oq.OK
+    delta = 10.0 * 2.0 ** -10
+    for k in range(n):
+        rec, rst = h.solve_history(k)
+        assert len(rec) == st[k]["steps"] and len(rst) == st[k]["resets"] >= 2
+        assert rst[-1, 0] == st[k]["steps"] and np.isclose(rst[-1, 1], st[k]["true_rel_res"], rtol=1e-14)
+        assert np.all(np.diff(rst[:, 0]) > 0) and rst[-1, 1] < rst[0, 1]
+        start, prev = 0, 1.0                     # the first inner solve starts from eta
+        for step, res in rst:
+            step = int(step)
+            inner = rec[start:step]
+            stop = np.minimum(delta * prev, 1e-10)
+            met = (inner <= delta * prev * 1.01) | (inner <= 1e-10 * 1.01)
+            assert met[-1], (k, step)            # the inner solve ended on the reset rule
+            assert not np.any((inner[:-1] <= delta * prev * 0.99) | (inner[:-1] <= 1e-10 * 0.99)), (k, step, stop)
+            start, prev = step, res
